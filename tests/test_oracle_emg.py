@@ -1,0 +1,154 @@
+"""Pins of the oracle's PRK, EXP1/Krylov, transfer operators and control (Secs. 2, 4)."""
+import math
+
+import numpy as np
+import pytest
+import scipy.integrate
+import scipy.linalg
+
+from oracle import emg
+from oracle.basis import exponents
+from oracle.dg import DG
+from tests.helpers import perturbed_state
+from workloads import BC_FARFIELD, ogrid
+
+
+def test_prk_amplification_polynomial():
+    """Linear scalar R(u) = lam (u - u*): one PRK step with P = 1/dtau - lam multiplies
+    the error by sum_{j<=4} z^j/j!, z = lam/(1/dtau - lam) (from beta_k = 1/(s-k+1))."""
+    for lam, dt in [(-2.0, 0.3), (-50.0, 10.0), (-0.1 + 0.0, 100.0)]:
+        ustar = 0.7
+        u0 = np.array([[[1.9]]])
+        P = np.array([[[1.0 / dt - lam]]])
+        u1 = emg.prk_step(lambda u: lam * (u - ustar), P, u0, stages=4)
+        z = lam / (1.0 / dt - lam)
+        g = sum(z ** j / math.factorial(j) for j in range(5))
+        assert abs((u1[0, 0, 0] - ustar) - g * (1.9 - ustar)) < 1e-14
+
+
+def rand_stable(K, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((K, K)) / np.sqrt(K)
+    return A - 2.5 * np.eye(K)
+
+
+def test_krylov_phi1_equals_dense_when_space_is_exhausted():
+    for K, seed in [(6, 0), (15, 1)]:
+        A = rand_stable(K, seed) * 7.0
+        b = np.random.default_rng(seed + 10).standard_normal(K)
+        y, k = emg.krylov_phi1(lambda x: A @ x, b, m=30)
+        assert K <= k <= K + 1       # MGS may need one extra step to see the breakdown
+        dense = np.linalg.solve(A, (scipy.linalg.expm(A) - np.eye(K)) @ b)
+        assert np.allclose(y, dense, rtol=1e-11, atol=1e-12)
+
+
+def test_phi1_of_diagonal_matrix_closed_form():
+    d = np.array([-30.0, -1.0, -1e-3, 0.0, 0.5])
+    b = np.ones(5)
+    y, k = emg.krylov_phi1(lambda x: d * x, b, m=30)
+    ref = np.where(d == 0, 1.0, np.expm1(d) / np.where(d == 0, 1.0, d))
+    assert np.allclose(y, ref, rtol=1e-12)
+
+
+def test_exp1_is_exact_flow_of_linear_ode():
+    """For du/dt = A u + c, u + dt phi_1(dt A)(A u + c) is the exact solution at dt."""
+    K = 8
+    A = rand_stable(K, 3)
+    c = np.random.default_rng(4).standard_normal(K)
+    u0 = np.random.default_rng(5).standard_normal(K)
+    dt = 0.8
+    step, _ = emg.krylov_phi1(lambda x: dt * (A @ x), dt * (A @ u0 + c), m=30)
+    sol = scipy.integrate.solve_ivp(lambda t, u: A @ u + c, (0, dt), u0, rtol=1e-12, atol=1e-13,
+                                    method='DOP853')
+    assert np.allclose(u0 + step, sol.y[:, -1], rtol=1e-9, atol=1e-10)
+
+
+def test_exp1_time_step_limits():
+    K = 6
+    A = rand_stable(K, 7)
+    R = np.random.default_rng(8).standard_normal(K)
+    small, _ = emg.krylov_phi1(lambda x: 1e-8 * (A @ x), 1e-8 * R, m=30)
+    assert np.allclose(small, 1e-8 * R, rtol=1e-7)
+    big, _ = emg.krylov_phi1(lambda x: 1e3 * (A @ x), 1e3 * R, m=30)
+    assert np.allclose(big, -np.linalg.solve(A, R), rtol=1e-9)      # Newton step
+
+
+def test_restriction_prolongation_identities():
+    dg = DG(ogrid(6, 2), 3)
+    u = perturbed_state(dg, amp=0.05)
+    for p in (3, 2, 1):
+        n0 = dg.N(p - 1)
+        e = u[:, :, :n0] * 0.3
+        # R o P = I
+        assert np.array_equal(emg.restrict(emg.prolong_add(np.zeros_like(u[:, :, :dg.N(p)]), e), n0), e)
+    # the restriction of a degree <= p-1 field is exact: its level-(p-1) expansion
+    # reproduces the field at the level-p points
+    L2, L1 = dg.levels[2], dg.levels[1]
+    coeff = np.random.default_rng(1).standard_normal((dg.E, 5, dg.N(1)))
+    fine = np.zeros((dg.E, 5, dg.N(2)))
+    fine[:, :, :dg.N(1)] = coeff
+    coarse = emg.restrict(fine, dg.N(1))
+    f_at = np.einsum('eai,eqi->eqa', fine, L2.psi)
+    c_at = np.einsum('eai,eqi->eqa', coarse, L2.psi[:, :, :dg.N(1)])
+    assert np.allclose(f_at, c_at, atol=1e-13)
+
+
+def test_cfl_sequence():
+    assert emg.cfl_n(1.0, 1, 2, 100.0, 1.0) == 1.0
+    assert emg.cfl_n(1.0, 6, 2, 100.0, 1.0) == 2.0               # 1 + 5/5
+    assert emg.cfl_n(1e-3, 2, 2, 100.0, 1.0) == 100.0            # capped
+    assert emg.cfl_n(0.05, 2, 3, 100.0, 1.0) == 20.0             # residual branch
+    assert emg.cfl_n(0.0, 2, 3, 100.0, 1.0) == 100.0
+
+
+def test_dtau_freestream_closed_form():
+    dg = DG(ogrid(8, 3), 2, mach=0.3)
+    u = dg.freestream_state()
+    for p in (2, 1, 0):
+        dt = emg.dtau(dg, p, u[:, :, :dg.N(p)], 50.0)
+        assert np.allclose(dt, 50.0 * dg.mesh.h / ((2 * p + 1) * 1.3), rtol=1e-13)
+
+
+def test_vcycle_keeps_a_steady_state():
+    dg = DG(ogrid(8, 3, inner_bc=BC_FARFIELD), 2)
+    u = dg.freestream_state()
+    u1, info = emg.vcycle(dg, u, 1)
+    assert np.abs(u1 - u).max() < 1e-13
+    assert info.res < 1e-15
+
+
+def mirror_map(dg, nt, nr):
+    """Element and sign maps of the reflection y -> -y of the O-grid (theta -> -theta)."""
+    perm = np.empty(dg.E, dtype=np.int64)
+    for l in range(nr):
+        for k in range(nt):
+            perm[l * nt + k] = l * nt + (nt - 1 - k) % nt
+    ex = exponents(2, dg.p_max)
+    sgn_mode = (-1.0) ** ex[:, 1]
+    sgn_var = np.array([1.0, 1.0, -1.0, 1.0, 1.0])
+    return perm, sgn_var[:, None] * sgn_mode[None, :]
+
+
+def test_cylinder_vcycles_preserve_mirror_symmetry():
+    nt, nr = 8, 3
+    dg = DG(ogrid(nt, nr), 1)
+    u = dg.freestream_state()
+    perm, sgn = mirror_map(dg, nt, nr)
+    opts = emg.Options()
+    for n in (1, 2, 3):
+        u, info = emg.vcycle(dg, u, n, opts)
+        if n == 1:
+            opts.res_ref = info.res
+    assert np.abs(u[perm] * sgn[None] - u).max() < 1e-12 * np.abs(u).max()
+
+
+@pytest.mark.slow
+def test_emg_converges_to_the_newton_steady_state():
+    """Path independence: the eMG fixed point is the discrete steady state R_p(U) = 0."""
+    from tests.test_oracle_dg import mms_error
+    _, dg, u_newton = mms_error(4, 1)
+    u0 = np.einsum('eq,eqi,eqa->eai', dg.levels[1].W, dg.levels[1].psi,
+                   dg.exact_state(dg.levels[1].x))
+    u, cycles, ok = emg.solve_steady(dg, u0, drop=1e-11, max_cycles=300)
+    assert ok, cycles
+    assert np.abs(u - u_newton).max() < 1e-9 * np.abs(u_newton).max()
