@@ -1,0 +1,282 @@
+"""Benchmark of the eMG V-cycle on the 128 x 64 cylinder O-grid at p = 4 (one GB300).
+
+A step is one FAS V-cycle p = 4 -> 0 -> 4 (every hot-path kernel: residuals, exact
+block assembly, batched LU, PRK stages, transfers, p = 0 Jacobian, Arnoldi, phi_1).
+`value` is V-cycle throughput in GDoF/s (K = 5 N_4 E degrees of freedom per cycle
+divided by the time per cycle), inputs resident in HBM.  The line also carries the
+DG residual throughput, the wall time to a 1e-10 drop of ||R(rho)||, the end-to-end
+rate through the C ABI with host buffers, the roofline of the dominant kernel and the
+CPU oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl emg|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="cyl128x64_p4", n_theta=128, n_r=64, p_max=4, mach=0.3)
+METRIC = "time to 1e-10 residual drop & DG residual GDoF/s: mixed vs FP64, 1 GB300"
+FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 (non-tensor) nominal; see the design doc
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="emg", choices=["emg", "reference"])
+    ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-10 solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample(steps, warmup):
+    """The oracle's V-cycle (FP64 numpy) on a bounded sample of the workload: the same
+    O-grid family and degree at 16 x 8 elements.  Returns (GDoF/s, seconds, threads)."""
+    from oracle import emg as oemg
+    from oracle.dg import DG
+    from workloads import ogrid
+    dg = DG(ogrid(16, 8), WORKLOAD["p_max"], mach=WORKLOAD["mach"])
+    u = dg.freestream_state()
+    opts = oemg.Options()
+    n = 1
+    for _ in range(warmup):
+        u, _ = oemg.vcycle(dg, u, n, opts)
+        n += 1
+    t = time.perf_counter()
+    for _ in range(steps):
+        u, _ = oemg.vcycle(dg, u, n, opts)
+        n += 1
+    el = time.perf_counter() - t
+    K = 5 * dg.N(WORKLOAD["p_max"]) * dg.E
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        threads = 1
+    return K * steps / el / 1e9, el, threads, dg.E
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, idx, path):
+        self.path = path
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={idx}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return json.load(open(path)), "measured"
+        except Exception:
+            pass
+    return {}, "fallback"
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    v, el, threads, E = oracle_sample(args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "GDoF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "sample": f"oracle V-cycles on the 16x8 O-grid at p=4 ({E} elements)"},
+        "cpu_baseline": {"value": v, "unit": "GDoF/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} oracle V-cycles, 16x8 O-grid, p=4"},
+        "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, el, threads, E = oracle_sample(2, 0)   # before any GPU work (no fork after CUDA init)
+        cpu = {"value": v, "unit": "GDoF/s", "cores": threads, "kind": "oracle",
+               "sample": f"2 oracle V-cycles of the 16x8 O-grid at p=4 ({E} elements), {el:.1f} s"}
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1807_01151_gb300 as emg_pkg
+    from paper_1807_01151_gb300 import perfmodel
+    from workloads import ogrid
+    W = WORKLOAD
+    mesh = ogrid(W["n_theta"], W["n_r"])
+    stream = torch.cuda.Stream()
+    s = emg_pkg.Solver(mesh, p_max=W["p_max"], mach=W["mach"], stream=stream.cuda_stream)
+    E = s.E
+    N = s.n_modes(W["p_max"])
+    K = 5 * N * E
+    F = (4 * E + 2 * W["n_theta"]) // 2
+    # warm-up: free stream and W V-cycles (the timed state is a developing flow)
+    s.set_state(None)
+    for _ in range(args.warmup):
+        s.vcycle(info=False)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                        f"clocks_rank{rank}.csv"))
+    s.profile(True)
+    l0 = s.launch_count
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        s.vcycle(info=False)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = s.launch_count - l0
+    prof = s.profile_read()
+    s.profile(False)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * K * args.steps / (ms * 1e-3) / 1e9
+    # residual throughput (p_max residual, device buffers, back-to-back)
+    u = torch.empty((E, 5, N), dtype=torch.float64, device="cuda")
+    R = torch.empty_like(u)
+    s.get_state(u)
+    torch.cuda.synchronize()
+    for _ in range(10):
+        s.residual(W["p_max"], u, R)
+    nres = 200
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(nres):
+        s.residual(W["p_max"], u, R)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    res_ms = e0.elapsed_time(e1) / nres
+    # end to end through the C ABI with host buffers: H2D state, V-cycle, D2H state + info
+    host = torch.empty((E, 5, N), dtype=torch.float64, pin_memory=True).numpy()
+    s.get_state(host)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.set_state(host)
+        s.vcycle(info=True)
+        s.get_state(host)
+    e2e_s = time.perf_counter() - t0
+    e2e = world * K * args.steps / e2e_s / 1e9
+    # time to a 1e-10 drop from the free stream
+    solve = None
+    if not args.no_solve:
+        s.set_state(None)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = s.solve_steady(drop=1e-10, max_cycles=3000, raise_on_fail=False)
+        solve = {"seconds": time.perf_counter() - t0, "cycles": rep["cycles"], "converged": rep["converged"],
+                 "drop": rep["res_final"] / rep["res0"] if rep["res0"] else None}
+    # roofline of the dominant kernel class over the timed region
+    work = perfmodel.vcycle_work(2, W["p_max"], E, F)
+    top = max((k for k in prof if k in work), key=lambda k: prof[k][0])
+    t_top = prof[top][0] * 1e-3 / args.steps          # seconds per V-cycle
+    flops_top = work[top][0]
+    peaks, src = measured_peaks()
+    achieved = flops_top / t_top / 1e12
+    roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "GB300 FP64 nominal (no FP64 entry in the measured peaks)",
+                "algorithmic_flops_per_cycle": flops_top, "ms_per_cycle": t_top * 1e3,
+                "launches": prof[top][1]}
+    kernels = {k: {"ms_per_cycle": v[0] / args.steps, "launches_per_cycle": v[1] / args.steps}
+               for k, v in prof.items() if v[1]}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": W["name"], "mesh": f"O-grid {W['n_theta']}x{W['n_r']} r in [0.5,20]",
+                       "p_max": W["p_max"], "elements": E, "dof": K, "mach": W["mach"],
+                       "l2": "working set per V-cycle > L2 (block factors 369 MB + tables)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "residual_gdofs": K / (res_ms * 1e-3) / 1e9, "residual_ms": res_ms,
+            "time_to_1e-10": solve,
+            "e2e": {"value": e2e, "unit": "GDoF/s", "h2d_bytes_per_step": K * 8, "d2h_bytes_per_step": K * 8 + 64},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "kernels": kernels,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "peaks_source": src,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

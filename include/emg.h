@@ -1,0 +1,188 @@
+/*
+ * emg.h -- C ABI of the GB300 exponential p-multigrid (eMG) solver for the steady
+ * compressible Euler equations with a modal discontinuous Galerkin discretisation
+ * (Li, "Efficient p-multigrid method based on an exponential time discretization
+ * for compressible steady flows", arXiv:1807.01151).
+ *
+ * Conventions for every call:
+ *   - Plain C types only; no exceptions cross the boundary.  Every call returns an
+ *     emg_status; on failure emg_last_error(ctx) holds a one-line message.
+ *   - A context owns all device memory it allocates (freed by emg_destroy).  Caller
+ *     arrays are only read/written during the call.
+ *   - `on_device` = 0: the pointer is host memory (pageable or pinned); the call
+ *     copies through the context's stream and returns after the data is in place.
+ *     `on_device` = 1: the pointer is device memory on the context's device; work is
+ *     enqueued on the context's stream and the call returns without synchronising,
+ *     except where a host-visible scalar output (emg_cycle_info, norms, Krylov
+ *     dimension) is requested, which synchronises the stream.
+ *   - Modal states use the canonical layout [n_elems][5][N_p] (float64), variables
+ *     (rho, rho u, rho v, rho w, rho E) (rho w is kept, and stays 0, in 2-D), modes
+ *     in the basis order: total degree 0..p, within a degree x exponent descending,
+ *     then y (then z).  N_p = (p+1)(p+2)/2 in 2-D, (p+1)(p+2)(p+3)/6 in 3-D.
+ *   - A context is not thread-safe; distinct contexts may be used concurrently.
+ */
+#ifndef EMG_H
+#define EMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct emg_ctx emg_ctx;
+
+typedef enum {
+    EMG_OK = 0,
+    EMG_ERR_ARG = 1,           /* invalid argument or unsupported configuration      */
+    EMG_ERR_OOM = 2,           /* admission: the context does not fit in free memory */
+    EMG_ERR_CUDA = 3,          /* a CUDA runtime call failed                         */
+    EMG_ERR_NONFINITE = 4,     /* NaN/Inf in a state or residual                      */
+    EMG_ERR_UNPHYSICAL = 5,    /* non-positive density or pressure at a cell centre  */
+    EMG_ERR_NOT_CONVERGED = 6, /* emg_solve_steady reached max_cycles                 */
+    EMG_ERR_TIMEOUT = 7        /* a bounded device-side wait gave up                  */
+} emg_status;
+
+/* Boundary codes of emg_mesh_desc.face_bc. */
+#define EMG_BC_INTERIOR (-1)
+#define EMG_BC_WALL 1      /* inviscid slip wall: ghost with mirrored normal velocity (Sec. 3.3) */
+#define EMG_BC_FARFIELD 2  /* characteristic far field from 1-D Riemann invariants (Sec. 5)     */
+
+typedef enum {
+    EMG_PREC_FP64 = 0,        /* every step in float64                                   */
+    EMG_PREC_FP32_BLOCKS = 1  /* PRK block assembly, LU and solves in float32; residual,
+                                 Arnoldi and phi_1 in float64                             */
+} emg_prec;
+
+/* Mesh of straight-sided bilinear quadrilaterals (dim 2) or trilinear hexahedra (dim 3).
+ * xyz: [dim][n_nodes] (structure of arrays).  elem_nodes: [n_elems][2^dim], reference
+ * node order (-1,-1),(1,-1),(1,1),(-1,1) (quads); the same at zeta=-1 then zeta=+1
+ * (hexes); the map must have a positive Jacobian determinant.  face_bc: [n_elems][2*dim],
+ * local face f = 2*axis + (side > 0) (xi-, xi+, eta-, eta+, zeta-, zeta+); -1 marks an
+ * interior face whose neighbour is found by matching its nodes. */
+typedef struct {
+    int32_t dim;
+    int64_t n_nodes;
+    const double* xyz;
+    int64_t n_elems;
+    const int64_t* elem_nodes;
+    const int32_t* face_bc;
+} emg_mesh_desc;
+
+typedef struct {
+    double gamma;          /* ratio of specific heats (7/5, Sec. 3)                         */
+    double mach;           /* free-stream Mach number; rho = 1, p = 1/gamma                  */
+    double alpha_deg;      /* free-stream angle in the x-y plane                              */
+    int32_t p_max;         /* finest DG degree, 0..4                                          */
+    int32_t rk_stages;     /* s of Eq. prk_scalar (paper: 4)                                  */
+    int32_t krylov_m;      /* Krylov dimension of the EXP1 step (paper: 30), <= 64            */
+    double cfl_max;        /* CFL_max of Eq. cfl (paper: 100 for eMG)                         */
+    double exp_dt_factor;  /* EXP1 step = factor * dtau(p_max); <= 0 selects p_max + 1 (Sec. 4) */
+    int32_t pre_smooth;    /* PRK steps per level on the down leg (default 1)                 */
+    int32_t prec;          /* emg_prec                                                         */
+    void* cuda_stream;     /* cudaStream_t to run on; NULL = a stream owned by the context     */
+} emg_params;
+
+typedef struct {
+    int64_t n;             /* index of the V-cycle just run (1-based)                         */
+    double res_rho;        /* ||R(rho)|| of Eq. cfl at the state entering this cycle          */
+    double res[5];         /* the same norm for each conservative variable                   */
+    double cfl;            /* CFL_n used by this cycle                                        */
+    int32_t krylov_dim;    /* Arnoldi steps taken by the EXP1 step                            */
+} emg_cycle_info;
+
+typedef struct {
+    int64_t cycles;        /* V-cycles run                                                    */
+    double res0;           /* ||R(rho)|| of the initial state                                 */
+    double res_final;      /* ||R(rho)|| of the returned state                                */
+    int32_t converged;     /* 1 if res_final <= drop * res0                                    */
+} emg_solve_report;
+
+/* Fill p with the paper's defaults (gamma 1.4, Ma 0.3, alpha 0, p_max 2, s = 4, m = 30,
+ * CFL_max = 100, EXP1 factor p_max+1, 1 PRK step per level, FP64, own stream). */
+void emg_default_params(emg_params* p);
+
+/* Build connectivity, geometry (|E|, x_c, half bounding box L, |dE|, h = 2d|E|/|dE|,
+ * Eq. x3d), the orthonormal Cartesian basis of Eqs. basis2/basis by modified
+ * Gram-Schmidt and the quadrature tables of every level (Gauss-Legendre, q = p + 2 per
+ * direction), all on the device.  Admission: fails with EMG_ERR_OOM, allocating
+ * nothing, when the estimated footprint exceeds the device's free memory.  The state is
+ * initialised to the free stream. */
+emg_status emg_create_mesh(const emg_mesh_desc* mesh, const emg_params* params, emg_ctx** out);
+emg_status emg_destroy(emg_ctx* ctx);
+const char* emg_last_error(const emg_ctx* ctx);
+
+/* Bytes of device memory the context holds. */
+int64_t emg_device_bytes(const emg_ctx* ctx);
+
+/* Set / get the p_max state, [n_elems][5][N_pmax].  U = NULL in emg_set_state selects the
+ * free stream.  emg_set_state restarts the CFL schedule of Eq. cfl (cycle counter 1,
+ * reference residual unset) and rejects non-finite input (EMG_ERR_NONFINITE). */
+emg_status emg_set_state(emg_ctx* ctx, const double* U, int32_t on_device);
+emg_status emg_get_state(emg_ctx* ctx, double* U, int32_t on_device);
+
+/* CFL schedule state (Eq. cfl): the index of the next V-cycle and the reference
+ * residual ||R(rho_1)|| (<= 0: taken from the next cycle).  For checkpoint/resume. */
+emg_status emg_set_cycle(emg_ctx* ctx, int64_t n, double res_ref);
+emg_status emg_get_cycle(emg_ctx* ctx, int64_t* n, double* res_ref);
+
+/* One FAS V-cycle p_max -> 0 -> p_max (Sec. 2.3): one PRK step (Eq. prk_scalar) per level
+ * p >= 1 with exact element-diagonal Jacobian blocks (Eq. jac1) and P = I/dtau - dR/du,
+ * restriction/forcing, EXP1 (Eq. EXP1) with an Arnoldi phi_1 product (Eqs. vm, final) on
+ * p = 0, prolongation and correction.  info may be NULL (then nothing is read back). */
+emg_status emg_vcycle(emg_ctx* ctx, emg_cycle_info* info);
+
+/* Run V-cycles until ||R(rho)|| <= drop * ||R(rho)|| of the entry state, or max_cycles.
+ * Returns EMG_ERR_NOT_CONVERGED (report still filled) when the cap is reached. */
+emg_status emg_solve_steady(emg_ctx* ctx, double drop, int64_t max_cycles, emg_solve_report* report);
+
+/* ||R(rho)|| (Eq. cfl) and the per-variable norms of the current p_max state. */
+emg_status emg_residual_norm(emg_ctx* ctx, double* res_rho, double* res5);
+
+/* ---- component entry points (same kernels as emg_vcycle; used by parity tests) ---- */
+
+/* R_p(u) of Eq. euler3, u and R [n_elems][5][N_p]. */
+emg_status emg_residual(emg_ctx* ctx, int32_t p, const double* u, double* R, int32_t on_device);
+
+/* Element-diagonal Jacobian blocks D_e = dR_{p,e}/du_e (Eq. jac1, with the boundary chain
+ * rule of Sec. 3.3), [n_elems][5 N_p][5 N_p] row-major, row/column index var*N_p + mode. */
+emg_status emg_jacobian_diag(emg_ctx* ctx, int32_t p, const double* u, double* D, int32_t on_device);
+
+/* One PRK step (Eq. prk_scalar) at level p >= 1 from u with forcing tau (NULL = 0) at the
+ * given CFL: P_e = I/dtau_e - D_e(u), dtau_e of Eq. x3d. */
+emg_status emg_prk_step(emg_ctx* ctx, int32_t p, const double* u, const double* tau, double cfl,
+                        double* u_out, int32_t on_device);
+
+/* p = 0 Jacobian in block-sparse form (Eqs. jac1, jac2): diag [n_elems][5][5],
+ * off [n_elems][2 dim][5][5] (dR_e/du_nb across local face f; zero on boundaries),
+ * nbr [n_elems][2 dim] (neighbour index or -1). */
+emg_status emg_jacobian_p0(emg_ctx* ctx, const double* u0, double* diag, double* off, int64_t* nbr,
+                           int32_t on_device);
+
+/* One EXP1 step on level 0 (Eq. EXP1): u0 + phi_1(DT J_0) DT (R_0(u0) + tau0), DT =
+ * diag(dt_e); tau0 may be NULL.  krylov_dim receives the Arnoldi steps taken. */
+emg_status emg_exp1_step(emg_ctx* ctx, const double* u0, const double* tau0, const double* dt,
+                         double* u_out, int32_t* krylov_dim, int32_t on_device);
+
+/* Element volumes |E| and length scales h = 2d|E|/|dE| (Eq. x3d), [n_elems] each. */
+emg_status emg_element_geometry(emg_ctx* ctx, double* vol, double* h);
+
+/* ---- tracing (no counterpart in the paper) ----
+ * Event profiler: when enabled, every kernel launch of the context is bracketed by CUDA
+ * events on the context's stream and its time accumulated per kernel class (class ids
+ * 0..12, names from emg_profile_class_name).  Enabling or disabling resets the totals.
+ * emg_profile_read synchronises the stream. */
+emg_status emg_profile_enable(emg_ctx* ctx, int32_t on);
+emg_status emg_profile_read(emg_ctx* ctx, int32_t cls, double* total_ms, int64_t* launches);
+const char* emg_profile_class_name(int32_t cls);
+/* Number of kernels the context has launched since creation. */
+int64_t emg_launch_count(const emg_ctx* ctx);
+
+/* Build identification string (architecture and kernel variants). */
+const char* emg_build_info(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMG_H */

@@ -149,8 +149,9 @@ def vcycle_entry(dg, u, n, opts):
     """Residual, its norm and CFL_n at the state entering V-cycle n."""
     R0 = dg.residual(dg.p_max, u)
     res = residual_norm(dg, R0)
-    ref = opts.res_ref if opts.res_ref > 0.0 else res
-    return R0, res, cfl_n(res, n, dg.p_max, opts.cfl_max, ref)
+    if not opts.res_ref > 0.0:
+        opts.res_ref = res          # the first cycle fixes the reference residual
+    return R0, res, cfl_n(res, n, dg.p_max, opts.cfl_max, opts.res_ref)
 
 
 def vcycle(dg, u, n, opts=None):

@@ -1,0 +1,519 @@
+// C ABI (include/emg.h): context life cycle, state I/O, the FAS V-cycle of Sec. 2.3 and
+// the component entry points.  All arithmetic runs in the kernels of the other files; this
+// file only sequences launches on the context's stream.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+using namespace emg;
+
+namespace {
+
+emg_status fail(emg_ctx* c, emg_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+emg_status sync(emg_ctx* c) {
+    EMG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return EMG_OK;
+}
+
+emg_status read_scalars(emg_ctx* c) {
+    EMG_CUDA_TRY(c, cudaMemcpyAsync(c->sc_host, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+emg_status copy_in(emg_ctx* c, double* dst, const double* src, int64_t n, int on_device) {
+    EMG_CUDA_TRY(c, cudaMemcpyAsync(dst, src, n * sizeof(double),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    return EMG_OK;
+}
+
+emg_status copy_out(emg_ctx* c, double* dst, const double* src, int64_t n, int on_device) {
+    EMG_CUDA_TRY(c, cudaMemcpyAsync(dst, src, n * sizeof(double),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) return sync(c);
+    return EMG_OK;
+}
+
+}  // namespace
+
+namespace emg {
+
+__global__ void k_set_freestream(int64_t E, int N, const double* __restrict__ vol, double u0, double u1, double u2,
+                                 double u3, double u4, double* __restrict__ v) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= E * 5 * N) return;
+    const int i = (int)(idx % N);
+    const int a = (int)((idx / N) % 5);
+    const int64_t e = idx / (5 * N);
+    const double U[5] = {u0, u1, u2, u3, u4};
+    v[idx] = i == 0 ? U[a] * sqrt(vol[e]) : 0.0;
+}
+
+__global__ void k_set_cfl(DevScalars* sc, double cfl) { sc->cfl = cfl; }
+__global__ void k_set_ref(DevScalars* sc, double ref) { sc->res_ref = ref; }
+
+// One PRK step (Eq. prk_scalar) on level p: u^n = L.v on entry, result in L.v.
+// r_first: R~_p(u^n) if already available (else computed here).
+static emg_status prk_step(emg_ctx* c, int p, const double* tau, const double* r_first) {
+    LevelDev& L = c->lv[p];
+    const int64_t S = c->E * L.B;
+    EMG_CUDA_TRY(c, cudaMemcpyAsync(L.un, L.v, S * 8, cudaMemcpyDeviceToDevice, c->stream));
+    emg_status st = launch_diag_blocks(c, p, L.un, &c->sc->cfl, 1, L.blk);
+    if (st != EMG_OK) return st;
+    st = launch_lu(c, p);
+    if (st != EMG_OK) return st;
+    const int s = c->prm.rk_stages;
+    for (int k = 1; k <= s; ++k) {
+        const double beta = 1.0 / (double)(s - k + 1);
+        const double* r = nullptr;
+        if (k == 1 && r_first) {
+            r = r_first;
+        } else {
+            st = launch_residual(c, p, L.v, tau, L.r);
+            if (st != EMG_OK) return st;
+            r = L.r;
+        }
+        st = launch_stage(c, p, r, L.un, beta, L.v);
+        if (st != EMG_OK) return st;
+    }
+    return EMG_OK;
+}
+
+// Entry of V-cycle n: R_pmax(v), ||R(rho)||, CFL_n and the EXP1 steps dt_e.
+static emg_status vcycle_entry(emg_ctx* c, int64_t n) {
+    LevelDev& T = c->lv[c->p_max];
+    emg_status st = launch_residual(c, c->p_max, T.v, nullptr, T.r);
+    if (st != EMG_OK) return st;
+    return launch_norm_cfl(c, T.r, n, 1);
+}
+
+static emg_status vcycle_body(emg_ctx* c) {
+    const int P = c->p_max;
+    const double fac = c->prm.exp_dt_factor > 0.0 ? c->prm.exp_dt_factor : (double)(P + 1);
+    emg_status st = launch_dtau(c, P, c->lv[P].v, &c->sc->cfl, fac, c->dt);
+    if (st != EMG_OK) return st;
+    for (int p = P; p >= 1; --p) {
+        LevelDev& L = c->lv[p];
+        LevelDev& Lc = c->lv[p - 1];
+        const double* tau = p == P ? nullptr : L.tau;
+        const int64_t S = c->E * L.B;
+        for (int sm = 0; sm < c->prm.pre_smooth; ++sm) {
+            const double* rfirst = nullptr;
+            if (sm == 0) {
+                if (p == P) {
+                    rfirst = L.r;  // R_pmax(v) from the cycle entry
+                } else {
+                    // R~_p(v0_p) = R_p(v0_p) + tau_p, R_p(v0_p) computed for the forcing (in r2)
+                    st = launch_axpby(c, S, 1.0, L.r2, 1.0, L.tau, L.r);
+                    if (st != EMG_OK) return st;
+                    rfirst = L.r;
+                }
+            }
+            st = prk_step(c, p, tau, rfirst);
+            if (st != EMG_OK) return st;
+        }
+        // restriction of the smoothed state and of its residual, FAS forcing of level p-1
+        st = launch_residual(c, p, L.v, tau, L.r);
+        if (st != EMG_OK) return st;
+        st = launch_restrict(c, p, L.v, Lc.v0);
+        if (st != EMG_OK) return st;
+        EMG_CUDA_TRY(c, cudaMemcpyAsync(Lc.v, Lc.v0, c->E * Lc.B * 8, cudaMemcpyDeviceToDevice, c->stream));
+        st = launch_residual(c, p - 1, Lc.v0, nullptr, Lc.r2);
+        if (st != EMG_OK) return st;
+        st = launch_tau(c, p - 1, L.r, Lc.r2, Lc.tau);
+        if (st != EMG_OK) return st;
+    }
+    LevelDev& L0 = c->lv[0];
+    if (P == 0) {
+        EMG_CUDA_TRY(c, cudaMemcpyAsync(L0.v0, L0.v, c->E * 5 * 8, cudaMemcpyDeviceToDevice, c->stream));
+        st = launch_exp1(c, L0.v0, nullptr, c->dt, L0.v);
+    } else {
+        st = launch_exp1(c, L0.v0, L0.tau, c->dt, L0.v);
+    }
+    if (st != EMG_OK) return st;
+    for (int p = 1; p <= P; ++p) {
+        st = launch_prolong(c, p, c->lv[p].v, c->lv[p - 1].v, c->lv[p - 1].v0);
+        if (st != EMG_OK) return st;
+    }
+    return EMG_OK;
+}
+
+void prof_flush(emg_ctx* c) {
+    if (c->prof.used == 0) return;
+    cudaStreamSynchronize(c->stream);
+    for (int k = 0; k < c->prof.used / 2; ++k) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, c->prof.ev[2 * k], c->prof.ev[2 * k + 1]) == cudaSuccess) {
+            c->prof.ms[c->prof.pair_cls[k]] += ms;
+            c->prof.cnt[c->prof.pair_cls[k]] += 1;
+        }
+    }
+    c->prof.used = 0;
+}
+
+static emg_status check_flags(emg_ctx* c) {
+    if (c->sc_host->nonfinite) return fail(c, EMG_ERR_NONFINITE, "non-finite residual or Krylov quantity");
+    if (c->sc_host->pad) return fail(c, EMG_ERR_UNPHYSICAL, "non-positive density or pressure at a cell centre");
+    return EMG_OK;
+}
+
+}  // namespace emg
+
+extern "C" {
+
+void emg_default_params(emg_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->gamma = 1.4;
+    p->mach = 0.3;
+    p->alpha_deg = 0.0;
+    p->p_max = 2;
+    p->rk_stages = 4;
+    p->krylov_m = 30;
+    p->cfl_max = 100.0;
+    p->exp_dt_factor = 0.0;
+    p->pre_smooth = 1;
+    p->prec = EMG_PREC_FP64;
+    p->cuda_stream = nullptr;
+}
+
+const char* emg_build_info(void) {
+    return "emg sm_103a fp64: residual(face Roe + element volume), AD face Jacobians, block assembly, "
+           "smem LU + warp substitution, CGS2 Arnoldi, Pade-13 phi_1";
+}
+
+emg_status emg_create_mesh(const emg_mesh_desc* m, const emg_params* prm, emg_ctx** out) {
+    if (!out) return EMG_ERR_ARG;
+    *out = nullptr;
+    if (!m || !prm) return EMG_ERR_ARG;
+    emg_ctx* c = new (std::nothrow) emg_ctx();
+    if (!c) return EMG_ERR_OOM;
+    *out = c;
+    c->prm = *prm;
+    if (m->dim != 2 && m->dim != 3) return fail(c, EMG_ERR_ARG, "dim must be 2 or 3");
+    if (m->n_elems <= 0 || m->n_nodes <= 0 || !m->xyz || !m->elem_nodes || !m->face_bc)
+        return fail(c, EMG_ERR_ARG, "empty or incomplete mesh");
+    if (m->n_elems > (int64_t)1 << 30) return fail(c, EMG_ERR_ARG, "too many elements");
+    if (prm->p_max < 0 || prm->p_max > MAX_P) return fail(c, EMG_ERR_ARG, "p_max must be in 0..4");
+    if (prm->rk_stages < 1 || prm->rk_stages > 16) return fail(c, EMG_ERR_ARG, "rk_stages must be in 1..16");
+    if (prm->krylov_m < 1 || prm->krylov_m > 40) return fail(c, EMG_ERR_ARG, "krylov_m must be in 1..40");
+    if (!(prm->cfl_max > 0.0)) return fail(c, EMG_ERR_ARG, "cfl_max must be positive");
+    if (prm->pre_smooth < 1) return fail(c, EMG_ERR_ARG, "pre_smooth must be >= 1");
+    if (!(prm->gamma > 1.0) || !(prm->mach >= 0.0)) return fail(c, EMG_ERR_ARG, "bad gamma or mach");
+    if (prm->prec != EMG_PREC_FP64) return fail(c, EMG_ERR_ARG, "only EMG_PREC_FP64 is built");
+    c->p_max = prm->p_max;
+    EMG_CUDA_TRY(c, cudaGetDevice(&c->device));
+    if (prm->cuda_stream) {
+        c->stream = (cudaStream_t)prm->cuda_stream;
+    } else {
+        EMG_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    const double g = prm->gamma;
+    const double a = prm->alpha_deg * M_PI / 180.0;
+    const double vx = prm->mach * std::cos(a), vy = prm->mach * std::sin(a);
+    c->uinf[0] = 1.0;
+    c->uinf[1] = vx;
+    c->uinf[2] = vy;
+    c->uinf[3] = 0.0;
+    c->uinf[4] = (1.0 / g) / (g - 1.0) + 0.5 * (vx * vx + vy * vy);
+    emg_status st = setup_device_mesh(c, m);
+    if (st != EMG_OK) return st;
+    return emg_set_state(c, nullptr, 0);
+}
+
+emg_status emg_destroy(emg_ctx* c) {
+    if (!c) return EMG_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& e : c->prof.ev) cudaEventDestroy(e);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->sc_host) cudaFreeHost(c->sc_host);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return EMG_OK;
+}
+
+const char* emg_last_error(const emg_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int64_t emg_device_bytes(const emg_ctx* c) { return c ? c->bytes : 0; }
+
+emg_status emg_set_state(emg_ctx* c, const double* U, int32_t on_device) {
+    if (!c || !c->sc) return EMG_ERR_ARG;
+    LevelDev& T = c->lv[c->p_max];
+    const int64_t n = c->E * T.B;
+    if (U) {
+        emg_status st = copy_in(c, T.v, U, n, on_device);
+        if (st != EMG_OK) return st;
+    } else {
+        { ProfScope _ps(c, PC_SETUP); k_set_freestream<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(
+            c->E, T.N, c->vol, c->uinf[0], c->uinf[1], c->uinf[2], c->uinf[3], c->uinf[4], T.v); }
+        EMG_CHECK_LAUNCH(c);
+    }
+    EMG_CUDA_TRY(c, cudaMemsetAsync(c->sc, 0, sizeof(DevScalars), c->stream));
+    emg_status st = launch_check_state(c, T.v, n);
+    if (st != EMG_OK) return st;
+    st = read_scalars(c);
+    if (st != EMG_OK) return st;
+    if (c->sc_host->nonfinite) return fail(c, EMG_ERR_NONFINITE, "state contains NaN or Inf");
+    c->cycle_n = 1;
+    c->res_ref = 0.0;
+    return EMG_OK;
+}
+
+emg_status emg_get_state(emg_ctx* c, double* U, int32_t on_device) {
+    if (!c || !U) return EMG_ERR_ARG;
+    LevelDev& T = c->lv[c->p_max];
+    return copy_out(c, U, T.v, c->E * T.B, on_device);
+}
+
+emg_status emg_set_cycle(emg_ctx* c, int64_t n, double res_ref) {
+    if (!c || n < 1) return EMG_ERR_ARG;
+    c->cycle_n = n;
+    { ProfScope _ps(c, PC_CONTROL); k_set_ref<<<1, 1, 0, c->stream>>>(c->sc, res_ref > 0.0 ? res_ref : 0.0); }
+    EMG_CHECK_LAUNCH(c);
+    return EMG_OK;
+}
+
+emg_status emg_get_cycle(emg_ctx* c, int64_t* n, double* res_ref) {
+    if (!c) return EMG_ERR_ARG;
+    emg_status st = read_scalars(c);
+    if (st != EMG_OK) return st;
+    if (n) *n = c->cycle_n;
+    if (res_ref) *res_ref = c->sc_host->res_ref;
+    return EMG_OK;
+}
+
+emg_status emg_vcycle(emg_ctx* c, emg_cycle_info* info) {
+    if (!c) return EMG_ERR_ARG;
+    const int64_t n = c->cycle_n;
+    emg_status st = vcycle_entry(c, n);
+    if (st != EMG_OK) return st;
+    st = vcycle_body(c);
+    if (st != EMG_OK) return st;
+    c->cycle_n = n + 1;
+    if (info) {
+        st = read_scalars(c);
+        if (st != EMG_OK) return st;
+        info->n = n;
+        info->res_rho = c->sc_host->res;
+        for (int a = 0; a < 5; ++a) info->res[a] = c->sc_host->res5[a];
+        info->cfl = c->sc_host->cfl;
+        info->krylov_dim = c->sc_host->m_used;
+        return check_flags(c);
+    }
+    return EMG_OK;
+}
+
+emg_status emg_solve_steady(emg_ctx* c, double drop, int64_t max_cycles, emg_solve_report* rep) {
+    if (!c || !(drop > 0.0) || max_cycles < 0) return EMG_ERR_ARG;
+    double r0 = -1.0, res = 0.0;
+    int64_t done = 0;
+    for (int64_t k = 0; k <= max_cycles; ++k) {
+        const int64_t n = c->cycle_n;
+        emg_status st = vcycle_entry(c, n);
+        if (st != EMG_OK) return st;
+        st = read_scalars(c);
+        if (st != EMG_OK) return st;
+        st = check_flags(c);
+        if (st != EMG_OK) return st;
+        res = c->sc_host->res;
+        if (r0 < 0.0) r0 = res;
+        if (res <= drop * r0 || k == max_cycles) break;
+        st = vcycle_body(c);
+        if (st != EMG_OK) return st;
+        c->cycle_n = n + 1;
+        ++done;
+    }
+    if (rep) {
+        rep->cycles = done;
+        rep->res0 = r0;
+        rep->res_final = res;
+        rep->converged = res <= drop * r0 ? 1 : 0;
+    }
+    if (!(res <= drop * r0)) return fail(c, EMG_ERR_NOT_CONVERGED, "max_cycles reached");
+    return EMG_OK;
+}
+
+emg_status emg_residual_norm(emg_ctx* c, double* res_rho, double* res5) {
+    if (!c) return EMG_ERR_ARG;
+    LevelDev& T = c->lv[c->p_max];
+    emg_status st = launch_residual(c, c->p_max, T.v, nullptr, T.r2);
+    if (st != EMG_OK) return st;
+    st = launch_norm_cfl(c, T.r2, c->cycle_n, 0);
+    if (st != EMG_OK) return st;
+    st = read_scalars(c);
+    if (st != EMG_OK) return st;
+    if (res_rho) *res_rho = c->sc_host->res;
+    if (res5)
+        for (int a = 0; a < 5; ++a) res5[a] = c->sc_host->res5[a];
+    return c->sc_host->nonfinite ? fail(c, EMG_ERR_NONFINITE, "non-finite residual") : EMG_OK;
+}
+
+emg_status emg_residual(emg_ctx* c, int32_t p, const double* u, double* R, int32_t on_device) {
+    if (!c || !u || !R || p < 0 || p > c->p_max) return EMG_ERR_ARG;
+    const int64_t n = c->E * c->lv[p].B;
+    const double* ud = u;
+    double* Rd = R;
+    if (!on_device) {
+        emg_status st = copy_in(c, c->stage_in, u, n, 0);
+        if (st != EMG_OK) return st;
+        ud = c->stage_in;
+        Rd = c->stage_out;
+    }
+    emg_status st = launch_residual(c, p, ud, nullptr, Rd);
+    if (st != EMG_OK) return st;
+    if (!on_device) return copy_out(c, R, Rd, n, 0);
+    return EMG_OK;
+}
+
+emg_status emg_jacobian_diag(emg_ctx* c, int32_t p, const double* u, double* D, int32_t on_device) {
+    if (!c || !u || !D || p < 0 || p > c->p_max) return EMG_ERR_ARG;
+    const int B = c->lv[p].B;
+    const int64_t n = c->E * B;
+    const double* ud = u;
+    double* Dd = D;
+    if (!on_device) {
+        emg_status st = copy_in(c, c->stage_in, u, n, 0);
+        if (st != EMG_OK) return st;
+        ud = c->stage_in;
+        Dd = c->stage_out;
+    }
+    emg_status st = launch_diag_blocks(c, p, ud, &c->sc->cfl, 0, Dd);
+    if (st != EMG_OK) return st;
+    if (!on_device) return copy_out(c, D, Dd, n * B, 0);
+    return EMG_OK;
+}
+
+emg_status emg_prk_step(emg_ctx* c, int32_t p, const double* u, const double* tau, double cfl, double* u_out,
+                        int32_t on_device) {
+    if (!c || !u || !u_out || p < 1 || p > c->p_max || !(cfl > 0.0)) return EMG_ERR_ARG;
+    LevelDev& L = c->lv[p];
+    const int64_t n = c->E * L.B;
+    emg_status st = copy_in(c, L.v, u, n, on_device);
+    if (st != EMG_OK) return st;
+    if (tau) {
+        st = copy_in(c, L.tau, tau, n, on_device);
+        if (st != EMG_OK) return st;
+    }
+    { ProfScope _ps(c, PC_CONTROL); k_set_cfl<<<1, 1, 0, c->stream>>>(c->sc, cfl); }
+    EMG_CHECK_LAUNCH(c);
+    st = prk_step(c, p, tau ? L.tau : nullptr, nullptr);
+    if (st != EMG_OK) return st;
+    return copy_out(c, u_out, L.v, n, on_device);
+}
+
+emg_status emg_jacobian_p0(emg_ctx* c, const double* u0, double* diag, double* off, int64_t* nbr, int32_t on_device) {
+    if (!c || !u0) return EMG_ERR_ARG;
+    const int NF = 2 * c->dim;
+    const int64_t n = c->E * 5;
+    const double* ud = u0;
+    if (!on_device) {
+        emg_status st = copy_in(c, c->stage_in, u0, n, 0);
+        if (st != EMG_OK) return st;
+        ud = c->stage_in;
+    }
+    emg_status st = launch_face_jacobian(c, 0, ud);
+    if (st != EMG_OK) return st;
+    st = launch_bsr0(c);
+    if (st != EMG_OK) return st;
+    std::vector<double> hb((size_t)c->E * (1 + NF) * 25);
+    EMG_CUDA_TRY(c, cudaMemcpyAsync(hb.data(), c->bsr, hb.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<int> hn((size_t)c->E * NF);
+    EMG_CUDA_TRY(c, cudaMemcpyAsync(hn.data(), c->elem_nbr, hn.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+    st = sync(c);
+    if (st != EMG_OK) return st;
+    // unpacking is layout conversion only
+    std::vector<double> hd((size_t)c->E * 25), ho((size_t)c->E * NF * 25);
+    for (int64_t e = 0; e < c->E; ++e) {
+        std::memcpy(&hd[e * 25], &hb[e * (1 + NF) * 25], 25 * 8);
+        std::memcpy(&ho[e * NF * 25], &hb[e * (1 + NF) * 25 + 25], NF * 25 * 8);
+    }
+    if (diag) {
+        if (on_device)
+            EMG_CUDA_TRY(c, cudaMemcpy(diag, hd.data(), hd.size() * 8, cudaMemcpyHostToDevice));
+        else
+            std::memcpy(diag, hd.data(), hd.size() * 8);
+    }
+    if (off) {
+        if (on_device)
+            EMG_CUDA_TRY(c, cudaMemcpy(off, ho.data(), ho.size() * 8, cudaMemcpyHostToDevice));
+        else
+            std::memcpy(off, ho.data(), ho.size() * 8);
+    }
+    if (nbr)
+        for (size_t i = 0; i < hn.size(); ++i) nbr[i] = hn[i];
+    return EMG_OK;
+}
+
+emg_status emg_exp1_step(emg_ctx* c, const double* u0, const double* tau0, const double* dt, double* u_out,
+                         int32_t* krylov_dim, int32_t on_device) {
+    if (!c || !u0 || !dt || !u_out) return EMG_ERR_ARG;
+    LevelDev& L = c->lv[0];
+    const int64_t n = c->E * 5;
+    emg_status st = copy_in(c, c->stage_in, u0, n, on_device);
+    if (st != EMG_OK) return st;
+    if (tau0) {
+        st = copy_in(c, c->stage_in2, tau0, n, on_device);
+        if (st != EMG_OK) return st;
+    }
+    st = copy_in(c, c->stage_small, dt, c->E, on_device);
+    if (st != EMG_OK) return st;
+    st = launch_exp1(c, c->stage_in, tau0 ? c->stage_in2 : nullptr, c->stage_small, c->stage_out);
+    if (st != EMG_OK) return st;
+    (void)L;
+    st = copy_out(c, u_out, c->stage_out, n, on_device);
+    if (st != EMG_OK) return st;
+    st = read_scalars(c);
+    if (st != EMG_OK) return st;
+    if (krylov_dim) *krylov_dim = c->sc_host->m_used;
+    return c->sc_host->nonfinite ? fail(c, EMG_ERR_NONFINITE, "non-finite Krylov quantity") : EMG_OK;
+}
+
+static const char* kClassNames[PC_COUNT] = {"residual_face_flux", "residual_volume", "face_jacobian",
+                                            "diag_block_assembly", "block_lu", "prk_stage_solve", "p0_bsr",
+                                            "arnoldi", "phi1_pade", "krylov_combine", "level_transfer",
+                                            "norm_cfl_dtau", "setup"};
+
+emg_status emg_profile_enable(emg_ctx* c, int32_t on) {
+    if (!c) return EMG_ERR_ARG;
+    prof_flush(c);
+    if (on && c->prof.ev.empty()) {
+        c->prof.ev.resize(16384);
+        c->prof.pair_cls.resize(8192);
+        for (auto& e : c->prof.ev) EMG_CUDA_TRY(c, cudaEventCreate(&e));
+    }
+    for (int k = 0; k < PC_COUNT; ++k) {
+        c->prof.ms[k] = 0.0;
+        c->prof.cnt[k] = 0;
+    }
+    c->prof.on = on != 0;
+    return EMG_OK;
+}
+
+emg_status emg_profile_read(emg_ctx* c, int32_t cls, double* total_ms, int64_t* launches) {
+    if (!c || cls < 0 || cls >= PC_COUNT) return EMG_ERR_ARG;
+    prof_flush(c);
+    if (total_ms) *total_ms = c->prof.ms[cls];
+    if (launches) *launches = c->prof.cnt[cls];
+    return EMG_OK;
+}
+
+const char* emg_profile_class_name(int32_t cls) {
+    return (cls >= 0 && cls < PC_COUNT) ? kClassNames[cls] : nullptr;
+}
+
+int64_t emg_launch_count(const emg_ctx* c) { return c ? c->launches : 0; }
+
+emg_status emg_element_geometry(emg_ctx* c, double* vol, double* h) {
+    if (!c) return EMG_ERR_ARG;
+    if (vol) EMG_CUDA_TRY(c, cudaMemcpyAsync(vol, c->vol, c->E * 8, cudaMemcpyDeviceToHost, c->stream));
+    if (h) EMG_CUDA_TRY(c, cudaMemcpyAsync(h, c->h, c->E * 8, cudaMemcpyDeviceToHost, c->stream));
+    return sync(c);
+}
+
+}  // extern "C"

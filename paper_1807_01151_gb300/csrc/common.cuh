@@ -1,0 +1,201 @@
+// Shared definitions of the eMG CUDA library: compile-time level shapes, the context
+// layout in device memory, and error plumbing.  Everything here is private to the
+// library; the public surface is include/emg.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/emg.h"
+
+namespace emg {
+
+constexpr int NVAR = 5;
+constexpr int MAX_P = 4;
+constexpr int MAX_KRYLOV = 64;
+
+__host__ __device__ constexpr int n_modes(int D, int P) {
+    return D == 2 ? (P + 1) * (P + 2) / 2 : (P + 1) * (P + 2) * (P + 3) / 6;
+}
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// Shapes of level p in dimension D: N modes, q = p + 2 Gauss points per direction,
+// Q volume points, QF points per face, NF faces per element, B = 5N block size.
+template <int D_, int P_>
+struct Lv {
+    static constexpr int D = D_;
+    static constexpr int P = P_;
+    static constexpr int N = n_modes(D_, P_);
+    static constexpr int q = P_ + 2;
+    static constexpr int Q = ipow(P_ + 2, D_);
+    static constexpr int QF = ipow(P_ + 2, D_ - 1);
+    static constexpr int NF = 2 * D_;
+    static constexpr int B = 5 * n_modes(D_, P_);
+    static constexpr int NODES = 1 << D_;
+};
+
+// Device arrays of one multigrid level (p >= 0).
+struct LevelDev {
+    int p = 0, N = 0, q = 0, Q = 0, QF = 0, B = 0;
+    // quadrature tables (per element / per face)
+    double* vpsi = nullptr;    // [E][Q][N]      psi_i(x_q)
+    double* vgw = nullptr;     // [E][D][Q][N]   W_q d_k psi_i(x_q)
+    double* fnrm = nullptr;    // [F][QF][3]     unit outward normal of the L element
+    double* famag = nullptr;   // [F][QF]        w |n dS|
+    double* fpsiL = nullptr;   // [F][QF][N]     psi^L_i at the face points
+    double* fpsiR = nullptr;   // [F_int][QF][N] psi^R_i at the face points
+    // states and work vectors, [E][5][N]
+    double* v = nullptr;       // current approximation
+    double* v0 = nullptr;      // restricted state (levels below p_max)
+    double* tau = nullptr;     // FAS forcing (levels below p_max)
+    double* un = nullptr;      // u^n of the PRK step
+    double* r = nullptr;       // residual work
+    double* r2 = nullptr;      // second residual buffer
+    double* fhat = nullptr;    // [F][QF][5]     w|n dS| F~ at the face points
+    double* fjl = nullptr;     // [F][QF][25]    w|n dS| dF~/dU_L (boundary: total derivative)
+    double* fjr = nullptr;     // [F_int][QF][25] w|n dS| dF~/dU_R
+    double* blk = nullptr;     // [E][B][B]      P_e, then its LU factors (column-major)
+    int* piv = nullptr;        // [E][B]
+};
+
+// Small device-side scalars of the cycle (no host round trip inside a V-cycle).
+struct DevScalars {
+    double cfl;
+    double res;          // ||R(rho)|| at cycle entry
+    double res5[5];
+    double res_ref;      // ||R(rho_1)|| (<= 0: unset)
+    double beta;         // ||N|| of the Krylov start vector
+    double hsub;         // h_{j+1,j} of the current Arnoldi step
+    double w0;           // ||A v_j|| before orthogonalisation
+    int m_used;          // Arnoldi steps taken
+    int broken;          // happy breakdown seen
+    int nonfinite;       // non-finite residual seen
+    int pad;
+};
+
+// Kernel classes of the event profiler (emg_profile_*).
+enum ProfClass {
+    PC_RES_FACE = 0, PC_RES_VOL, PC_FACE_JAC, PC_DIAG, PC_LU, PC_STAGE, PC_BSR0, PC_ARNOLDI, PC_PHI,
+    PC_COMBINE, PC_TRANSFER, PC_CONTROL, PC_SETUP, PC_COUNT
+};
+
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;     // pool
+    std::vector<int> pair_cls;       // class of pair k (events 2k, 2k+1)
+    int used = 0;                    // events used
+    double ms[PC_COUNT] = {};
+    int64_t cnt[PC_COUNT] = {};
+};
+
+}  // namespace emg
+
+struct emg_ctx {
+    emg_params prm{};
+    int dim = 0;
+    int p_max = 0;
+    int64_t E = 0, F = 0, F_int = 0, n_nodes = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    std::string err;
+    int64_t bytes = 0;
+    std::vector<void*> allocs;
+    // mesh (device)
+    int* face_L = nullptr;       // [F]
+    int* face_fL = nullptr;      // [F]
+    int* face_R = nullptr;       // [F] (-1 on boundary faces)
+    int* face_bc = nullptr;      // [F]
+    int* elem_face = nullptr;    // [E][2D]  (face id << 1) | side (0 = L, 1 = R)
+    int* elem_nbr = nullptr;     // [E][2D]  neighbour or -1
+    double* elem_x = nullptr;    // [E][2^D][D]
+    double* xc = nullptr;        // [E][3]
+    double* Lh = nullptr;        // [E][3]
+    double* vol = nullptr;       // [E]
+    double* surf = nullptr;      // [E]
+    double* h = nullptr;         // [E]
+    double* C = nullptr;         // [E][Nmax][Nmax]
+    double* psic = nullptr;      // [E][Nmax] psi_i(x_c)
+    double* gl = nullptr;        // [8][2][8] Gauss-Legendre nodes/weights, q = 1..7
+    double domain_volume = 0.0;
+    double uinf[5] = {0, 0, 0, 0, 0};
+    emg::LevelDev lv[emg::MAX_P + 1];
+    // EXP1 / Krylov
+    double* dt = nullptr;        // [E] EXP1 steps
+    double* bsr = nullptr;       // [E][1+2D][25]
+    double* V = nullptr;         // [(m+1)][K0]
+    double* w = nullptr;         // [K0]
+    double* H = nullptr;         // [(m+1)][m] row-major
+    double* hcol = nullptr;      // [m+1] current Hessenberg column
+    double* y = nullptr;         // [m]
+    double* partial = nullptr;   // [nblk][MAX_KRYLOV+2]
+    int red_blocks = 0;
+    emg::DevScalars* sc = nullptr;
+    emg::DevScalars* sc_host = nullptr;   // pinned
+    double* stage_in = nullptr;  // staging for component calls, [E][5][Nmax]
+    double* stage_in2 = nullptr;
+    double* stage_out = nullptr; // [E][B][B] max for jacobian output
+    double* stage_small = nullptr; // [E] (dt input)
+    int64_t cycle_n = 1;
+    double res_ref = 0.0;
+    emg::Prof prof;
+    int64_t launches = 0;            // kernels launched by this context
+};
+
+namespace emg {
+void prof_flush(emg_ctx* c);
+// Brackets one kernel launch with events on the context's stream when profiling is on,
+// and counts the launch.
+struct ProfScope {
+    emg_ctx* c;
+    int cls;
+    int b = -1;
+    ProfScope(emg_ctx* c_, int cls_) : c(c_), cls(cls_) {
+        c->launches++;
+        if (!c->prof.on) return;
+        if (c->prof.used + 2 > (int)c->prof.ev.size()) prof_flush(c);
+        b = c->prof.used;
+        cudaEventRecord(c->prof.ev[b], c->stream);
+        c->prof.used += 2;
+        c->prof.pair_cls[b / 2] = cls;
+    }
+    ~ProfScope() {
+        if (b >= 0) cudaEventRecord(c->prof.ev[b + 1], c->stream);
+    }
+};
+}  // namespace emg
+
+#define EMG_CUDA_TRY(ctx, call)                                                           \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);              \
+            return EMG_ERR_CUDA;                                                          \
+        }                                                                                 \
+    } while (0)
+
+#define EMG_CHECK_LAUNCH(ctx) EMG_CUDA_TRY(ctx, cudaGetLastError())
+
+// Launch helpers implemented in the .cu files (host side).
+namespace emg {
+emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m);
+emg_status launch_residual(emg_ctx* c, int p, const double* u, const double* tau, double* R);
+emg_status launch_face_jacobian(emg_ctx* c, int p, const double* u);
+emg_status launch_diag_blocks(emg_ctx* c, int p, const double* u, const double* cfl_dev, int shifted,
+                              double* out);
+emg_status launch_lu(emg_ctx* c, int p);
+emg_status launch_stage(emg_ctx* c, int p, const double* r, const double* un, double beta, double* out);
+emg_status launch_bsr0(emg_ctx* c);
+emg_status launch_exp1(emg_ctx* c, const double* u0, const double* tau0, const double* dt, double* out);
+emg_status launch_restrict(emg_ctx* c, int p_fine, const double* fine, double* coarse);
+emg_status launch_tau(emg_ctx* c, int p_coarse, const double* rfine, const double* rcoarse, double* tau);
+emg_status launch_prolong(emg_ctx* c, int p_fine, double* fine, const double* vc, const double* v0c);
+emg_status launch_norm_cfl(emg_ctx* c, const double* R, int64_t n, int update_cfl);
+emg_status launch_dtau(emg_ctx* c, int p, const double* u, const double* cfl_dev, double factor, double* dt);
+emg_status launch_axpby(emg_ctx* c, int64_t n, double a, const double* x, double b, const double* y, double* out);
+emg_status launch_check_state(emg_ctx* c, const double* u, int64_t n);
+}  // namespace emg

@@ -1,0 +1,287 @@
+// Exact Jacobian blocks (Sec. 3.3).
+//  * k_face_jac: per face point, dF~/dU_L and dF~/dU_R of the Roe flux by forward-mode
+//    AD (Dual<5>); on boundary faces the total derivative through the ghost state,
+//    dF~/dU_L + dF~/dU_ghost dU_ghost/dU_L.
+//  * k_diag_blocks: element-diagonal block of Eq. jac1,
+//      D[(a,i),(b,j)] = sum_q psi_j(x_q) sum_k W_q d_k psi_i(x_q) A_k[a][b](U_q)
+//                       - sum_{L faces} sum_t psi_i psi_j w|n dS| dF~/dU_L[a][b]
+//                       + sum_{R faces} sum_t psi_i psi_j w|n dS| dF~/dU_R[a][b]
+//    with A_k = dF_k/dU in closed form (Appendix, Eq. dfdu, omega = 0), written either as
+//    D or as the PRK operator P = I/dtau - D with dtau of Eq. x3d.
+//  * k_bsr0: the p = 0 Jacobian (Eqs. jac1, jac2) as one diagonal and 2d off-diagonal
+//    5x5 blocks per element.
+#include "common.cuh"
+#include "dispatch.cuh"
+#include "euler.cuh"
+
+namespace emg {
+
+template <int D, int P>
+__global__ void __launch_bounds__(128) k_face_jac(int F, int F_int, const int* __restrict__ fL,
+                                                  const int* __restrict__ fR, const int* __restrict__ fbc,
+                                                  const double* __restrict__ fnrm,
+                                                  const double* __restrict__ famag,
+                                                  const double* __restrict__ fpsiL,
+                                                  const double* __restrict__ fpsiR,
+                                                  const double* __restrict__ u, double g, U5 uinf,
+                                                  double* __restrict__ fjl, double* __restrict__ fjr) {
+    using L = Lv<D, P>;
+    constexpr int N = L::N, QF = L::QF;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)F * QF) return;
+    const int f = (int)(idx / QF);
+    const double n[3] = {fnrm[idx * 3], fnrm[idx * 3 + 1], fnrm[idx * 3 + 2]};
+    const double am = famag[idx];
+    double UL[5], UR[5];
+    {
+        const double* ue = u + (size_t)fL[f] * 5 * N;
+        const double* ps = fpsiL + idx * N;
+        for (int a = 0; a < 5; ++a) {
+            double s = 0.0;
+            for (int i = 0; i < N; ++i) s += ue[a * N + i] * ps[i];
+            UL[a] = s;
+        }
+    }
+    Dual<5> dL[5], dR[5], Fd[5];
+    for (int a = 0; a < 5; ++a) {
+        dL[a] = dconst<5>(UL[a]);
+        dL[a].d[a] = 1.0;
+    }
+    if (f < F_int) {
+        const double* ur = u + (size_t)fR[f] * 5 * N;
+        const double* pr = fpsiR + idx * N;
+        for (int a = 0; a < 5; ++a) {
+            double s = 0.0;
+            for (int i = 0; i < N; ++i) s += ur[a * N + i] * pr[i];
+            UR[a] = s;
+            dR[a] = dconst<5>(s);
+        }
+        roe_flux(dL, dR, n, g, Fd);
+        for (int a = 0; a < 5; ++a)
+            for (int b = 0; b < 5; ++b) fjl[idx * 25 + a * 5 + b] = am * Fd[a].d[b];
+        Dual<5> cL[5];
+        for (int a = 0; a < 5; ++a) {
+            cL[a] = dconst<5>(UL[a]);
+            dR[a].d[a] = 1.0;
+        }
+        roe_flux(cL, dR, n, g, Fd);
+        for (int a = 0; a < 5; ++a)
+            for (int b = 0; b < 5; ++b) fjr[idx * 25 + a * 5 + b] = am * Fd[a].d[b];
+    } else {
+        if (fbc[f] == EMG_BC_WALL)
+            wall_ghost(dL, n, dR);
+        else
+            farfield_ghost(dL, n, uinf.v, g, dR);
+        roe_flux(dL, dR, n, g, Fd);
+        for (int a = 0; a < 5; ++a)
+            for (int b = 0; b < 5; ++b) fjl[idx * 25 + a * 5 + b] = am * Fd[a].d[b];
+    }
+}
+
+// A_k = dF_k/dU (closed form, Appendix Eq. dfdu with grad psi -> e_k and omega = 0).
+__device__ __forceinline__ void flux_jac_k(const double U[5], double g, int k, double A[25]) {
+    const double ir = 1.0 / U[0];
+    const double v[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
+    const double q2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const double a0 = 0.5 * (g - 1.0) * q2;
+    const double p = (g - 1.0) * (U[4] - 0.5 * U[0] * q2);
+    const double H = (U[4] + p) * ir;
+    const double vk = v[k];
+#pragma unroll
+    for (int t = 0; t < 25; ++t) A[t] = 0.0;
+    A[1 + k] = 1.0;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        double* row = A + 5 * (1 + m);
+        row[0] = (m == k ? a0 : 0.0) - v[m] * vk;
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+            row[1 + l] = (l == k ? v[m] : 0.0) - (m == k ? (g - 1.0) * v[l] : 0.0) + (m == l ? vk : 0.0);
+        row[4] = m == k ? (g - 1.0) : 0.0;
+    }
+    A[20] = (a0 - H) * vk;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) A[21 + l] = (l == k ? H : 0.0) - (g - 1.0) * v[l] * vk;
+    A[24] = g * vk;
+}
+
+template <int D, int P>
+struct DiagCfg {
+    static constexpr int QC = 32;  // volume points per shared-memory chunk
+    static constexpr int THREADS = ((25 * Lv<D, P>::N + 31) / 32) * 32;
+};
+
+// One CTA per element; thread (a, b, i) accumulates row (a,i), columns (b, 0..N-1).
+template <int D, int P>
+__global__ void __launch_bounds__(DiagCfg<D, P>::THREADS) k_diag_blocks(
+    int E, int nmax, const double* __restrict__ u, const double* __restrict__ vpsi, const double* __restrict__ vgw,
+    const int* __restrict__ elem_face, const double* __restrict__ fpsiL, const double* __restrict__ fpsiR,
+    const double* __restrict__ fjl, const double* __restrict__ fjr, const double* __restrict__ psic,
+    const double* __restrict__ hlen, const double* __restrict__ cfl_dev, double g, int shifted,
+    double* __restrict__ out) {
+    using L = Lv<D, P>;
+    constexpr int N = L::N, Q = L::Q, QF = L::QF, B = L::B, NF = L::NF;
+    constexpr int QC = DiagCfg<D, P>::QC;
+    __shared__ double us[B];
+    __shared__ double As[QC][D][25];
+    __shared__ double ps[QC][N];
+    __shared__ double s_dtau;
+    const int e = blockIdx.x;
+    const int tid = threadIdx.x;
+    for (int t = tid; t < B; t += blockDim.x) us[t] = u[(size_t)e * B + t];
+    __syncthreads();
+    if (tid == 0 && shifted) {
+        double Uc[5];
+        for (int a = 0; a < 5; ++a) {
+            double s = 0.0;
+            for (int i = 0; i < N; ++i) s += us[a * N + i] * psic[(size_t)e * nmax + i];
+            Uc[a] = s;
+        }
+        const double ir = 1.0 / Uc[0];
+        const double vx = Uc[1] * ir, vy = Uc[2] * ir, vz = Uc[3] * ir;
+        const double q2 = vx * vx + vy * vy + vz * vz;
+        const double pr = (g - 1.0) * (Uc[4] - 0.5 * Uc[0] * q2);
+        const double cs = sqrt(g * pr * ir);
+        s_dtau = cfl_dev[0] * hlen[e] / ((2 * P + 1) * (sqrt(q2) + cs));
+    }
+    const bool active = tid < 25 * N;
+    const int ab = tid / N, i = tid % N;
+    const int a = ab / 5, b = ab % 5;
+    double acc[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc[j] = 0.0;
+    if (P > 0) {
+        for (int q0 = 0; q0 < Q; q0 += QC) {
+            const int nq = (Q - q0) < QC ? (Q - q0) : QC;
+            __syncthreads();
+            for (int t = tid; t < nq; t += blockDim.x) {
+                const double* pq = vpsi + ((size_t)e * Q + q0 + t) * N;
+                double U[5];
+                for (int c = 0; c < 5; ++c) {
+                    double s = 0.0;
+                    for (int m = 0; m < N; ++m) s += us[c * N + m] * pq[m];
+                    U[c] = s;
+                }
+                for (int k = 0; k < D; ++k) flux_jac_k(U, g, k, As[t][k]);
+            }
+            for (int t = tid; t < nq * N; t += blockDim.x) ps[t / N][t % N] = vpsi[((size_t)e * Q + q0) * N + t];
+            __syncthreads();
+            if (active) {
+                for (int t = 0; t < nq; ++t) {
+                    double s = 0.0;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) s += vgw[(((size_t)e * D + k) * Q + q0 + t) * N + i] * As[t][k][ab];
+#pragma unroll
+                    for (int j = 0; j < N; ++j) acc[j] += s * ps[t][j];
+                }
+            }
+        }
+    }
+    if (active) {
+#pragma unroll
+        for (int lf = 0; lf < NF; ++lf) {
+            const int code = elem_face[(size_t)e * NF + lf];
+            const int f = code >> 1;
+            const bool rside = code & 1;
+            const double* pt = rside ? fpsiR : fpsiL;
+            const double* fj = rside ? fjr : fjl;
+            const double sg = rside ? 1.0 : -1.0;
+            for (int t = 0; t < QF; ++t) {
+                const size_t pidx = (size_t)f * QF + t;
+                const double s = sg * pt[pidx * N + i] * fj[pidx * 25 + ab];
+#pragma unroll
+                for (int j = 0; j < N; ++j) acc[j] += s * pt[pidx * N + j];
+            }
+        }
+    }
+    __syncthreads();
+    if (active) {
+        double* row = out + (size_t)e * B * B + (size_t)(a * N + i) * B + b * N;
+        if (shifted) {
+            const double idt = 1.0 / s_dtau;
+#pragma unroll
+            for (int j = 0; j < N; ++j) row[j] = ((a == b && i == j) ? idt : 0.0) - acc[j];
+        } else {
+#pragma unroll
+            for (int j = 0; j < N; ++j) row[j] = acc[j];
+        }
+    }
+}
+
+// p = 0 block-sparse Jacobian: bsr[e][0] = diagonal block, bsr[e][1+lf] = dR_e/du_nb(lf).
+__global__ void k_bsr0(int E, int NF, int QF, const int* __restrict__ elem_face, const double* __restrict__ fpsiL,
+                       const double* __restrict__ fpsiR, const double* __restrict__ fjl,
+                       const double* __restrict__ fjr, int F_int, double* __restrict__ bsr) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)E * 25) return;
+    const int e = (int)(idx / 25), ab = (int)(idx % 25);
+    double diag = 0.0;
+    double* row = bsr + (size_t)e * (1 + NF) * 25;
+    for (int lf = 0; lf < NF; ++lf) {
+        const int code = elem_face[(size_t)e * NF + lf];
+        const int f = code >> 1;
+        const bool rside = code & 1;
+        double sd = 0.0, so = 0.0;
+        for (int t = 0; t < QF; ++t) {
+            const size_t pidx = (size_t)f * QF + t;
+            if (!rside) {
+                const double pl = fpsiL[pidx];
+                sd -= pl * pl * fjl[pidx * 25 + ab];
+                if (f < F_int) so -= pl * fpsiR[pidx] * fjr[pidx * 25 + ab];
+            } else {
+                const double pr = fpsiR[pidx];
+                sd += pr * pr * fjr[pidx * 25 + ab];
+                so += pr * fpsiL[pidx] * fjl[pidx * 25 + ab];
+            }
+        }
+        diag += sd;
+        row[(1 + lf) * 25 + ab] = so;
+    }
+    row[ab] = diag;
+}
+
+emg_status launch_face_jacobian(emg_ctx* c, int p, const double* u) {
+    LevelDev& L = c->lv[p];
+    const int F = (int)c->F, Fi = (int)c->F_int;
+    U5 ui;
+    for (int a = 0; a < 5; ++a) ui.v[a] = c->uinf[a];
+#define EMG_FJ(DD, PP)                                                                                       \
+    {                                                                                                        \
+        const int64_t nf = (int64_t)F * Lv<DD, PP>::QF;                                                      \
+        { ProfScope _ps(c, PC_FACE_JAC); k_face_jac<DD, PP><<<(unsigned)((nf + 127) / 128), 128, 0, c->stream>>>(                             \
+            F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL, L.fpsiR, u, c->prm.gamma, ui, \
+            L.fjl, L.fjr); }                                                                                   \
+        EMG_CHECK_LAUNCH(c);                                                                                 \
+    }
+    EMG_DISPATCH_DP(c->dim, p, EMG_FJ)
+#undef EMG_FJ
+    return EMG_OK;
+}
+
+emg_status launch_diag_blocks(emg_ctx* c, int p, const double* u, const double* cfl_dev, int shifted, double* out) {
+    emg_status st = launch_face_jacobian(c, p, u);
+    if (st != EMG_OK) return st;
+    LevelDev& L = c->lv[p];
+    const int nmax = n_modes(c->dim, c->p_max);
+#define EMG_DB(DD, PP)                                                                                          \
+    {                                                                                                           \
+        { ProfScope _ps(c, PC_DIAG); k_diag_blocks<DD, PP><<<(unsigned)c->E, DiagCfg<DD, PP>::THREADS, 0, c->stream>>>(                      \
+            (int)c->E, nmax, u, L.vpsi, L.vgw, c->elem_face, L.fpsiL, L.fpsiR, L.fjl, L.fjr, c->psic, c->h,     \
+            cfl_dev, c->prm.gamma, shifted, out); }                                                               \
+        EMG_CHECK_LAUNCH(c);                                                                                    \
+    }
+    EMG_DISPATCH_DP(c->dim, p, EMG_DB)
+#undef EMG_DB
+    return EMG_OK;
+}
+
+emg_status launch_bsr0(emg_ctx* c) {
+    LevelDev& L = c->lv[0];
+    const int64_t n = c->E * 25;
+    { ProfScope _ps(c, PC_BSR0); k_bsr0<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>((int)c->E, 2 * c->dim, L.QF, c->elem_face, L.fpsiL,
+                                                               L.fpsiR, L.fjl, L.fjr, (int)c->F_int, c->bsr); }
+    EMG_CHECK_LAUNCH(c);
+    return EMG_OK;
+}
+
+}  // namespace emg
