@@ -59,7 +59,13 @@ typedef enum {
  * node order (-1,-1),(1,-1),(1,1),(-1,1) (quads); the same at zeta=-1 then zeta=+1
  * (hexes); the map must have a positive Jacobian determinant.  face_bc: [n_elems][2*dim],
  * local face f = 2*axis + (side > 0) (xi-, xi+, eta-, eta+, zeta-, zeta+); -1 marks an
- * interior face whose neighbour is found by matching its nodes. */
+ * interior face whose neighbour is found by matching its nodes.
+ * wall_normal: optional [dim][n_nodes] unit normal of the true (curved) body at the
+ * nodes of wall faces (other entries are ignored), or NULL.  The paper's meshes are
+ * curved (Sec. 5); on straight-sided elements the slip-wall ghost state mirrors the
+ * velocity about the body normal interpolated from these node normals (normalised
+ * multilinear interpolation along the face), while fluxes are integrated on the flat
+ * faces.  NULL mirrors about the flat face normal. */
 typedef struct {
     int32_t dim;
     int64_t n_nodes;
@@ -67,6 +73,7 @@ typedef struct {
     int64_t n_elems;
     const int64_t* elem_nodes;
     const int32_t* face_bc;
+    const double* wall_normal;
 } emg_mesh_desc;
 
 typedef struct {

@@ -72,6 +72,13 @@ class DG:
         L.bnd_x = xb
         L.bnd_amag = np.linalg.norm(ab, axis=-1)
         L.bnd_n = ab / L.bnd_amag[..., None] if ab.size else ab
+        wn = m.face_wall_normals(m.bnd_L, m.bnd_f, q) if len(m.bnd_L) else None
+        # slip-wall reflection normal: the true body normal when given, else the facet's
+        if wn is None:
+            L.bnd_wn = L.bnd_n
+        else:
+            have = np.linalg.norm(wn, axis=-1, keepdims=True) > 0
+            L.bnd_wn = np.where(have, wn, L.bnd_n)
         L.bnd_psi, _ = b.evaluate(xb, m.bnd_L, n) if len(m.bnd_L) else (np.zeros((0, 1, n)), None)
         L.bnd_code = m.bnd_code
         if self.source is not None:
@@ -94,13 +101,14 @@ class DG:
         return self.evaluate_at(p, u, x, np.arange(self.E))[:, 0, :]
 
     # -- residual -------------------------------------------------------------
-    def ghost(self, UL, n, x, code):
+    def ghost(self, UL, n, x, code, wn=None):
+        """Ghost states; the slip wall mirrors the velocity about wn (body normal)."""
         G = np.empty_like(UL)
         wall = code == BC_WALL
         far = code == BC_FARFIELD
         exact = code == BC_EXACT
         if wall.any():
-            G[wall] = euler.wall_ghost(UL[wall], n[wall])
+            G[wall] = euler.wall_ghost(UL[wall], (n if wn is None else wn)[wall])
         if far.any():
             G[far] = euler.farfield_ghost(UL[far], n[far], self.Uinf, self.gamma)
         if exact.any():
@@ -124,7 +132,7 @@ class DG:
         if len(m.bnd_L):
             UL = np.einsum('fai,fqi->fqa', u[m.bnd_L], L.bnd_psi)
             code = np.broadcast_to(L.bnd_code[:, None], UL.shape[:2])
-            G = self.ghost(UL, L.bnd_n, L.bnd_x, code)
+            G = self.ghost(UL, L.bnd_n, L.bnd_x, code, L.bnd_wn)
             Fh = L.bnd_amag[..., None] * euler.roe(UL, G, L.bnd_n, self.gamma)
             np.add.at(R, m.bnd_L, -np.einsum('fqi,fqa->fai', L.bnd_psi, Fh))
         if self.source is not None:

@@ -75,6 +75,8 @@ class Mesh:
         self.nodes = np.ascontiguousarray(desc.xyz.T)          # [n_nodes][d]
         self.elems = np.asarray(desc.elem_nodes, dtype=np.int64)
         self.face_bc = np.asarray(desc.face_bc, dtype=np.int64)
+        wn = getattr(desc, "wall_normal", None)
+        self.node_wall_normal = None if wn is None else np.ascontiguousarray(np.asarray(wn).T)
         self.E = self.elems.shape[0]
         self.nf = 2 * d
         self._match_faces()
@@ -162,6 +164,26 @@ class Mesh:
             cof = np.linalg.det(J)[..., None, None] * np.swapaxes(np.linalg.inv(J), -1, -2)
             a[sel, :, :d] = side * cof[..., :, axis] * w[None, :, None]
         return x, a
+
+    def face_wall_normals(self, elem_idx, f_idx, q):
+        """Unit normal of the true wall at face points: the node normals interpolated with
+        the face's shape functions and normalised (for a circle or sphere centred at the
+        origin this is exactly the radial direction of the point).  None without normals."""
+        if self.node_wall_normal is None:
+            return None
+        d = self.dim
+        out = np.zeros((len(elem_idx), q ** (d - 1), 3))
+        for f in range(self.nf):
+            sel = np.nonzero(f_idx == f)[0]
+            if len(sel) == 0:
+                continue
+            pts, _, _, _ = face_rule(d, q, f)
+            N, _ = shape_functions(d, pts)
+            nn = self.node_wall_normal[self.elems[elem_idx[sel]]]        # [k][a][d]
+            v = np.einsum('pa,ead->epd', N, nn)
+            nv = np.linalg.norm(v, axis=-1, keepdims=True)
+            out[sel, :, :d] = np.divide(v, nv, out=np.zeros_like(v), where=nv > 0)
+        return out
 
     def _geometry(self, q):
         xi, w = volume_rule(self.dim, q)

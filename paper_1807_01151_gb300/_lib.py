@@ -18,7 +18,7 @@ STATUS = {0: "EMG_OK", 1: "EMG_ERR_ARG", 2: "EMG_ERR_OOM", 3: "EMG_ERR_CUDA", 4:
 class MeshDescC(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n_nodes", C.c_int64), ("xyz", C.POINTER(C.c_double)),
                 ("n_elems", C.c_int64), ("elem_nodes", C.POINTER(C.c_int64)),
-                ("face_bc", C.POINTER(C.c_int32))]
+                ("face_bc", C.POINTER(C.c_int32)), ("wall_normal", C.POINTER(C.c_double))]
 
 
 class ParamsC(C.Structure):
@@ -118,9 +118,12 @@ class Solver:
         self._xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
         self._en = np.ascontiguousarray(mesh.elem_nodes, dtype=np.int64)
         self._fb = np.ascontiguousarray(mesh.face_bc, dtype=np.int32)
+        wn = getattr(mesh, "wall_normal", None)
+        self._wn = None if wn is None else np.ascontiguousarray(wn, dtype=np.float64)
         d = MeshDescC(self.dim, self._xyz.shape[1], self._xyz.ctypes.data_as(C.POINTER(C.c_double)),
                       self.E, self._en.ctypes.data_as(C.POINTER(C.c_int64)),
-                      self._fb.ctypes.data_as(C.POINTER(C.c_int32)))
+                      self._fb.ctypes.data_as(C.POINTER(C.c_int32)),
+                      None if self._wn is None else self._wn.ctypes.data_as(C.POINTER(C.c_double)))
         prm = ParamsC()
         self.lib.emg_default_params(C.byref(prm))
         prm.gamma, prm.mach, prm.alpha_deg = gamma, mach, alpha_deg

@@ -48,6 +48,7 @@ struct LevelDev {
     double* famag = nullptr;   // [F][QF]        w |n dS|
     double* fpsiL = nullptr;   // [F][QF][N]     psi^L_i at the face points
     double* fpsiR = nullptr;   // [F_int][QF][N] psi^R_i at the face points
+    double* fwn = nullptr;     // [F-F_int][QF][3] slip-wall reflection normal (body normal)
     // states and work vectors, [E][5][N]
     double* v = nullptr;       // current approximation
     double* v0 = nullptr;      // restricted state (levels below p_max)
@@ -113,6 +114,8 @@ struct emg_ctx {
     int* elem_face = nullptr;    // [E][2D]  (face id << 1) | side (0 = L, 1 = R)
     int* elem_nbr = nullptr;     // [E][2D]  neighbour or -1
     double* elem_x = nullptr;    // [E][2^D][D]
+    double* elem_wn = nullptr;   // [E][2^D][D] body normals at the nodes (wall_normal input)
+    int has_wn = 0;
     double* xc = nullptr;        // [E][3]
     double* Lh = nullptr;        // [E][3]
     double* vol = nullptr;       // [E]

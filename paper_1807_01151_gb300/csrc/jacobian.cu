@@ -23,6 +23,7 @@ __global__ void __launch_bounds__(128) k_face_jac(int F, int F_int, const int* _
                                                   const double* __restrict__ famag,
                                                   const double* __restrict__ fpsiL,
                                                   const double* __restrict__ fpsiR,
+                                                  const double* __restrict__ fwn,
                                                   const double* __restrict__ u, double g, U5 uinf,
                                                   double* __restrict__ fjl, double* __restrict__ fjr) {
     using L = Lv<D, P>;
@@ -69,7 +70,11 @@ __global__ void __launch_bounds__(128) k_face_jac(int F, int F_int, const int* _
             for (int b = 0; b < 5; ++b) fjr[idx * 25 + a * 5 + b] = am * Fd[a].d[b];
     } else {
         if (fbc[f] == EMG_BC_WALL)
-            wall_ghost(dL, n, dR);
+        {
+            const int64_t bi = idx - (int64_t)F_int * QF;
+            const double nw[3] = {fwn[bi * 3], fwn[bi * 3 + 1], fwn[bi * 3 + 2]};
+            wall_ghost(dL, nw, dR);
+        }
         else
             farfield_ghost(dL, n, uinf.v, g, dR);
         roe_flux(dL, dR, n, g, Fd);
@@ -249,7 +254,7 @@ emg_status launch_face_jacobian(emg_ctx* c, int p, const double* u) {
     {                                                                                                        \
         const int64_t nf = (int64_t)F * Lv<DD, PP>::QF;                                                      \
         { ProfScope _ps(c, PC_FACE_JAC); k_face_jac<DD, PP><<<(unsigned)((nf + 127) / 128), 128, 0, c->stream>>>(                             \
-            F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL, L.fpsiR, u, c->prm.gamma, ui, \
+            F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL, L.fpsiR, L.fwn, u, c->prm.gamma, ui, \
             L.fjl, L.fjr); }                                                                                   \
         EMG_CHECK_LAUNCH(c);                                                                                 \
     }

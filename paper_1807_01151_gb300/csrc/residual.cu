@@ -18,6 +18,7 @@ __global__ void __launch_bounds__(128) k_face_flux(int F, int F_int, const int* 
                                                    const double* __restrict__ famag,
                                                    const double* __restrict__ fpsiL,
                                                    const double* __restrict__ fpsiR,
+                                                   const double* __restrict__ fwn,
                                                    const double* __restrict__ u, double g, U5 uinf,
                                                    double* __restrict__ fhat) {
     using L = Lv<D, P>;
@@ -47,7 +48,11 @@ __global__ void __launch_bounds__(128) k_face_flux(int F, int F_int, const int* 
             UR[a] = s;
         }
     } else if (fbc[f] == EMG_BC_WALL) {
-        wall_ghost(UL, n, UR);
+        {
+        const int64_t bi = idx - (int64_t)F_int * QF;
+        const double nw[3] = {fwn[bi * 3], fwn[bi * 3 + 1], fwn[bi * 3 + 2]};
+        wall_ghost(UL, nw, UR);
+    }
     } else {
         farfield_ghost(UL, n, uinf.v, g, UR);
     }
@@ -142,7 +147,7 @@ emg_status launch_residual(emg_ctx* c, int p, const double* u, const double* tau
     {                                                                                                          \
         const int64_t nf = (int64_t)F * Lv<DD, PP>::QF;                                                        \
         { ProfScope _ps(c, PC_RES_FACE); k_face_flux<DD, PP><<<(unsigned)((nf + 127) / 128), 128, 0, c->stream>>>(                              \
-            F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL, L.fpsiR, u, g, ui, L.fhat); }     \
+            F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL, L.fpsiR, L.fwn, u, g, ui, L.fhat); }     \
         EMG_CHECK_LAUNCH(c);                                                                                   \
         constexpr int ET = VolCfg<DD, PP>::ET;                                                                 \
         { ProfScope _ps(c, PC_RES_VOL); k_volume<DD, PP><<<(unsigned)((E + ET - 1) / ET), 128, 0, c->stream>>>(                                \

@@ -269,8 +269,8 @@ __global__ void k_face_tables(int F, int F_int, int n, int nmax, int q, const in
                               const int* __restrict__ ffL, const int* __restrict__ fR, const double* __restrict__ ex,
                               const double* __restrict__ gl, const double* __restrict__ xc,
                               const double* __restrict__ Lh, const int* __restrict__ exps,
-                              const double* __restrict__ C, double* fnrm, double* famag, double* fpsiL,
-                              double* fpsiR) {
+                              const double* __restrict__ C, const double* __restrict__ ewn, int has_wn,
+                              double* fnrm, double* famag, double* fpsiL, double* fpsiR, double* fwn) {
     int QF = 1;
     for (int d = 0; d < D - 1; ++d) QF *= q;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -287,6 +287,25 @@ __global__ void k_face_tables(int F, int F_int, int n, int nmax, int q, const in
     const double am = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
     famag[idx] = am;
     for (int k = 0; k < 3; ++k) fnrm[idx * 3 + k] = a[k] / am;
+    if (f >= F_int) {
+        // reflection normal of the slip wall: node body normals interpolated with the
+        // multilinear shape functions at this face point and normalised
+        double nw[3] = {a[0] / am, a[1] / am, a[2] / am};
+        if (has_wn) {
+            double v[3] = {0.0, 0.0, 0.0};
+            const double* Wn = ewn + (size_t)eL * (1 << D) * D;
+            for (int nd = 0; nd < (1 << D); ++nd) {
+                double Na = 1.0;
+                for (int d = 0; d < D; ++d) Na *= 0.5 * (1.0 + xi[d] * ref_coord(nd, d));
+                for (int d = 0; d < D; ++d) v[d] += Na * Wn[nd * D + d];
+            }
+            const double vm = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            if (vm > 0.0)
+                for (int k = 0; k < 3; ++k) nw[k] = v[k] / vm;
+        }
+        const int64_t bi = (int64_t)(f - F_int) * QF + t;
+        for (int k = 0; k < 3; ++k) fwn[bi * 3 + k] = nw[k];
+    }
     eval_basis<D, NM>(x, eL, n, nmax, xc, Lh, exps, C, psi, g);
     for (int i = 0; i < n; ++i) fpsiL[idx * n + i] = psi[i];
     if (f < F_int) {
@@ -371,7 +390,7 @@ static emg_status build_tables(emg_ctx* c, int nmax, const int* exps_d) {
         int64_t nf = c->F * L.QF;
         { ProfScope _ps(c, PC_SETUP); k_face_tables<D, NM><<<(unsigned)((nf + thr - 1) / thr), thr, 0, c->stream>>>(
             (int)c->F, (int)c->F_int, L.N, nmax, L.q, c->face_L, c->face_fL, c->face_R, c->elem_x, c->gl, c->xc,
-            c->Lh, exps_d, c->C, L.fnrm, L.famag, L.fpsiL, L.fpsiR); }
+            c->Lh, exps_d, c->C, c->elem_wn, c->has_wn, L.fnrm, L.famag, L.fpsiL, L.fpsiR, L.fwn); }
         EMG_CHECK_LAUNCH(c);
     }
     return EMG_OK;
@@ -492,6 +511,18 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
     EMG_ALLOC(c->elem_face, int, E * nf);
     EMG_ALLOC(c->elem_nbr, int, E * nf);
     EMG_ALLOC(c->elem_x, double, E * nn * D);
+    EMG_ALLOC(c->elem_wn, double, E * nn * D);
+    if (m->wall_normal) {
+        std::vector<double> hw((size_t)E * nn * D);
+        for (int64_t e = 0; e < E; ++e)
+            for (int a = 0; a < nn; ++a)
+                for (int d = 0; d < D; ++d)
+                    hw[((size_t)e * nn + a) * D + d] =
+                        m->wall_normal[(size_t)d * m->n_nodes + m->elem_nodes[e * nn + a]];
+        EMG_CUDA_TRY(c, cudaMemcpyAsync(c->elem_wn, hw.data(), hw.size() * 8, cudaMemcpyHostToDevice, c->stream));
+        EMG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        c->has_wn = 1;
+    }
     EMG_ALLOC(c->xc, double, E * 3);
     EMG_ALLOC(c->Lh, double, E * 3);
     EMG_ALLOC(c->vol, double, E);
@@ -533,6 +564,7 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
         EMG_ALLOC(L.famag, double, F * L.QF);
         EMG_ALLOC(L.fpsiL, double, F * L.QF * L.N);
         EMG_ALLOC(L.fpsiR, double, std::max<int64_t>(F_int, 1) * L.QF * L.N);
+        EMG_ALLOC(L.fwn, double, std::max<int64_t>(F - F_int, 1) * L.QF * 3);
         EMG_ALLOC(L.v, double, S);
         EMG_ALLOC(L.v0, double, S);
         EMG_ALLOC(L.tau, double, S);

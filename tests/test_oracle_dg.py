@@ -48,9 +48,24 @@ def test_residual_conservation_split():
     m = dg.mesh
     UL = np.einsum('fai,fqi->fqa', u[m.bnd_L], L.bnd_psi)
     code = np.broadcast_to(L.bnd_code[:, None], UL.shape[:2])
-    Gs = dg.ghost(UL, L.bnd_n, L.bnd_x, code)
+    Gs = dg.ghost(UL, L.bnd_n, L.bnd_x, code, L.bnd_wn)
     bflux = np.einsum('fq,fqa->a', L.bnd_amag, euler.roe(UL, Gs, L.bnd_n))
     assert np.allclose(total, -bflux, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("desc", [ogrid(7, 2), cubed_sphere_shell(2, 1)])
+def test_wall_reflection_normal_is_the_body_normal(desc):
+    """Interpolated node normals at wall face points equal the radial direction of the
+    point (circle / sphere centred at the origin), in closed form."""
+    dg = DG(desc, 2)
+    L = dg.levels[2]
+    wall = L.bnd_code == BC_WALL
+    x = L.bnd_x[wall]
+    radial = x / np.linalg.norm(x, axis=-1, keepdims=True)
+    wn = L.bnd_wn[wall][..., :dg.dim]
+    assert np.abs(np.abs(np.sum(wn * radial, axis=-1)) - 1.0).max() < 1e-14
+    # the facet normal differs from it (the walls are faceted)
+    assert np.abs(np.abs(np.sum(L.bnd_n[wall][..., :dg.dim] * radial, axis=-1)) - 1.0).max() > 1e-4
 
 
 def test_jvp_and_blocks_against_finite_differences():

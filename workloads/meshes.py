@@ -11,6 +11,11 @@ Conventions shared by every consumer (they are the interface, not the method):
                   interior face (its neighbour is found by matching nodes), otherwise a
                   boundary code below.
 
+* ``wall_normal``  optional float64 [dim][n_nodes]: unit normal of the true (curved)
+                  wall at wall nodes (other entries unused).  Straight-sided elements
+                  only approximate a curved body; the slip-wall condition reflects the
+                  velocity about this normal.
+
 The paper's meshes (896 curved hexes around a cylinder, 14026 curved tets/prisms
 around a sphere, Sec. 5) are not available; these straight-sided O-grids and
 cubed-sphere shells with geometric radial stretching stand in for them.
@@ -33,6 +38,7 @@ class MeshDesc:
     elem_nodes: np.ndarray  # [n_elems][2**dim] int64
     face_bc: np.ndarray     # [n_elems][2*dim] int32
     name: str = ""
+    wall_normal: np.ndarray = None   # [dim][n_nodes] unit normal of the true wall at wall nodes
 
     @property
     def n_elems(self):
@@ -77,7 +83,11 @@ def ogrid(n_theta, n_r, r0=0.5, r1=20.0, inner_bc=BC_WALL, outer_bc=BC_FARFIELD)
                 fb[e, 0] = inner_bc
             if l == n_r - 1:
                 fb[e, 1] = outer_bc
-    return MeshDesc(2, xyz, en, fb, name=f"ogrid{n_theta}x{n_r}")
+    # the wall is the circle r = r0: its normal at a wall node is the radial direction
+    wn = np.zeros_like(xyz)
+    wn[0, :n_theta] = np.cos(th)
+    wn[1, :n_theta] = np.sin(th)
+    return MeshDesc(2, xyz, en, fb, name=f"ogrid{n_theta}x{n_r}", wall_normal=wn)
 
 
 def box(nx, ny, x0=0.0, x1=1.0, y0=0.0, y1=1.0, bc=BC_EXACT, jitter=0.0, seed=0):
@@ -184,7 +194,9 @@ def cubed_sphere_shell(n, n_r, r0=0.5, r1=20.0, inner_bc=BC_WALL, outer_bc=BC_FA
             if l == n_r - 1:
                 fb[e, 5] = outer_bc
             e += 1
-    return MeshDesc(3, xyz, en, fb, name=f"cubedsphere6x{n}x{n}x{n_r}")
+    wn = np.zeros_like(xyz)
+    wn[:, :ns] = unit.T          # sphere r = r0: radial unit vectors at the wall nodes
+    return MeshDesc(3, xyz, en, fb, name=f"cubedsphere6x{n}x{n}x{n_r}", wall_normal=wn)
 
 
 # The synthetic stand-ins for the paper's cylinder and sphere cases.
