@@ -82,18 +82,21 @@ def test_diag_blocks(lib, name, mk, p):
 def test_prk_step(lib, name, mk, p):
     desc = mk()
     s, dg = make(lib, desc, p)
-    u = perturbed_state(dg, amp=0.05)
+    # a random state is far from any flow: keep the step moderate so that both sides stay
+    # physical (CFL 10 already drives the 5 x 3 p = 4 case to negative pressures)
+    u = perturbed_state(dg, amp=0.002)
     rng = np.random.default_rng(5)
     for lev in range(p, 0, -1):
         ul = np.ascontiguousarray(u[:, :, :dg.N(lev)])
-        tau = 1e-3 * rng.standard_normal(ul.shape) * np.sqrt(dg.mesh.vol)[:, None, None]
-        for cfl, tu in ((3.0, None), (30.0, 1e-2 * tau)):
+        tau = 1e-6 * rng.standard_normal(ul.shape) * np.sqrt(dg.mesh.vol)[:, None, None]
+        for cfl, tu in ((1.0, None), (3.0, tau)):
             ug = s.prk_step(lev, ul, tau=tu, cfl=cfl)
             D = dg.diag_blocks(lev, ul)
             dt = oemg.dtau(dg, lev, ul, cfl)
             P = np.eye(D.shape[-1])[None] / dt[:, None, None] - D
             tt = tu if tu is not None else 0.0
             uo = oemg.prk_step(lambda w: dg.residual(lev, w) + tt, P, ul)
+            assert np.isfinite(uo).all() and np.isfinite(ug).all()
             assert rel_err(ug - ul, uo - ul) < TOL_CYCLE, (lev, cfl, rel_err(ug - ul, uo - ul))
     s.close()
 
