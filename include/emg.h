@@ -85,7 +85,7 @@ typedef struct {
     int32_t krylov_m;      /* Krylov dimension of the EXP1 step (paper: 30), <= 64            */
     double cfl_max;        /* CFL_max of Eq. cfl (paper: 100 for eMG)                         */
     double exp_dt_factor;  /* EXP1 step = factor * dtau(p_max); <= 0 selects p_max + 1 (Sec. 4) */
-    int32_t pre_smooth;    /* PRK steps per level on the down leg (default 1)                 */
+    int32_t pre_smooth;    /* PRK steps per level on the down leg (default 2)                 */
     int32_t prec;          /* emg_prec                                                         */
     void* cuda_stream;     /* cudaStream_t to run on; NULL = a stream owned by the context     */
 } emg_params;
@@ -106,7 +106,7 @@ typedef struct {
 } emg_solve_report;
 
 /* Fill p with the paper's defaults (gamma 1.4, Ma 0.3, alpha 0, p_max 2, s = 4, m = 30,
- * CFL_max = 100, EXP1 factor p_max+1, 1 PRK step per level, FP64, own stream). */
+ * CFL_max = 100, EXP1 factor p_max+1, 2 PRK steps per level, FP64, own stream). */
 void emg_default_params(emg_params* p);
 
 /* Build connectivity, geometry (|E|, x_c, half bounding box L, |dE|, h = 2d|E|/|dE|,

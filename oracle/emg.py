@@ -10,7 +10,9 @@ Passages followed:
   the exponential of the augmented matrix [[H_m, e_1], [0, 0]] (scipy's expm, a
   Pade scaling-and-squaring routine, replaces the Chebyshev rational approximation).
   With per-element steps the scheme is applied to du/dtau = DT R(u), DT = diag(dt_e).
-* Sec. 2.3 steps 1-6: FAS V-cycle; restriction = truncation to the first N_{p-1}
+* Sec. 2.3 steps 1-6: FAS V-cycle with `pre_smooth` PRK steps per level p >= 1 on the
+  down leg (the paper does not fix the count; reading: 2, see Options), one EXP1 step
+  on p = 0, no post-smoothing; restriction = truncation to the first N_{p-1}
   modes of the hierarchical orthonormal basis, prolongation = zero padding,
   tau_{p-1} = restrict(R~_p(v_p)) - R_{p-1}(restrict(v_p)), R~_p = R_p + tau_p.
 * Eq. x3d: dtau = CFL h / ((2p+1)(|v|+c)) with v, c at the cell centre;
@@ -38,6 +40,7 @@ class Options:
     exp_dt_factor: float = 0.0      # <= 0 -> p_max + 1
     breakdown_rel: float = 1e-12
     res_ref: float = 0.0            # ||R(rho_1)|| of the first cycle (set by the driver)
+    pre_smooth: int = 2             # PRK steps per level on the down leg
 
 
 def prk_step(resid, P, u_n, stages=4):
@@ -167,11 +170,13 @@ def vcycle(dg, u, n, opts=None):
     for p in range(P, 0, -1):
         def resid(w, p=p):
             return dg.residual(p, w) + tau[p]
-        D = dg.diag_blocks(p, v[p])
-        dt_p = dtau(dg, p, v[p], cfl)
-        b = D.shape[-1]
-        Pm = np.eye(b)[None, :, :] / dt_p[:, None, None] - D
-        v[p] = prk_step(resid, Pm, v[p], opts.rk_stages)
+        for _ in range(opts.pre_smooth):
+            # P(u^n) is re-evaluated at the state entering every PRK step
+            D = dg.diag_blocks(p, v[p])
+            dt_p = dtau(dg, p, v[p], cfl)
+            b = D.shape[-1]
+            Pm = np.eye(b)[None, :, :] / dt_p[:, None, None] - D
+            v[p] = prk_step(resid, Pm, v[p], opts.rk_stages)
         nc = dg.N(p - 1)
         v0[p - 1] = restrict(v[p], nc)
         rbar = restrict(resid(v[p]), nc)

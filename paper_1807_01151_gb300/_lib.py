@@ -110,7 +110,7 @@ class Solver:
     """One eMG context (device-resident mesh, basis tables, state and work arrays)."""
 
     def __init__(self, mesh, p_max=2, mach=0.3, alpha_deg=0.0, gamma=1.4, rk_stages=4, krylov_m=30,
-                 cfl_max=100.0, exp_dt_factor=0.0, pre_smooth=1, prec=0, stream=None):
+                 cfl_max=100.0, exp_dt_factor=0.0, pre_smooth=2, prec=0, stream=None):
         self.lib = load()
         self.dim = int(mesh.dim)
         self.E = int(mesh.n_elems)

@@ -177,7 +177,7 @@ void emg_default_params(emg_params* p) {
     p->krylov_m = 30;
     p->cfl_max = 100.0;
     p->exp_dt_factor = 0.0;
-    p->pre_smooth = 1;
+    p->pre_smooth = 2;
     p->prec = EMG_PREC_FP64;
     p->cuda_stream = nullptr;
 }

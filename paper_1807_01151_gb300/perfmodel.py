@@ -90,7 +90,7 @@ def stage_bytes(s):
     return s.E * (s.B * s.B * 8 + 3 * s.B * 8 + s.B * 4)
 
 
-def vcycle_work(dim, p_max, E, F, rk_stages=4, pre_smooth=1, krylov_m=30):
+def vcycle_work(dim, p_max, E, F, rk_stages=4, pre_smooth=2, krylov_m=30):
     """Per-V-cycle algorithmic FLOPs and compulsory bytes of each kernel class."""
     w = {k: [0.0, 0.0] for k in ("residual_face_flux", "residual_volume", "diag_block_assembly", "block_lu",
                                  "prk_stage_solve", "arnoldi")}

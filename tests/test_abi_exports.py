@@ -44,7 +44,7 @@ def test_host_only_calls(lib):
     from paper_1807_01151_gb300 import _lib
     p = _lib.ParamsC()
     lib.emg_default_params(p)
-    assert p.gamma == 1.4 and p.krylov_m == 30 and p.rk_stages == 4 and p.cfl_max == 100.0
+    assert p.gamma == 1.4 and p.krylov_m == 30 and p.rk_stages == 4 and p.cfl_max == 100.0 and p.pre_smooth == 2
     assert b"sm_103a" in lib.emg_build_info()
     assert lib.emg_profile_class_name(0) == b"residual_face_flux"
     assert lib.emg_last_error(None) == b"null context"
