@@ -2,11 +2,12 @@
 
 A step is one FAS V-cycle p = 4 -> 0 -> 4 (every hot-path kernel: residuals, exact
 block assembly, batched LU, PRK stages, transfers, p = 0 Jacobian, Arnoldi, phi_1).
-`value` is V-cycle throughput in GDoF/s (K = 5 N_4 E degrees of freedom per cycle
-divided by the time per cycle), inputs resident in HBM.  The line also carries the
-DG residual throughput, the wall time to a 1e-10 drop of ||R(rho)||, the end-to-end
-rate through the C ABI with host buffers, the roofline of the dominant kernel and the
-CPU oracle timed on a bounded sample.
+`value` is the V-cycle throughput of the mixed form (PRK blocks in FP32; residual,
+Arnoldi and phi_1 in FP64) in GDoF/s: K = 5 N_4 E degrees of freedom per cycle over the
+time per cycle, inputs resident in HBM.  The plain FP64 form is measured beside it.  The
+line also carries the DG residual throughput, the wall time to a 1e-10 drop of ||R(rho)||
+for both forms, the end-to-end rate through the C ABI with host buffers, the roofline of
+the dominant kernel and the CPU oracle timed on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl emg|reference]
 """
@@ -18,8 +19,6 @@ import subprocess
 import sys
 import time
 
-import numpy as np
-
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -30,10 +29,9 @@ WORKLOADS = {
     "cyl64x32_p4": dict(name="cyl64x32_p4", n_theta=64, n_r=32, p_max=4, mach=0.3),
     "cyl32x16_p2": dict(name="cyl32x16_p2", n_theta=32, n_r=16, p_max=2, mach=0.3),
 }
-WORKLOAD = WORKLOADS["cyl128x64_p4"]
 METRIC = "time to 1e-10 residual drop & DG residual GDoF/s: mixed vs FP64, 1 GB300"
-FP64_PEAK_TFLOPS = 1.25     # GB300 FP64 (non-tensor) nominal; see the design doc
-FALLBACK_HBM_GBS = 6800.0
+FP64_PEAK_TFLOPS = 1.254     # FP64 FMA throughput measured on this machine's GB300
+PREC_NAMES = {0: "fp64", 1: "fp32_blocks"}
 
 
 def parse():
@@ -42,26 +40,25 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="emg", choices=["emg", "reference"])
-    ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-10 solve")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--workload", default="cyl128x64_p4", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-10 solves")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
 
 
 def dist_info():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def oracle_sample(steps, warmup):
+def oracle_sample(W, steps, warmup):
     """The oracle's V-cycle (FP64 numpy) on a bounded sample of the workload: the same
-    O-grid family and degree at 16 x 8 elements.  Returns (GDoF/s, seconds, threads)."""
+    O-grid family and degree at 16 x 8 elements.  Returns (GDoF/s, seconds, threads, E)."""
     from oracle import emg as oemg
     from oracle.dg import DG
     from workloads import ogrid
-    dg = DG(ogrid(16, 8), WORKLOAD["p_max"], mach=WORKLOAD["mach"])
+    dg = DG(ogrid(16, 8), W["p_max"], mach=W["mach"])
     u = dg.freestream_state()
     opts = oemg.Options()
     n = 1
@@ -73,7 +70,7 @@ def oracle_sample(steps, warmup):
         u, _ = oemg.vcycle(dg, u, n, opts)
         n += 1
     el = time.perf_counter() - t
-    K = 5 * dg.N(WORKLOAD["p_max"]) * dg.E
+    K = 5 * dg.N(W["p_max"]) * dg.E
     try:
         from threadpoolctl import threadpool_info
         threads = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
@@ -93,7 +90,7 @@ class Clocks:
         try:
             self.f = open(path, "w")
             self.p = subprocess.Popen(["nvidia-smi", f"--id={idx}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
 
@@ -139,48 +136,28 @@ def measured_peaks():
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    v, el, threads, E = oracle_sample(args.steps, args.warmup)
+    W = WORKLOADS[args.workload]
+    v, el, threads, E = oracle_sample(W, args.steps, args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "GDoF/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD["name"], "sample": f"oracle V-cycles on the 16x8 O-grid at p=4 ({E} elements)"},
+        "config": {"workload": W["name"], "sample": f"oracle V-cycles on the 16x8 O-grid at p={W['p_max']} ({E} elements)"},
         "cpu_baseline": {"value": v, "unit": "GDoF/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{args.steps} oracle V-cycles, 16x8 O-grid, p=4"},
+                         "sample": f"{args.steps} oracle V-cycles, 16x8 O-grid, p={W['p_max']}"},
         "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def main():
-    global WORKLOAD
-    args = parse()
-    WORKLOAD = WORKLOADS[args.workload]
-    rank, world, local = dist_info()
-    if args.impl == "reference":
-        return run_reference(args, rank, world)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        v, el, threads, E = oracle_sample(2, 0)   # before any GPU work (no fork after CUDA init)
-        cpu = {"value": v, "unit": "GDoF/s", "cores": threads, "kind": "oracle",
-               "sample": f"2 oracle V-cycles of the 16x8 O-grid at p=4 ({E} elements), {el:.1f} s"}
-    import torch
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    import paper_1807_01151_gb300 as emg_pkg
+def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks):
+    """Time K V-cycles of one form; return a dict of results (and the solver closed)."""
     from paper_1807_01151_gb300 import perfmodel
-    from workloads import ogrid
-    W = WORKLOAD
-    mesh = ogrid(W["n_theta"], W["n_r"])
     stream = torch.cuda.Stream()
-    s = emg_pkg.Solver(mesh, p_max=W["p_max"], mach=W["mach"], stream=stream.cuda_stream)
-    E = s.E
-    N = s.n_modes(W["p_max"])
+    s = pkg.Solver(mesh, p_max=W["p_max"], mach=W["mach"], prec=prec, stream=stream.cuda_stream)
+    E, N = s.E, s.n_modes(W["p_max"])
     K = 5 * N * E
     F = (4 * E + 2 * W["n_theta"]) // 2
-    # warm-up: free stream and W V-cycles (the timed state is a developing flow)
     s.set_state(None)
     for _ in range(args.warmup):
         s.vcycle(info=False)
@@ -191,8 +168,8 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    clocks = Clocks(local, os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                                        f"clocks_rank{rank}.csv"))
+    outdir = os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ROOT
+    clocks = Clocks(local, os.path.join(outdir, f"clocks_rank{rank}_{PREC_NAMES[prec]}.csv")) if with_clocks else None
     s.profile(True)
     l0 = s.launch_count
     barrier()
@@ -207,12 +184,13 @@ def main():
     launches = s.launch_count - l0
     prof = s.profile_read()
     s.profile(False)
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * K * args.steps / (ms * 1e-3) / 1e9
+    out = {"value": world * K * args.steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / args.steps,
+           "gpu_launches": launches, "clocks": clk, "K": K, "E": E}
     # residual throughput (p_max residual, device buffers, back-to-back)
     u = torch.empty((E, 5, N), dtype=torch.float64, device="cuda")
     R = torch.empty_like(u)
@@ -229,6 +207,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     res_ms = e0.elapsed_time(e1) / nres
+    out["residual_gdofs"] = K / (res_ms * 1e-3) / 1e9
+    out["residual_ms"] = res_ms
     # end to end through the C ABI with host buffers: H2D state, V-cycle, D2H state + info
     host = torch.empty((E, 5, N), dtype=torch.float64, pin_memory=True).numpy()
     s.get_state(host)
@@ -239,51 +219,78 @@ def main():
         s.vcycle(info=True)
         s.get_state(host)
     e2e_s = time.perf_counter() - t0
-    e2e = world * K * args.steps / e2e_s / 1e9
+    out["e2e"] = {"value": world * K * args.steps / e2e_s / 1e9, "unit": "GDoF/s",
+                  "h2d_bytes_per_step": K * 8, "d2h_bytes_per_step": K * 8 + 64}
     # time to a 1e-10 drop from the free stream
-    solve = None
     if not args.no_solve:
         s.set_state(None)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         rep = s.solve_steady(drop=1e-10, max_cycles=5000, raise_on_fail=False)
-        solve = {"seconds": time.perf_counter() - t0, "cycles": rep["cycles"], "converged": rep["converged"],
-                 "drop": rep["res_final"] / rep["res0"] if rep["res0"] else None}
-    # roofline of the dominant kernel class over the timed region
+        out["time_to_1e-10"] = {"seconds": time.perf_counter() - t0, "cycles": rep["cycles"],
+                                "converged": rep["converged"],
+                                "drop": rep["res_final"] / rep["res0"] if rep["res0"] else None}
+    # per-class kernel times over the timed region and the roofline of the dominant class
     work = perfmodel.vcycle_work(2, W["p_max"], E, F)
-    top = max((k for k in prof if k in work), key=lambda k: prof[k][0])
-    t_top = prof[top][0] * 1e-3 / args.steps          # seconds per V-cycle
-    flops_top = work[top][0]
-    peaks, src = measured_peaks()
-    achieved = flops_top / t_top / 1e12
-    roofline = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "GB300 FP64 nominal (no FP64 entry in the measured peaks)",
-                "algorithmic_flops_per_cycle": flops_top, "ms_per_cycle": t_top * 1e3,
-                "launches": prof[top][1]}
-    kernels = {k: {"ms_per_cycle": v[0] / args.steps, "launches_per_cycle": v[1] / args.steps}
-               for k, v in prof.items() if v[1]}
+    out["kernels"] = {k: {"ms_per_cycle": v[0] / args.steps, "launches_per_cycle": v[1] / args.steps}
+                      for k, v in prof.items() if v[1]}
+    fp64_classes = [k for k in prof if k in work and not (prec == 1 and k in ("diag_block_assembly", "block_lu",
+                                                                             "prk_stage_solve"))]
+    top = max(fp64_classes, key=lambda k: prof[k][0])
+    t_top = prof[top][0] * 1e-3 / args.steps
+    achieved = work[top][0] / t_top / 1e12
+    out["roofline"] = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                       "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                       "peak_source": "FP64 FMA throughput measured on GB300 (1.254 TFLOP/s), DESIGN.md",
+                       "algorithmic_flops_per_cycle": work[top][0], "ms_per_cycle": t_top * 1e3,
+                       "launches_per_cycle": prof[top][1] / args.steps}
+    s.close()
+    return out
+
+
+def main():
+    args = parse()
+    W = WORKLOADS[args.workload]
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, el, threads, E = oracle_sample(W, 2, 0)   # before any GPU work (no fork after CUDA init)
+        cpu = {"value": v, "unit": "GDoF/s", "cores": threads, "kind": "oracle",
+               "sample": f"2 oracle V-cycles of the 16x8 O-grid at p={W['p_max']} ({E} elements), {el:.1f} s"}
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1807_01151_gb300 as pkg
+    from workloads import ogrid
+    mesh = ogrid(W["n_theta"], W["n_r"])
+    precs = {"both": [1, 0], "mixed": [1], "fp64": [0]}[args.prec]
+    res = {p: measure(pkg, torch, mesh, W, p, args, world, local, rank, with_clocks=(i == 0))
+           for i, p in enumerate(precs)}
+    head = res[precs[0]]
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "metric": METRIC, "value": head["value"], "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32" if precs[0] == 1 else "f64", "data": "synthetic",
             "config": {"workload": W["name"], "mesh": f"O-grid {W['n_theta']}x{W['n_r']} r in [0.5,20]",
-                       "p_max": W["p_max"], "elements": E, "dof": K, "mach": W["mach"],
-                       "l2": "working set per V-cycle > L2 (block factors 369 MB + tables)",
+                       "p_max": W["p_max"], "elements": head["E"], "dof": head["K"], "mach": W["mach"],
+                       "form": PREC_NAMES[precs[0]],
+                       "l2": "inputs larger than L2: tables and block factors stream > 1 GB per V-cycle",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "residual_gdofs": K / (res_ms * 1e-3) / 1e9, "residual_ms": res_ms,
-            "time_to_1e-10": solve,
-            "e2e": {"value": e2e, "unit": "GDoF/s", "h2d_bytes_per_step": K * 8, "d2h_bytes_per_step": K * 8 + 64},
-            "gpu_launches": launches,
-            "roofline": roofline,
-            "kernels": kernels,
-            "clocks": clk,
-            "cpu_baseline": cpu,
-            "peaks_source": src,
+            "residual_gdofs": head["residual_gdofs"], "residual_ms": head["residual_ms"],
+            "time_to_1e-10": head.get("time_to_1e-10"),
+            "e2e": head["e2e"], "gpu_launches": head["gpu_launches"], "roofline": head["roofline"],
+            "clocks": head["clocks"], "cpu_baseline": cpu, "kernels": head["kernels"],
         }
+        for p in precs[1:]:
+            r = res[p]
+            line[PREC_NAMES[p]] = {k: r[k] for k in ("value", "ms_per_step", "residual_gdofs", "time_to_1e-10",
+                                                     "gpu_launches", "roofline", "kernels") if k in r}
         print(json.dumps(line), flush=True)
-    s.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -185,6 +185,14 @@ const char* emg_profile_class_name(int32_t cls);
 /* Number of kernels the context has launched since creation. */
 int64_t emg_launch_count(const emg_ctx* ctx);
 
+/* ---- failure detection (no counterpart in the paper) ----
+ * Every device-side wait (the grid barriers of the persistent Arnoldi kernel) gives up
+ * after a bounded number of clock cycles, records the timeout and returns, and the call
+ * reports EMG_ERR_TIMEOUT with the context still usable.  This self-test launches one
+ * block at a barrier that expects two, so the wait runs out (~0.1 s); it returns
+ * EMG_ERR_TIMEOUT when the bounded wait works and clears the flag afterwards. */
+emg_status emg_selftest_wait_timeout(emg_ctx* ctx);
+
 /* Build identification string (architecture and kernel variants). */
 const char* emg_build_info(void);
 

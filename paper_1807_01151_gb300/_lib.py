@@ -63,6 +63,7 @@ EXPORTS = {
     "emg_profile_read": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "emg_profile_class_name": (C.c_char_p, [C.c_int32]),
     "emg_launch_count": (C.c_int64, [C.c_void_p]),
+    "emg_selftest_wait_timeout": (C.c_int, [C.c_void_p]),
     "emg_build_info": (C.c_char_p, []),
 }
 

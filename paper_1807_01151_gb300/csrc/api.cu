@@ -63,9 +63,11 @@ static emg_status prk_step(emg_ctx* c, int p, const double* tau, const double* r
     LevelDev& L = c->lv[p];
     const int64_t S = c->E * L.B;
     EMG_CUDA_TRY(c, cudaMemcpyAsync(L.un, L.v, S * 8, cudaMemcpyDeviceToDevice, c->stream));
-    emg_status st = launch_diag_blocks(c, p, L.un, &c->sc->cfl, 1, L.blk);
+    const bool f32 = c->prm.prec == EMG_PREC_FP32_BLOCKS;
+    emg_status st = f32 ? launch_diag_blocks32(c, p, L.un, &c->sc->cfl, 1, L.blk32)
+                        : launch_diag_blocks(c, p, L.un, &c->sc->cfl, 1, L.blk);
     if (st != EMG_OK) return st;
-    st = launch_lu(c, p);
+    st = f32 ? launch_lu32(c, p) : launch_lu(c, p);
     if (st != EMG_OK) return st;
     const int s = c->prm.rk_stages;
     for (int k = 1; k <= s; ++k) {
@@ -78,7 +80,7 @@ static emg_status prk_step(emg_ctx* c, int p, const double* tau, const double* r
             if (st != EMG_OK) return st;
             r = L.r;
         }
-        st = launch_stage(c, p, r, L.un, beta, L.v);
+        st = f32 ? launch_stage32(c, p, r, L.un, beta, L.v) : launch_stage(c, p, r, L.un, beta, L.v);
         if (st != EMG_OK) return st;
     }
     return EMG_OK;
@@ -157,6 +159,7 @@ void prof_flush(emg_ctx* c) {
 }
 
 static emg_status check_flags(emg_ctx* c) {
+    if (c->sc_host->timeout) return fail(c, EMG_ERR_TIMEOUT, "a grid barrier wait in the Arnoldi kernel timed out");
     if (c->sc_host->nonfinite) return fail(c, EMG_ERR_NONFINITE, "non-finite residual or Krylov quantity");
     if (c->sc_host->pad) return fail(c, EMG_ERR_UNPHYSICAL, "non-positive density or pressure at a cell centre");
     return EMG_OK;
@@ -205,7 +208,8 @@ emg_status emg_create_mesh(const emg_mesh_desc* m, const emg_params* prm, emg_ct
     if (!(prm->cfl_max > 0.0)) return fail(c, EMG_ERR_ARG, "cfl_max must be positive");
     if (prm->pre_smooth < 1) return fail(c, EMG_ERR_ARG, "pre_smooth must be >= 1");
     if (!(prm->gamma > 1.0) || !(prm->mach >= 0.0)) return fail(c, EMG_ERR_ARG, "bad gamma or mach");
-    if (prm->prec != EMG_PREC_FP64) return fail(c, EMG_ERR_ARG, "only EMG_PREC_FP64 is built");
+    if (prm->prec != EMG_PREC_FP64 && prm->prec != EMG_PREC_FP32_BLOCKS)
+        return fail(c, EMG_ERR_ARG, "prec must be EMG_PREC_FP64 or EMG_PREC_FP32_BLOCKS");
     c->p_max = prm->p_max;
     EMG_CUDA_TRY(c, cudaGetDevice(&c->device));
     if (prm->cuda_stream) {
@@ -471,7 +475,7 @@ emg_status emg_exp1_step(emg_ctx* c, const double* u0, const double* tau0, const
     st = read_scalars(c);
     if (st != EMG_OK) return st;
     if (krylov_dim) *krylov_dim = c->sc_host->m_used;
-    return c->sc_host->nonfinite ? fail(c, EMG_ERR_NONFINITE, "non-finite Krylov quantity") : EMG_OK;
+    return check_flags(c);
 }
 
 static const char* kClassNames[PC_COUNT] = {"residual_face_flux", "residual_volume", "face_jacobian",
@@ -508,6 +512,15 @@ const char* emg_profile_class_name(int32_t cls) {
 }
 
 int64_t emg_launch_count(const emg_ctx* c) { return c ? c->launches : 0; }
+
+emg_status emg_selftest_wait_timeout(emg_ctx* c) {
+    if (!c) return EMG_ERR_ARG;
+    int flag = 0;
+    emg_status st = selftest_barrier_timeout(c, &flag);
+    if (st != EMG_OK) return st;
+    if (!flag) return fail(c, EMG_ERR_CUDA, "bounded wait did not report its timeout");
+    return fail(c, EMG_ERR_TIMEOUT, "bounded wait gave up as designed");
+}
 
 emg_status emg_element_geometry(emg_ctx* c, double* vol, double* h) {
     if (!c) return EMG_ERR_ARG;

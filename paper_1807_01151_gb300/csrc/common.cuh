@@ -61,6 +61,12 @@ struct LevelDev {
     double* fjr = nullptr;     // [F_int][QF][25] w|n dS| dF~/dU_R
     double* blk = nullptr;     // [E][B][B]      P_e, then its LU factors (column-major)
     int* piv = nullptr;        // [E][B]
+    // FP32 block path (EMG_PREC_FP32_BLOCKS): float copies of the tables and blocks
+    float* vpsi32 = nullptr;
+    float* vgw32 = nullptr;
+    float* fpsiL32 = nullptr;
+    float* fpsiR32 = nullptr;
+    float* blk32 = nullptr;    // [E][B][B]
 };
 
 // Small device-side scalars of the cycle (no host round trip inside a V-cycle).
@@ -75,7 +81,8 @@ struct DevScalars {
     int m_used;          // Arnoldi steps taken
     int broken;          // happy breakdown seen
     int nonfinite;       // non-finite residual seen
-    int pad;
+    int pad;             // non-positive density or pressure seen
+    int timeout;         // a bounded device-side wait gave up
 };
 
 // Kernel classes of the event profiler (emg_profile_*).
@@ -135,7 +142,8 @@ struct emg_ctx {
     double* H = nullptr;         // [(m+1)][m] row-major
     double* hcol = nullptr;      // [m+1] current Hessenberg column
     double* y = nullptr;         // [m]
-    double* partial = nullptr;   // [nblk][MAX_KRYLOV+2]
+    double* partial = nullptr;   // 3 x [red_blocks][MAX_KRYLOV+8] reduction partials
+    unsigned int* bar = nullptr; // grid barrier state of the persistent Arnoldi kernel
     int red_blocks = 0;
     emg::DevScalars* sc = nullptr;
     emg::DevScalars* sc_host = nullptr;   // pinned
@@ -192,6 +200,11 @@ emg_status launch_diag_blocks(emg_ctx* c, int p, const double* u, const double* 
                               double* out);
 emg_status launch_lu(emg_ctx* c, int p);
 emg_status launch_stage(emg_ctx* c, int p, const double* r, const double* un, double beta, double* out);
+emg_status launch_diag_blocks32(emg_ctx* c, int p, const double* u, const double* cfl_dev, int shifted, float* out);
+emg_status launch_lu32(emg_ctx* c, int p);
+emg_status launch_stage32(emg_ctx* c, int p, const double* r, const double* un, double beta, double* out);
+emg_status build_float_tables(emg_ctx* c);
+emg_status selftest_barrier_timeout(emg_ctx* c, int* timed_out);
 emg_status launch_bsr0(emg_ctx* c);
 emg_status launch_exp1(emg_ctx* c, const double* u0, const double* tau0, const double* dt, double* out);
 emg_status launch_restrict(emg_ctx* c, int p_fine, const double* fine, double* coarse);

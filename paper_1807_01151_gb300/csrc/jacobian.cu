@@ -10,6 +10,8 @@
 //    D or as the PRK operator P = I/dtau - D with dtau of Eq. x3d.
 //  * k_bsr0: the p = 0 Jacobian (Eqs. jac1, jac2) as one diagonal and 2d off-diagonal
 //    5x5 blocks per element.
+#include <algorithm>
+
 #include "common.cuh"
 #include "dispatch.cuh"
 #include "euler.cuh"
@@ -110,6 +112,33 @@ __device__ __forceinline__ void flux_jac_k(const double U[5], double g, int k, d
     A[24] = g * vk;
 }
 
+// The same closed form in float for the FP32 block path.
+__device__ __forceinline__ void flux_jac_k(const float U[5], float g, int k, float A[25]) {
+    const float ir = 1.0f / U[0];
+    const float v[3] = {U[1] * ir, U[2] * ir, U[3] * ir};
+    const float q2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const float a0 = 0.5f * (g - 1.0f) * q2;
+    const float p = (g - 1.0f) * (U[4] - 0.5f * U[0] * q2);
+    const float H = (U[4] + p) * ir;
+    const float vk = v[k];
+#pragma unroll
+    for (int t = 0; t < 25; ++t) A[t] = 0.0f;
+    A[1 + k] = 1.0f;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        float* row = A + 5 * (1 + m);
+        row[0] = (m == k ? a0 : 0.0f) - v[m] * vk;
+#pragma unroll
+        for (int l = 0; l < 3; ++l)
+            row[1 + l] = (l == k ? v[m] : 0.0f) - (m == k ? (g - 1.0f) * v[l] : 0.0f) + (m == l ? vk : 0.0f);
+        row[4] = m == k ? (g - 1.0f) : 0.0f;
+    }
+    A[20] = (a0 - H) * vk;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) A[21 + l] = (l == k ? H : 0.0f) - (g - 1.0f) * v[l] * vk;
+    A[24] = g * vk;
+}
+
 template <int D, int P>
 struct DiagCfg {
     static constexpr int QC = 32;  // volume points per shared-memory chunk
@@ -117,29 +146,36 @@ struct DiagCfg {
 };
 
 // One CTA per element; thread (a, b, i) accumulates row (a,i), columns (b, 0..N-1).
-template <int D, int P>
+// T is the block precision: double (FP64 form) or float (FP32 block form, with float
+// copies of the basis tables; state and face Jacobians are rounded to float on load).
+template <int D, int P, class T>
 __global__ void __launch_bounds__(DiagCfg<D, P>::THREADS) k_diag_blocks(
-    int E, int nmax, const double* __restrict__ u, const double* __restrict__ vpsi, const double* __restrict__ vgw,
-    const int* __restrict__ elem_face, const double* __restrict__ fpsiL, const double* __restrict__ fpsiR,
+    int E, int nmax, const double* __restrict__ u, const T* __restrict__ vpsi, const T* __restrict__ vgw,
+    const int* __restrict__ elem_face, const T* __restrict__ fpsiL, const T* __restrict__ fpsiR,
     const double* __restrict__ fjl, const double* __restrict__ fjr, const double* __restrict__ psic,
     const double* __restrict__ hlen, const double* __restrict__ cfl_dev, double g, int shifted,
-    double* __restrict__ out) {
+    T* __restrict__ out) {
     using L = Lv<D, P>;
     constexpr int N = L::N, Q = L::Q, QF = L::QF, B = L::B, NF = L::NF;
     constexpr int QC = DiagCfg<D, P>::QC;
-    __shared__ double us[B];
-    __shared__ double As[QC][D][25];
-    __shared__ double ps[QC][N];
+    __shared__ double ud[B];
+    __shared__ T us[B];
+    __shared__ T As[QC][D][25];
+    __shared__ T ps[QC][N];
     __shared__ double s_dtau;
     const int e = blockIdx.x;
     const int tid = threadIdx.x;
-    for (int t = tid; t < B; t += blockDim.x) us[t] = u[(size_t)e * B + t];
+    for (int t = tid; t < B; t += blockDim.x) {
+        const double v = u[(size_t)e * B + t];
+        ud[t] = v;
+        us[t] = (T)v;
+    }
     __syncthreads();
     if (tid == 0 && shifted) {
         double Uc[5];
         for (int a = 0; a < 5; ++a) {
             double s = 0.0;
-            for (int i = 0; i < N; ++i) s += us[a * N + i] * psic[(size_t)e * nmax + i];
+            for (int i = 0; i < N; ++i) s += ud[a * N + i] * psic[(size_t)e * nmax + i];
             Uc[a] = s;
         }
         const double ir = 1.0 / Uc[0];
@@ -152,28 +188,28 @@ __global__ void __launch_bounds__(DiagCfg<D, P>::THREADS) k_diag_blocks(
     const bool active = tid < 25 * N;
     const int ab = tid / N, i = tid % N;
     const int a = ab / 5, b = ab % 5;
-    double acc[N];
+    T acc[N];
 #pragma unroll
-    for (int j = 0; j < N; ++j) acc[j] = 0.0;
+    for (int j = 0; j < N; ++j) acc[j] = (T)0;
     if (P > 0) {
         for (int q0 = 0; q0 < Q; q0 += QC) {
             const int nq = (Q - q0) < QC ? (Q - q0) : QC;
             __syncthreads();
             for (int t = tid; t < nq; t += blockDim.x) {
-                const double* pq = vpsi + ((size_t)e * Q + q0 + t) * N;
-                double U[5];
+                const T* pq = vpsi + ((size_t)e * Q + q0 + t) * N;
+                T U[5];
                 for (int c = 0; c < 5; ++c) {
-                    double s = 0.0;
+                    T s = (T)0;
                     for (int m = 0; m < N; ++m) s += us[c * N + m] * pq[m];
                     U[c] = s;
                 }
-                for (int k = 0; k < D; ++k) flux_jac_k(U, g, k, As[t][k]);
+                for (int k = 0; k < D; ++k) flux_jac_k(U, (T)g, k, As[t][k]);
             }
             for (int t = tid; t < nq * N; t += blockDim.x) ps[t / N][t % N] = vpsi[((size_t)e * Q + q0) * N + t];
             __syncthreads();
             if (active) {
                 for (int t = 0; t < nq; ++t) {
-                    double s = 0.0;
+                    T s = (T)0;
 #pragma unroll
                     for (int k = 0; k < D; ++k) s += vgw[(((size_t)e * D + k) * Q + q0 + t) * N + i] * As[t][k][ab];
 #pragma unroll
@@ -188,12 +224,12 @@ __global__ void __launch_bounds__(DiagCfg<D, P>::THREADS) k_diag_blocks(
             const int code = elem_face[(size_t)e * NF + lf];
             const int f = code >> 1;
             const bool rside = code & 1;
-            const double* pt = rside ? fpsiR : fpsiL;
+            const T* pt = rside ? fpsiR : fpsiL;
             const double* fj = rside ? fjr : fjl;
-            const double sg = rside ? 1.0 : -1.0;
+            const T sg = rside ? (T)1 : (T)-1;
             for (int t = 0; t < QF; ++t) {
                 const size_t pidx = (size_t)f * QF + t;
-                const double s = sg * pt[pidx * N + i] * fj[pidx * 25 + ab];
+                const T s = sg * pt[pidx * N + i] * (T)fj[pidx * 25 + ab];
 #pragma unroll
                 for (int j = 0; j < N; ++j) acc[j] += s * pt[pidx * N + j];
             }
@@ -201,16 +237,22 @@ __global__ void __launch_bounds__(DiagCfg<D, P>::THREADS) k_diag_blocks(
     }
     __syncthreads();
     if (active) {
-        double* row = out + (size_t)e * B * B + (size_t)(a * N + i) * B + b * N;
+        T* row = out + (size_t)e * B * B + (size_t)(a * N + i) * B + b * N;
         if (shifted) {
-            const double idt = 1.0 / s_dtau;
+            const T idt = (T)(1.0 / s_dtau);
 #pragma unroll
-            for (int j = 0; j < N; ++j) row[j] = ((a == b && i == j) ? idt : 0.0) - acc[j];
+            for (int j = 0; j < N; ++j) row[j] = ((a == b && i == j) ? idt : (T)0) - acc[j];
         } else {
 #pragma unroll
             for (int j = 0; j < N; ++j) row[j] = acc[j];
         }
     }
+}
+
+// Float copies of the level tables used by the FP32 block path.
+__global__ void k_to_float(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (float)x[i];
 }
 
 // p = 0 block-sparse Jacobian: bsr[e][0] = diagonal block, bsr[e][1+lf] = dR_e/du_nb(lf).
@@ -268,15 +310,56 @@ emg_status launch_diag_blocks(emg_ctx* c, int p, const double* u, const double* 
     if (st != EMG_OK) return st;
     LevelDev& L = c->lv[p];
     const int nmax = n_modes(c->dim, c->p_max);
-#define EMG_DB(DD, PP)                                                                                          \
-    {                                                                                                           \
-        { ProfScope _ps(c, PC_DIAG); k_diag_blocks<DD, PP><<<(unsigned)c->E, DiagCfg<DD, PP>::THREADS, 0, c->stream>>>(                      \
-            (int)c->E, nmax, u, L.vpsi, L.vgw, c->elem_face, L.fpsiL, L.fpsiR, L.fjl, L.fjr, c->psic, c->h,     \
-            cfl_dev, c->prm.gamma, shifted, out); }                                                               \
-        EMG_CHECK_LAUNCH(c);                                                                                    \
+#define EMG_DB(DD, PP)                                                                                      \
+    {                                                                                                       \
+        ProfScope _ps(c, PC_DIAG);                                                                          \
+        k_diag_blocks<DD, PP, double><<<(unsigned)c->E, DiagCfg<DD, PP>::THREADS, 0, c->stream>>>(          \
+            (int)c->E, nmax, u, L.vpsi, L.vgw, c->elem_face, L.fpsiL, L.fpsiR, L.fjl, L.fjr, c->psic, c->h, \
+            cfl_dev, c->prm.gamma, shifted, out);                                                           \
     }
     EMG_DISPATCH_DP(c->dim, p, EMG_DB)
 #undef EMG_DB
+    EMG_CHECK_LAUNCH(c);
+    return EMG_OK;
+}
+
+emg_status launch_diag_blocks32(emg_ctx* c, int p, const double* u, const double* cfl_dev, int shifted,
+                                float* out) {
+    emg_status st = launch_face_jacobian(c, p, u);
+    if (st != EMG_OK) return st;
+    LevelDev& L = c->lv[p];
+    if (!L.vpsi32) {
+        c->err = "FP32 tables not built";
+        return EMG_ERR_ARG;
+    }
+    const int nmax = n_modes(c->dim, c->p_max);
+#define EMG_DB32(DD, PP)                                                                                    \
+    {                                                                                                       \
+        ProfScope _ps(c, PC_DIAG);                                                                          \
+        k_diag_blocks<DD, PP, float><<<(unsigned)c->E, DiagCfg<DD, PP>::THREADS, 0, c->stream>>>(           \
+            (int)c->E, nmax, u, L.vpsi32, L.vgw32, c->elem_face, L.fpsiL32, L.fpsiR32, L.fjl, L.fjr, c->psic, \
+            c->h, cfl_dev, c->prm.gamma, shifted, out);                                                     \
+    }
+    EMG_DISPATCH_DP(c->dim, p, EMG_DB32)
+#undef EMG_DB32
+    EMG_CHECK_LAUNCH(c);
+    return EMG_OK;
+}
+
+emg_status build_float_tables(emg_ctx* c) {
+    for (int p = 1; p <= c->p_max; ++p) {
+        LevelDev& L = c->lv[p];
+        const int64_t n1 = c->E * L.Q * L.N, n2 = c->E * c->dim * L.Q * L.N;
+        const int64_t n3 = c->F * L.QF * L.N, n4 = std::max<int64_t>(c->F_int, 1) * L.QF * L.N;
+        const double* src[4] = {L.vpsi, L.vgw, L.fpsiL, L.fpsiR};
+        float* dst[4] = {L.vpsi32, L.vgw32, L.fpsiL32, L.fpsiR32};
+        const int64_t cnt[4] = {n1, n2, n3, n4};
+        for (int k = 0; k < 4; ++k) {
+            ProfScope _ps(c, PC_SETUP);
+            k_to_float<<<(unsigned)((cnt[k] + 255) / 256), 256, 0, c->stream>>>(cnt[k], src[k], dst[k]);
+        }
+        EMG_CHECK_LAUNCH(c);
+    }
     return EMG_OK;
 }
 

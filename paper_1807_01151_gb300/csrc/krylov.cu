@@ -7,163 +7,240 @@
 // exp([[H_k, e_1], [0, 0]]), computed in one CTA by [13/13] Pade scaling-and-squaring
 // (Higham, SIAM J. Matrix Anal. Appl. 26 (2005) 1179).  The device decides happy
 // breakdown itself, so the loop needs no host round trip.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
 
 namespace emg {
 
-constexpr int RED_THREADS = 256;
+// ---- persistent Arnoldi: one cooperative launch for the whole Krylov loop ------------------
+// Grid barrier on a counter/generation pair in global memory.  Waits are bounded: after
+// `budget` clock cycles the block records a timeout in sc->timeout and the kernel returns
+// (the host maps it to EMG_ERR_TIMEOUT); nothing spins forever.
+struct GridBar {
+    unsigned int count;
+    unsigned int gen;
+};
 
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+__device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned nblocks, long long budget, DevScalars* sc,
+                                          int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* vgen = &bar->gen;
+        const unsigned int g = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&bar->count, 1u) + 1u;
+        int ok = 1;
+        if (arrived == nblocks) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == g) {
+                if (clock64() - t0 > budget) {
+                    atomicExch(&sc->timeout, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *s_ok = ok && !*((volatile int*)&sc->timeout);
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+constexpr int ARN_THREADS = 256;
+constexpr int ARN_CHUNK = 8;  // vectors per dot-product sweep
+
+// Block-reduce v[0..n) (n <= ARN_CHUNK) and store into dst[0..n) from thread 0 (fixed order).
+__device__ __forceinline__ void block_reduce_store(double v[ARN_CHUNK], int n, double* dst,
+                                                   double (*sh)[ARN_CHUNK]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-    return s;  // valid in thread 0
-}
-
-// Reduce partial[0..nb-1][col] in a fixed order; result valid in thread 0... broadcast via shared.
-__device__ __forceinline__ double reduce_partials(const double* partial, int nb, int stride, int col, double* sh) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partial[(size_t)b * stride + col];
-    double s = block_sum(v, sh);
-    __syncthreads();
-    if (threadIdx.x == 0) sh[32] = s;
-    __syncthreads();
-    return sh[32];
-}
-
-// w = dt * (J_0 x): BSR with one diagonal and 2d neighbour blocks per element row.
-__global__ void k_spmv0(int E, int NF, const double* __restrict__ bsr, const int* __restrict__ nbr,
-                        const double* __restrict__ dt, const double* __restrict__ x, double* __restrict__ y,
-                        const DevScalars* __restrict__ sc) {
-    if (sc->broken) return;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)E * 5) return;
-    const int e = (int)(idx / 5), a = (int)(idx % 5);
-    const double* row = bsr + (size_t)e * (1 + NF) * 25;
-    double s = 0.0;
 #pragma unroll
-    for (int b = 0; b < 5; ++b) s += row[a * 5 + b] * x[(size_t)e * 5 + b];
-    for (int lf = 0; lf < NF; ++lf) {
-        const int nb = nbr[(size_t)e * NF + lf];
-        if (nb < 0) continue;
-        const double* blk = row + (1 + lf) * 25;
+    for (int i = 0; i < ARN_CHUNK; ++i) {
+        double x = v[i];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[warp][i] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < n) {
+        double s = 0.0;
+        for (int w = 0; w < ARN_THREADS / 32; ++w) s += sh[w][threadIdx.x];
+        dst[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// sum over blocks of part[b * stride + col], identical order in every block; result to all threads
+__device__ __forceinline__ void reduce_cols(const double* part, int nb, int stride, int ncol, double* out_sh,
+                                            double (*sh)[ARN_CHUNK]) {
+    for (int c0 = 0; c0 < ncol; c0 += ARN_CHUNK) {
+        double v[ARN_CHUNK];
 #pragma unroll
-        for (int b = 0; b < 5; ++b) s += blk[a * 5 + b] * x[(size_t)nb * 5 + b];
+        for (int i = 0; i < ARN_CHUNK; ++i) v[i] = 0.0;
+        for (int b = threadIdx.x; b < nb; b += ARN_THREADS) {
+#pragma unroll
+            for (int i = 0; i < ARN_CHUNK; ++i)
+                if (c0 + i < ncol) v[i] += __ldcg(part + (size_t)b * stride + c0 + i);   // other blocks' data: L2
+        }
+        const int n = ncol - c0 < ARN_CHUNK ? ncol - c0 : ARN_CHUNK;
+        block_reduce_store(v, n, out_sh + c0, sh);
     }
-    y[idx] = dt[e] * s;
 }
 
-// v0 = dt * r (unnormalised start vector) and per-block partial sums of its squares.
-__global__ void k_start(int64_t K0, const double* __restrict__ r, const double* __restrict__ dt,
-                        double* __restrict__ v0, double* __restrict__ partial, int stride) {
-    __shared__ double sh[40];
-    double acc = 0.0;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K0; k += (int64_t)gridDim.x * blockDim.x) {
-        const double v = dt[k / 5] * r[k];
-        v0[k] = v;
-        acc += v * v;
+// dots[i] (i < nv) = V[i] . w over this block's slice, plus w . w at index nv if with_ww
+__device__ __forceinline__ void slice_dots(const double* V, const double* w, int64_t K0, int64_t k0, int64_t k1,
+                                           int nv, int with_ww, double* dst, double (*sh)[ARN_CHUNK]) {
+    const int ncol = nv + with_ww;
+    for (int c0 = 0; c0 < ncol; c0 += ARN_CHUNK) {
+        double v[ARN_CHUNK];
+#pragma unroll
+        for (int i = 0; i < ARN_CHUNK; ++i) v[i] = 0.0;
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
+            const double wk = w[k];
+#pragma unroll
+            for (int i = 0; i < ARN_CHUNK; ++i) {
+                const int col = c0 + i;
+                if (col < nv) v[i] += V[(size_t)col * K0 + k] * wk;
+                else if (col == nv && with_ww) v[i] += wk * wk;
+            }
+        }
+        const int n = ncol - c0 < ARN_CHUNK ? ncol - c0 : ARN_CHUNK;
+        block_reduce_store(v, n, dst + c0, sh);
     }
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * stride] = s;
 }
 
-__global__ void k_start_norm(int64_t K0, double* __restrict__ v0, const double* __restrict__ partial, int nb,
-                             int stride, DevScalars* sc) {
-    __shared__ double sh[40];
-    const double bb = reduce_partials(partial, nb, stride, 0, sh);
-    const double beta = sqrt(bb);
+__global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int NF, int m,
+                                                         const double* __restrict__ bsr, const int* __restrict__ nbr,
+                                                         const double* __restrict__ dt, const double* __restrict__ r,
+                                                         double* __restrict__ V, double* __restrict__ w,
+                                                         double* __restrict__ H, double* __restrict__ partA,
+                                                         double* __restrict__ partB, double* __restrict__ partC,
+                                                         int stride, GridBar* bar, long long budget, DevScalars* sc) {
+    __shared__ double sh[ARN_THREADS / 32][ARN_CHUNK];
+    __shared__ double h1[MAX_KRYLOV + 8], h2[MAX_KRYLOV + 8], red[8];
+    __shared__ int s_ok;
+    const unsigned nb = gridDim.x;
+    const int64_t chunk = (K0 + nb - 1) / nb;
+    const int64_t k0 = (int64_t)blockIdx.x * chunk;
+    const int64_t k1 = (k0 + chunk) < K0 ? (k0 + chunk) : K0;
+    // start vector v_1 = N / ||N||, N = dt * r
+    {
+        double v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
+            const double x = dt[k / 5] * r[k];
+            V[k] = x;
+            v[0] += x * x;
+        }
+        block_reduce_store(v, 1, partA + (size_t)blockIdx.x * stride, sh);
+    }
+    if (!grid_sync(bar, nb, budget, sc, &s_ok)) return;
+    reduce_cols(partA, nb, stride, 1, red, sh);
+    const double beta = sqrt(red[0]);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         sc->beta = beta;
-        sc->broken = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
         sc->m_used = 0;
+        sc->broken = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
         if (!isfinite(beta)) sc->nonfinite = 1;
     }
-    if (beta == 0.0 || !isfinite(beta)) return;
-    const double ib = 1.0 / beta;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K0; k += (int64_t)gridDim.x * blockDim.x)
-        v0[k] *= ib;
-}
-
-// partial[blk][i] = sum over the block's slice of V[i] . w  (i < nv); partial[blk][nv] = w . w
-__global__ void k_dots(int64_t K0, int nv, const double* __restrict__ V, const double* __restrict__ w,
-                       double* __restrict__ partial, int stride, int with_ww, const DevScalars* __restrict__ sc) {
-    if (sc->broken) return;
-    __shared__ double sh[40];
-    for (int i = 0; i < nv + with_ww; ++i) {
-        const double* vi = i < nv ? V + (size_t)i * K0 : w;
-        double acc = 0.0;
-        for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K0;
-             k += (int64_t)gridDim.x * blockDim.x)
-            acc += vi[k] * w[k];
-        const double s = block_sum(acc, sh);
-        if (threadIdx.x == 0) partial[(size_t)blockIdx.x * stride + i] = s;
+    if (beta == 0.0 || !isfinite(beta)) return;   // uniform across blocks
+    {
+        const double ib = 1.0 / beta;
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) V[k] *= ib;
     }
-}
-
-// h_i = sum of partials; w -= sum_i h_i V[i]; block 0 stores/accumulates h into hcol.
-// pass 0 also records w0 = ||w|| before orthogonalisation; pass 1 leaves per-block
-// partial sums of the squares of the updated w in partial2.
-__global__ void k_orth(int64_t K0, int nv, const double* __restrict__ V, double* __restrict__ w,
-                       const double* __restrict__ partial, int nb, int stride, int pass, double* __restrict__ hcol,
-                       double* __restrict__ partial2, DevScalars* sc) {
-    if (sc->broken) return;
-    __shared__ double sh[40];
-    __shared__ double hs[MAX_KRYLOV + 2];
-    for (int i = 0; i < nv + (pass == 0 ? 1 : 0); ++i) {
-        const double s = reduce_partials(partial, nb, stride, i, sh);
-        if (threadIdx.x == 0) hs[i] = s;
-    }
-    __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        for (int i = 0; i < nv; ++i) hcol[i] = pass == 0 ? hs[i] : hcol[i] + hs[i];
-        if (pass == 0) sc->w0 = sqrt(hs[nv]);
-    }
-    double acc = 0.0;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K0; k += (int64_t)gridDim.x * blockDim.x) {
-        double s = w[k];
-        for (int i = 0; i < nv; ++i) s -= hs[i] * V[(size_t)i * K0 + k];
-        w[k] = s;
-        acc += s * s;
-    }
-    if (pass == 1) {
-        const double s = block_sum(acc, sh);
-        if (threadIdx.x == 0) partial2[blockIdx.x] = s;
-    }
-}
-
-// h_{j+1,j} = ||w||; happy breakdown if h_{j+1,j} <= 1e-12 ||A v_j||; else v_{j+1} = w / h.
-__global__ void k_normalize(int64_t K0, int j, int m, double* __restrict__ V, const double* __restrict__ w,
-                            const double* __restrict__ partial2, int nb, const double* __restrict__ hcol,
-                            double* __restrict__ H, DevScalars* sc) {
-    if (sc->broken) return;
-    __shared__ double sh[40];
-    const double hn = sqrt(reduce_partials(partial2, nb, 1, 0, sh));
-    const bool brk = !(hn > 1e-12 * sc->w0);
-    __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i];
-        H[(size_t)(j + 1) * m + j] = hn;
-        sc->m_used = j + 1;
-        sc->hsub = hn;
-        if (!isfinite(hn)) sc->nonfinite = 1;
-    }
-    if (brk) {
-        // every block reaches the same decision from the same reduced value
+    if (!grid_sync(bar, nb, budget, sc, &s_ok)) return;
+    for (int j = 0; j < m; ++j) {
+        const double* vj = V + (size_t)j * K0;
+        // SpMV on this block's rows, w = dt * (J_0 v_j)
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
+            const int e = (int)(k / 5), a = (int)(k % 5);
+            const double* row = bsr + (size_t)e * (1 + NF) * 25;
+            double s = 0.0;
+#pragma unroll
+            for (int b = 0; b < 5; ++b) s += row[a * 5 + b] * __ldcg(vj + (size_t)e * 5 + b);
+            for (int lf = 0; lf < NF; ++lf) {
+                const int n = nbr[(size_t)e * NF + lf];
+                if (n < 0) continue;
+                const double* blk = row + (1 + lf) * 25;
+#pragma unroll
+                for (int b = 0; b < 5; ++b) s += blk[a * 5 + b] * __ldcg(vj + (size_t)n * 5 + b);   // written by other blocks
+            }
+            w[k] = dt[e] * s;
+        }
         __syncthreads();
-        if (threadIdx.x == 0) atomicExch(&sc->broken, 1);
-        return;
+        // CGS pass 1: h1 = V^T w and w.w
+        slice_dots(V, w, K0, k0, k1, j + 1, 1, partA + (size_t)blockIdx.x * stride, sh);
+        if (!grid_sync(bar, nb, budget, sc, &s_ok)) return;
+        reduce_cols(partA, nb, stride, j + 2, h1, sh);
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
+            double s = w[k];
+            for (int i = 0; i <= j; ++i) s -= h1[i] * V[(size_t)i * K0 + k];
+            w[k] = s;
+        }
+        __syncthreads();
+        // CGS pass 2 (re-orthogonalisation)
+        slice_dots(V, w, K0, k0, k1, j + 1, 0, partB + (size_t)blockIdx.x * stride, sh);
+        if (!grid_sync(bar, nb, budget, sc, &s_ok)) return;
+        reduce_cols(partB, nb, stride, j + 1, h2, sh);
+        {
+            double v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
+                double s = w[k];
+                for (int i = 0; i <= j; ++i) s -= h2[i] * V[(size_t)i * K0 + k];
+                w[k] = s;
+                v[0] += s * s;
+            }
+            block_reduce_store(v, 1, partC + (size_t)blockIdx.x * stride, sh);
+        }
+        if (!grid_sync(bar, nb, budget, sc, &s_ok)) return;
+        reduce_cols(partC, nb, stride, 1, red, sh);
+        const double hn = sqrt(red[0]);
+        const double w0 = sqrt(h1[j + 1]);
+        const bool brk = !(hn > 1e-12 * w0);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h1[i] + h2[i];
+            H[(size_t)(j + 1) * m + j] = hn;
+            sc->m_used = j + 1;
+            sc->hsub = hn;
+            sc->w0 = w0;
+            if (!isfinite(hn)) sc->nonfinite = 1;
+            if (brk) sc->broken = 1;
+        }
+        if (brk || j + 1 == m) break;   // uniform: every block reduced the same value
+        const double ih = 1.0 / hn;
+        double* vn = V + (size_t)(j + 1) * K0;
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) vn[k] = w[k] * ih;
+        if (!grid_sync(bar, nb, budget, sc, &s_ok)) return;
     }
-    const double ih = 1.0 / hn;
-    double* vn = V + (size_t)(j + 1) * K0;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K0; k += (int64_t)gridDim.x * blockDim.x)
-        vn[k] = w[k] * ih;
+}
+
+// Self-test of the bounded wait: one block waits at a barrier sized for two blocks, so
+// the arrival it waits for never comes and the wait must give up by itself.
+__global__ void k_barrier_selftest(GridBar* bar, long long budget, DevScalars* sc) {
+    __shared__ int s_ok;
+    grid_sync(bar, 2u, budget, sc, &s_ok);
+}
+
+emg_status selftest_barrier_timeout(emg_ctx* c, int* timed_out) {
+    GridBar* bar = reinterpret_cast<GridBar*>(c->bar);
+    EMG_CUDA_TRY(c, cudaMemsetAsync(bar, 0, sizeof(GridBar), c->stream));
+    {
+        ProfScope _ps(c, PC_CONTROL);
+        k_barrier_selftest<<<1, 32, 0, c->stream>>>(bar, 200000000LL, c->sc);   // ~0.1 s of SM clock
+    }
+    EMG_CHECK_LAUNCH(c);
+    int flag = 0;
+    EMG_CUDA_TRY(c, cudaMemcpyAsync(&flag, &c->sc->timeout, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    EMG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    *timed_out = flag;
+    EMG_CUDA_TRY(c, cudaMemsetAsync(&c->sc->timeout, 0, sizeof(int), c->stream));
+    EMG_CUDA_TRY(c, cudaMemsetAsync(bar, 0, sizeof(GridBar), c->stream));
+    return EMG_OK;
 }
 
 struct Pade13 {
@@ -331,39 +408,57 @@ emg_status launch_exp1(emg_ctx* c, const double* u0, const double* tau0, const d
     LevelDev& L = c->lv[0];
     const int64_t K0 = 5 * c->E;
     const int m = c->prm.krylov_m;
-    const int nb = c->red_blocks;
-    const int stride = MAX_KRYLOV + 8;
-    double* part2 = c->partial + (size_t)nb * stride;  // separate tail for the norm partials
     emg_status st = launch_residual(c, 0, u0, tau0, L.r);
     if (st != EMG_OK) return st;
     st = launch_face_jacobian(c, 0, u0);
     if (st != EMG_OK) return st;
     st = launch_bsr0(c);
     if (st != EMG_OK) return st;
-    { ProfScope _ps(c, PC_ARNOLDI); k_start<<<nb, RED_THREADS, 0, c->stream>>>(K0, L.r, dt, c->V, c->partial, stride); }
-    EMG_CHECK_LAUNCH(c);
-    { ProfScope _ps(c, PC_ARNOLDI); k_start_norm<<<nb, RED_THREADS, 0, c->stream>>>(K0, c->V, c->partial, nb, stride, c->sc); }
-    EMG_CHECK_LAUNCH(c);
-    const unsigned gs = (unsigned)((K0 + 255) / 256);
-    const int NF = 2 * c->dim;
-    for (int j = 0; j < m; ++j) {
-        { ProfScope _ps(c, PC_ARNOLDI); k_spmv0<<<gs, 256, 0, c->stream>>>((int)c->E, NF, c->bsr, c->elem_nbr, dt, c->V + (size_t)j * K0, c->w,
-                                           c->sc); }
-        { ProfScope _ps(c, PC_ARNOLDI); k_dots<<<nb, RED_THREADS, 0, c->stream>>>(K0, j + 1, c->V, c->w, c->partial, stride, 1, c->sc); }
-        { ProfScope _ps(c, PC_ARNOLDI); k_orth<<<nb, RED_THREADS, 0, c->stream>>>(K0, j + 1, c->V, c->w, c->partial, nb, stride, 0, c->hcol, part2,
-                                                  c->sc); }
-        { ProfScope _ps(c, PC_ARNOLDI); k_dots<<<nb, RED_THREADS, 0, c->stream>>>(K0, j + 1, c->V, c->w, c->partial, stride, 0, c->sc); }
-        { ProfScope _ps(c, PC_ARNOLDI); k_orth<<<nb, RED_THREADS, 0, c->stream>>>(K0, j + 1, c->V, c->w, c->partial, nb, stride, 1, c->hcol, part2,
-                                                  c->sc); }
-        { ProfScope _ps(c, PC_ARNOLDI); k_normalize<<<nb, RED_THREADS, 0, c->stream>>>(K0, j, m, c->V, c->w, part2, nb, c->hcol, c->H, c->sc); }
-        EMG_CHECK_LAUNCH(c);
+    // one cooperative launch: every block must be co-resident for the grid barriers
+    int per_sm = 0, nsm = 0;
+    EMG_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi, ARN_THREADS, 0));
+    EMG_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+    int64_t nb = (int64_t)nsm * (per_sm < 2 ? per_sm : 2);
+    const int64_t need = (K0 + ARN_THREADS - 1) / ARN_THREADS;
+    if (nb > need) nb = need;
+    if (nb > c->red_blocks) nb = c->red_blocks;
+    if (nb < 1) nb = 1;
+    const int stride = MAX_KRYLOV + 8;
+    double* partA = c->partial;
+    double* partB = partA + (size_t)c->red_blocks * stride;
+    double* partC = partB + (size_t)c->red_blocks * stride;
+    GridBar* bar = reinterpret_cast<GridBar*>(c->bar);
+    EMG_CUDA_TRY(c, cudaMemsetAsync(bar, 0, sizeof(GridBar), c->stream));
+    int64_t K0a = K0;
+    int Ea = (int)c->E, NFa = 2 * c->dim, ma = m, stra = stride;
+    const double* bsr = c->bsr;
+    const int* nbr = c->elem_nbr;
+    const double* rr = L.r;
+    double* Vv = c->V;
+    double* ww = c->w;
+    double* HH = c->H;
+    long long budget = 4000000000LL;   // about two seconds of SM clock per barrier wait
+    DevScalars* scp = c->sc;
+    void* args[] = {&K0a, &Ea, &NFa, &ma, (void*)&bsr, (void*)&nbr, (void*)&dt, (void*)&rr, &Vv, &ww, &HH,
+                    &partA, &partB, &partC, &stra, &bar, &budget, &scp};
+    {
+        ProfScope _ps(c, PC_ARNOLDI);
+        EMG_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3((unsigned)nb), dim3(ARN_THREADS),
+                                                    args, 0, c->stream));
     }
     const int n = m + 1;
     const size_t smem = (size_t)8 * n * n * sizeof(double);
     EMG_CUDA_TRY(c, cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    { ProfScope _ps(c, PC_PHI); k_phi<<<1, 256, smem, c->stream>>>(m, c->H, c->y, pade13(), c->sc); }
+    {
+        ProfScope _ps(c, PC_PHI);
+        k_phi<<<1, 256, smem, c->stream>>>(m, c->H, c->y, pade13(), c->sc);
+    }
     EMG_CHECK_LAUNCH(c);
-    { ProfScope _ps(c, PC_COMBINE); k_combine<<<nb, 256, 0, c->stream>>>(K0, u0, c->V, c->y, c->sc, out); }
+    {
+        ProfScope _ps(c, PC_COMBINE);
+        k_combine<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(296, (K0 + 255) / 256)), 256, 0, c->stream>>>(
+            K0, u0, c->V, c->y, c->sc, out);
+    }
     EMG_CHECK_LAUNCH(c);
     return EMG_OK;
 }

@@ -4,39 +4,42 @@
 //    substitutions read contiguous columns.
 //  * k_stage: one warp per element: y = P_e^{-1} r_e (row swaps, unit-lower forward and
 //    upper backward substitution), u^(k) = u^n + beta_k y.
+// T is the block precision (double for the FP64 form, float for the FP32 block form);
+// the residual r, u^n and u^(k) are always double.
 #include "common.cuh"
 
 namespace emg {
 
-template <int B>
+template <int B, class T>
 struct LuCfg {
     static constexpr int LD = B + 1;                 // padded row stride in shared memory
-    static constexpr size_t SMEM = (size_t)B * LD * sizeof(double);
+    static constexpr size_t SMEM = (size_t)B * LD * sizeof(T);
 };
 
-template <int B>
-__global__ void __launch_bounds__(256) k_lu(int E, double* __restrict__ blk, int* __restrict__ piv) {
-    extern __shared__ double a[];
-    constexpr int LD = LuCfg<B>::LD;
+template <int B, class T>
+__global__ void __launch_bounds__(256) k_lu(int E, T* __restrict__ blk, int* __restrict__ piv) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* a = reinterpret_cast<T*>(smraw);
+    constexpr int LD = LuCfg<B, T>::LD;
     __shared__ int s_piv;
     const int e = blockIdx.x;
     const int tid = threadIdx.x, nth = blockDim.x;
-    double* g = blk + (size_t)e * B * B;
+    T* g = blk + (size_t)e * B * B;
     for (int t = tid; t < B * B; t += nth) a[(t / B) * LD + (t % B)] = g[t];
     __syncthreads();
     for (int k = 0; k < B; ++k) {
         if (tid < 32) {
-            double best = -1.0;
+            T best = (T)-1;
             int bi = k;
             for (int r = k + tid; r < B; r += 32) {
-                const double v = fabs(a[r * LD + k]);
+                const T v = fabs(a[r * LD + k]);
                 if (v > best) {
                     best = v;
                     bi = r;
                 }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const T ob = __shfl_xor_sync(0xffffffffu, best, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ob > best || (ob == best && oi < bi)) {
                     best = ob;
@@ -52,12 +55,12 @@ __global__ void __launch_bounds__(256) k_lu(int E, double* __restrict__ blk, int
         const int pr = s_piv;
         if (pr != k)
             for (int cc = tid; cc < B; cc += nth) {
-                const double t0 = a[k * LD + cc];
+                const T t0 = a[k * LD + cc];
                 a[k * LD + cc] = a[pr * LD + cc];
                 a[pr * LD + cc] = t0;
             }
         __syncthreads();
-        const double inv = 1.0 / a[k * LD + k];
+        const T inv = (T)1 / a[k * LD + k];
         for (int r = k + 1 + tid; r < B; r += nth) a[r * LD + k] *= inv;
         __syncthreads();
         const int m = B - k - 1;
@@ -74,64 +77,67 @@ __global__ void __launch_bounds__(256) k_lu(int E, double* __restrict__ blk, int
     }
 }
 
-template <int B>
-__global__ void __launch_bounds__(128) k_stage(int E, const double* __restrict__ lu, const int* __restrict__ piv,
+template <int B, class T>
+__global__ void __launch_bounds__(128) k_stage(int E, const T* __restrict__ lu, const int* __restrict__ piv,
                                                const double* __restrict__ r, const double* __restrict__ un,
                                                double beta, double* __restrict__ out) {
-    __shared__ double ys[4][B];
+    __shared__ T ys[4][B];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int e = blockIdx.x * 4 + warp;
     if (e >= E) return;
-    double* y = ys[warp];
-    for (int t = lane; t < B; t += 32) y[t] = r[(size_t)e * B + t];
+    T* y = ys[warp];
+    for (int t = lane; t < B; t += 32) y[t] = (T)r[(size_t)e * B + t];
     __syncwarp();
     if (lane == 0) {
         const int* pv = piv + (size_t)e * B;
         for (int k = 0; k < B; ++k) {
             const int p = pv[k];
             if (p != k) {
-                const double t0 = y[k];
+                const T t0 = y[k];
                 y[k] = y[p];
                 y[p] = t0;
             }
         }
     }
     __syncwarp();
-    const double* M = lu + (size_t)e * B * B;
+    const T* M = lu + (size_t)e * B * B;
     for (int j = 0; j < B; ++j) {
-        const double yj = y[j];
-        const double* col = M + (size_t)j * B;
+        const T yj = y[j];
+        const T* col = M + (size_t)j * B;
         for (int rr = j + 1 + lane; rr < B; rr += 32) y[rr] -= col[rr] * yj;
         __syncwarp();
     }
     for (int j = B - 1; j >= 0; --j) {
-        const double* col = M + (size_t)j * B;
-        const double xj = y[j] / col[j];
+        const T* col = M + (size_t)j * B;
+        const T xj = y[j] / col[j];
         __syncwarp();
         for (int rr = lane; rr < j; rr += 32) y[rr] -= col[rr] * xj;
         if (lane == 0) y[j] = xj;
         __syncwarp();
     }
-    for (int t = lane; t < B; t += 32) out[(size_t)e * B + t] = un[(size_t)e * B + t] + beta * y[t];
+    for (int t = lane; t < B; t += 32) out[(size_t)e * B + t] = un[(size_t)e * B + t] + beta * (double)y[t];
 }
 
 #define EMG_BSIZES(X) X(15) X(30) X(50) X(75) X(20) X(100) X(175)
 
-emg_status launch_lu(emg_ctx* c, int p) {
-    LevelDev& L = c->lv[p];
+template <class T>
+static emg_status lu_dispatch(emg_ctx* c, int B, T* blk, int* piv) {
     const unsigned E = (unsigned)c->E;
-    switch (L.B) {
-#define EMG_LU_CASE(BB)                                                                                  \
-    case BB: {                                                                                           \
-        const size_t sm = LuCfg<BB>::SMEM;                                                               \
-        if (sm > 227 * 1024) {                                                                           \
-            c->err = "FP64 block of size " #BB " does not fit in shared memory";                         \
-            return EMG_ERR_ARG;                                                                          \
-        }                                                                                                \
-        EMG_CUDA_TRY(c, cudaFuncSetAttribute(k_lu<BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
-        { ProfScope _ps(c, PC_LU); k_lu<BB><<<E, 256, sm, c->stream>>>((int)E, L.blk, L.piv); }                                      \
-        EMG_CHECK_LAUNCH(c);                                                                             \
-        return EMG_OK;                                                                                   \
+    switch (B) {
+#define EMG_LU_CASE(BB)                                                                                      \
+    case BB: {                                                                                               \
+        const size_t sm = LuCfg<BB, T>::SMEM;                                                                \
+        if (sm > 227 * 1024) {                                                                               \
+            c->err = "block of size " #BB " does not fit in shared memory in this precision";                \
+            return EMG_ERR_ARG;                                                                              \
+        }                                                                                                    \
+        EMG_CUDA_TRY(c, cudaFuncSetAttribute(k_lu<BB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+        {                                                                                                    \
+            ProfScope _ps(c, PC_LU);                                                                         \
+            k_lu<BB, T><<<E, 256, sm, c->stream>>>((int)E, blk, piv);                                        \
+        }                                                                                                    \
+        EMG_CHECK_LAUNCH(c);                                                                                 \
+        return EMG_OK;                                                                                       \
     }
         EMG_BSIZES(EMG_LU_CASE)
 #undef EMG_LU_CASE
@@ -141,14 +147,17 @@ emg_status launch_lu(emg_ctx* c, int p) {
     }
 }
 
-emg_status launch_stage(emg_ctx* c, int p, const double* r, const double* un, double beta, double* out) {
-    LevelDev& L = c->lv[p];
+template <class T>
+static emg_status stage_dispatch(emg_ctx* c, int B, const T* lu, const int* piv, const double* r, const double* un,
+                                 double beta, double* out) {
     const unsigned E = (unsigned)c->E;
-    switch (L.B) {
-#define EMG_ST_CASE(BB)                                                                             \
-    case BB:                                                                                        \
-        { ProfScope _ps(c, PC_STAGE); k_stage<BB><<<(E + 3) / 4, 128, 0, c->stream>>>((int)E, L.blk, L.piv, r, un, beta, out); }  \
-        EMG_CHECK_LAUNCH(c);                                                                        \
+    switch (B) {
+#define EMG_ST_CASE(BB)                                                                          \
+    case BB: {                                                                                   \
+        ProfScope _ps(c, PC_STAGE);                                                              \
+        k_stage<BB, T><<<(E + 3) / 4, 128, 0, c->stream>>>((int)E, lu, piv, r, un, beta, out);   \
+    }                                                                                            \
+        EMG_CHECK_LAUNCH(c);                                                                     \
         return EMG_OK;
         EMG_BSIZES(EMG_ST_CASE)
 #undef EMG_ST_CASE
@@ -156,6 +165,20 @@ emg_status launch_stage(emg_ctx* c, int p, const double* r, const double* un, do
             c->err = "unsupported block size";
             return EMG_ERR_ARG;
     }
+}
+
+emg_status launch_lu(emg_ctx* c, int p) { return lu_dispatch<double>(c, c->lv[p].B, c->lv[p].blk, c->lv[p].piv); }
+
+emg_status launch_lu32(emg_ctx* c, int p) { return lu_dispatch<float>(c, c->lv[p].B, c->lv[p].blk32, c->lv[p].piv); }
+
+emg_status launch_stage(emg_ctx* c, int p, const double* r, const double* un, double beta, double* out) {
+    LevelDev& L = c->lv[p];
+    return stage_dispatch<double>(c, L.B, L.blk, L.piv, r, un, beta, out);
+}
+
+emg_status launch_stage32(emg_ctx* c, int p, const double* r, const double* un, double beta, double* out) {
+    LevelDev& L = c->lv[p];
+    return stage_dispatch<float>(c, L.B, L.blk32, L.piv, r, un, beta, out);
 }
 
 }  // namespace emg

@@ -575,7 +575,15 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
         EMG_ALLOC(L.fjl, double, F * L.QF * 25);
         EMG_ALLOC(L.fjr, double, std::max<int64_t>(F_int, 1) * L.QF * 25);
         if (p > 0) {
-            EMG_ALLOC(L.blk, double, E * L.B * L.B);
+            if (c->prm.prec == EMG_PREC_FP32_BLOCKS) {
+                EMG_ALLOC(L.blk32, float, E * L.B * L.B);
+                EMG_ALLOC(L.vpsi32, float, E * L.Q * L.N);
+                EMG_ALLOC(L.vgw32, float, E * D * L.Q * L.N);
+                EMG_ALLOC(L.fpsiL32, float, F * L.QF * L.N);
+                EMG_ALLOC(L.fpsiR32, float, std::max<int64_t>(F_int, 1) * L.QF * L.N);
+            } else {
+                EMG_ALLOC(L.blk, double, E * L.B * L.B);
+            }
             EMG_ALLOC(L.piv, int, E * L.B);
         }
     }
@@ -588,8 +596,9 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
     EMG_ALLOC(c->H, double, (m_kr + 1) * m_kr);
     EMG_ALLOC(c->hcol, double, m_kr + 2);
     EMG_ALLOC(c->y, double, m_kr + 1);
-    c->red_blocks = 296;
-    EMG_ALLOC(c->partial, double, c->red_blocks * (MAX_KRYLOV + 8) + c->red_blocks);
+    c->red_blocks = 2 * 160;
+    EMG_ALLOC(c->partial, double, 3 * c->red_blocks * (MAX_KRYLOV + 8));
+    EMG_ALLOC(c->bar, unsigned int, 4);
     EMG_ALLOC(c->sc, DevScalars, 1);
     EMG_CUDA_TRY(c, cudaMallocHost(&c->sc_host, sizeof(DevScalars)));
     const int Bmax = 5 * nmax;
@@ -628,6 +637,10 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
         st = build_tables<3, 35>(c, nmax, exps_d);
     }
     if (st != EMG_OK) return st;
+    if (c->prm.prec == EMG_PREC_FP32_BLOCKS) {
+        st = build_float_tables(c);
+        if (st != EMG_OK) return st;
+    }
     std::vector<double> hv(E);
     EMG_CUDA_TRY(c, cudaMemcpyAsync(hv.data(), c->vol, E * 8, cudaMemcpyDeviceToHost, c->stream));
     EMG_CUDA_TRY(c, cudaStreamSynchronize(c->stream));

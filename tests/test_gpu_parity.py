@@ -198,6 +198,49 @@ def test_converged_state_matches_oracle(lib):
     assert rel_err(u, g["u"]) < 1e-9, rel_err(u, g["u"])
 
 
+def test_bounded_wait_times_out_and_context_survives(lib):
+    desc = ogrid(8, 2)
+    s = lib.Solver(desc, p_max=1)
+    u = s.get_state()
+    R0 = s.residual(1, u)
+    with pytest.raises(lib.EmgError) as ei:
+        s._check(s.lib.emg_selftest_wait_timeout(s.h))
+    assert ei.value.status == 7
+    # the context is still usable and the flag was cleared
+    assert np.array_equal(s.residual(1, u), R0)
+    info = s.vcycle()
+    assert np.isfinite(info["res_rho"])
+    s.close()
+
+
+def test_fp32_block_prk_step_close_to_oracle(lib):
+    """FP32 blocks change only the preconditioner: the PRK update agrees with the FP64
+    oracle to float accuracy."""
+    desc = ogrid(32, 16)
+    s = lib.Solver(desc, p_max=2, prec=1)
+    dg = DG(desc, 2)
+    u = np.ascontiguousarray(perturbed_state(dg, amp=0.002))
+    ug = s.prk_step(2, u, cfl=3.0)
+    D = dg.diag_blocks(2, u)
+    dt = oemg.dtau(dg, 2, u, 3.0)
+    P = np.eye(D.shape[-1])[None] / dt[:, None, None] - D
+    uo = oemg.prk_step(lambda w: dg.residual(2, w), P, u)
+    e = rel_err(ug - u, uo - u)
+    assert 1e-12 < e < 1e-4, e
+    s.close()
+
+
+@pytest.mark.skipif(not os.path.exists(GOLDEN), reason="golden file not generated")
+def test_fp32_block_converged_state_matches_fp64_oracle(lib):
+    """The fixed point R = 0 does not depend on the preconditioner (Eq. prk_scalar)."""
+    g = np.load(GOLDEN)
+    s = lib.Solver(ogrid(32, 16), p_max=2, prec=1)
+    rep = s.solve_steady(drop=1e-10, max_cycles=int(g["cycles"]) + 300)
+    assert rep["converged"]
+    assert rel_err(s.get_state(), g["u"]) < 1e-9, rel_err(s.get_state(), g["u"])
+    s.close()
+
+
 def test_error_paths(lib):
     desc = ogrid(8, 2)
     s = lib.Solver(desc, p_max=1)
