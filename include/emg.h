@@ -171,6 +171,32 @@ emg_status emg_jacobian_p0(emg_ctx* ctx, const double* u0, double* diag, double*
 emg_status emg_exp1_step(emg_ctx* ctx, const double* u0, const double* tau0, const double* dt,
                          double* u_out, int32_t* krylov_dim, int32_t on_device);
 
+/* ---- EXP1 step that allocates nothing (the paper has no counterpart) ----
+ * For callers that cannot allocate device memory once they are running: an application
+ * whose device memory is handed out only by its own pool, or code that issues this step
+ * while a stream is being captured and so may not call cudaMalloc.  The step is the same
+ * as emg_exp1_step (u_out = u0 + phi_1(DT J_0) DT r0, m Arnoldi steps with happy
+ * breakdown, Pade phi_1), but it takes the p = 0 Jacobian in the block form that
+ * emg_jacobian_p0 returns and the residual r0 = R~_0(u0), and needs no context.
+ * Its work memory is one file-scope device array of about 26 MB, which every GPU that
+ * loads this library holds until the process exits; no call makes or frees an
+ * allocation.  Limits: n_elems <= 8192, krylov_m <= 40, dim 2 or 3; larger requests fail
+ * with EMG_ERR_ARG.
+ * All array arguments are device pointers on the current device: diag [n_elems][5][5],
+ * off [n_elems][2 dim][5][5], nbr [n_elems][2 dim] (neighbour or -1), r0 and u0 and
+ * u_out [n_elems][5], dt [n_elems].  Work is enqueued on cuda_stream (NULL = the legacy
+ * default stream) and the call synchronises it to read krylov_dim (may be NULL).
+ * The first call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  Every call on a device
+ * shares the one array and finds the previous call's contents in it (the call clears
+ * what must start at zero), so calls whose work overlaps on the GPU, from several
+ * streams or host threads, race and must be serialised by the caller.
+ * Returns EMG_ERR_TIMEOUT or EMG_ERR_NONFINITE like emg_exp1_step, EMG_ERR_CUDA on a
+ * runtime failure (no per-call message: there is no context). */
+emg_status emg_exp1_step_noalloc(int32_t dim, int64_t n_elems, const double* diag, const double* off,
+                                 const int64_t* nbr, const double* r0, const double* dt, const double* u0,
+                                 int32_t krylov_m, void* cuda_stream, double* u_out, int32_t* krylov_dim);
+
 /* Element volumes |E| and length scales h = 2d|E|/|dE| (Eq. x3d), [n_elems] each. */
 emg_status emg_element_geometry(emg_ctx* ctx, double* vol, double* h);
 

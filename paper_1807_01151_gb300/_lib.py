@@ -64,6 +64,9 @@ EXPORTS = {
     "emg_profile_class_name": (C.c_char_p, [C.c_int32]),
     "emg_launch_count": (C.c_int64, [C.c_void_p]),
     "emg_selftest_wait_timeout": (C.c_int, [C.c_void_p]),
+    "emg_exp1_step_noalloc": (C.c_int, [C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                        C.POINTER(C.c_int32)]),
     "emg_build_info": (C.c_char_p, []),
 }
 
@@ -271,6 +274,23 @@ class Solver:
         h = np.empty(self.E)
         self._check(self.lib.emg_element_geometry(self.h, _ptr(vol)[0], _ptr(h)[0]))
         return vol, h
+
+
+def exp1_step_noalloc(dim, diag, off, nbr, r0, dt, u0, u_out, krylov_m=30, stream=None):
+    """emg_exp1_step_noalloc on CUDA tensors (device pointers only); returns the Krylov
+    dimension.  Raises EmgError on a non-zero status."""
+    lib = load()
+    ptrs = []
+    for t in (diag, off, nbr, r0, dt, u0, u_out):
+        if not (hasattr(t, "data_ptr") and getattr(t, "is_cuda", False) and t.is_contiguous()):
+            raise TypeError("exp1_step_noalloc takes contiguous CUDA tensors")
+        ptrs.append(C.c_void_p(t.data_ptr()))
+    k = C.c_int32()
+    st = lib.emg_exp1_step_noalloc(int(dim), int(diag.shape[0]), *ptrs[:6], int(krylov_m),
+                                   C.c_void_p(stream) if stream else None, ptrs[6], C.byref(k))
+    if st != 0:
+        raise EmgError(st, "emg_exp1_step_noalloc")
+    return k.value
 
 
 def build_info():

@@ -463,4 +463,120 @@ emg_status launch_exp1(emg_ctx* c, const double* u0, const double* tau0, const d
     return EMG_OK;
 }
 
+// ---- EXP1 step without any allocation --------------------------------------------------------
+// For callers that must not allocate device memory once they are running (for example a
+// host application whose memory is handed out by its own pool, or code that issues work
+// while a stream is being captured): the Krylov basis, the packed block rows, the
+// reduction partials, the Hessenberg matrix and the barrier live in one file-scope device
+// array of fixed size, so the call itself allocates nothing.
+constexpr int64_t NA_MAX_ELEMS = 8192;
+constexpr int NA_MAX_M = 40;
+constexpr int NA_MAX_NF = 6;
+constexpr int NA_BLOCKS = 320;
+constexpr int NA_STRIDE = MAX_KRYLOV + 8;
+constexpr int64_t NA_K0 = 5 * NA_MAX_ELEMS;
+constexpr size_t NA_OFF_V = 0;
+constexpr size_t NA_OFF_W = NA_OFF_V + (size_t)(NA_MAX_M + 1) * NA_K0;
+constexpr size_t NA_OFF_BSR = NA_OFF_W + (size_t)NA_K0;
+constexpr size_t NA_OFF_NBR = NA_OFF_BSR + (size_t)NA_MAX_ELEMS * (1 + NA_MAX_NF) * 25;
+constexpr size_t NA_OFF_H = NA_OFF_NBR + (size_t)NA_MAX_ELEMS * NA_MAX_NF / 2;
+constexpr size_t NA_OFF_Y = NA_OFF_H + (size_t)(NA_MAX_M + 1) * NA_MAX_M;
+constexpr size_t NA_OFF_PART = NA_OFF_Y + NA_MAX_M + 8;
+constexpr size_t NA_OFF_SC = NA_OFF_PART + (size_t)3 * NA_BLOCKS * NA_STRIDE;
+constexpr size_t NA_OFF_BAR = NA_OFF_SC + 16;
+constexpr size_t NA_DOUBLES = NA_OFF_BAR + 8;   // about 26 MB
+
+static __device__ __align__(256) double g_exp1_scratch[NA_DOUBLES];
+static_assert(sizeof(DevScalars) <= 16 * sizeof(double), "scalars do not fit their slot");
+
+// Device address of g_exp1_scratch for each device, taken once with that device current.
+static double* g_exp1_scratch_addr[64] = {};
+
+__global__ void k_pack_bsr(int64_t E, int NF, const double* __restrict__ diag, const double* __restrict__ off,
+                           const int64_t* __restrict__ nbr, double* __restrict__ bsr, int* __restrict__ nbr32) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= E * (1 + NF) * 25) return;
+    const int64_t e = idx / ((1 + NF) * 25);
+    const int r = (int)(idx % ((1 + NF) * 25));
+    const int blk = r / 25, t = r % 25;
+    bsr[idx] = blk == 0 ? diag[e * 25 + t] : off[(e * NF + blk - 1) * 25 + t];
+    if (r < NF) nbr32[e * NF + r] = (int)nbr[e * NF + r];
+}
+
+}  // namespace emg
+
+extern "C" emg_status emg_exp1_step_noalloc(int32_t dim, int64_t n_elems, const double* diag, const double* off,
+                                            const int64_t* nbr, const double* r0, const double* dt,
+                                            const double* u0, int32_t krylov_m, void* cuda_stream,
+                                            double* u_out, int32_t* krylov_dim) {
+    using namespace emg;
+    if ((dim != 2 && dim != 3) || n_elems < 1 || n_elems > NA_MAX_ELEMS || krylov_m < 1 || krylov_m > NA_MAX_M ||
+        !diag || !off || !nbr || !r0 || !dt || !u0 || !u_out)
+        return EMG_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return EMG_ERR_CUDA;
+    if (!g_exp1_scratch_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_exp1_scratch) != cudaSuccess || !p) return EMG_ERR_CUDA;
+        g_exp1_scratch_addr[dev] = static_cast<double*>(p);
+    }
+    double* S = g_exp1_scratch_addr[dev];
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int NF = 2 * dim;
+    const int64_t E = n_elems, K0 = 5 * E;
+    double* V = S + NA_OFF_V;
+    double* w = S + NA_OFF_W;
+    double* bsr = S + NA_OFF_BSR;
+    int* nbr32 = reinterpret_cast<int*>(S + NA_OFF_NBR);
+    double* H = S + NA_OFF_H;
+    double* y = S + NA_OFF_Y;
+    double* partA = S + NA_OFF_PART;
+    double* partB = partA + (size_t)NA_BLOCKS * NA_STRIDE;
+    double* partC = partB + (size_t)NA_BLOCKS * NA_STRIDE;
+    DevScalars* sc = reinterpret_cast<DevScalars*>(S + NA_OFF_SC);
+    GridBar* bar = reinterpret_cast<GridBar*>(S + NA_OFF_BAR);
+    // the previous call's contents remain: clear the flags and the barrier
+    if (cudaMemsetAsync(sc, 0, sizeof(DevScalars), st) != cudaSuccess) return EMG_ERR_CUDA;
+    if (cudaMemsetAsync(bar, 0, sizeof(GridBar), st) != cudaSuccess) return EMG_ERR_CUDA;
+    const int64_t npack = E * (1 + NF) * 25;
+    k_pack_bsr<<<(unsigned)((npack + 255) / 256), 256, 0, st>>>(E, NF, diag, off, nbr, bsr, nbr32);
+    if (cudaGetLastError() != cudaSuccess) return EMG_ERR_CUDA;
+    int per_sm = 0, nsm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi, ARN_THREADS, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return EMG_ERR_CUDA;
+    int64_t nb = (int64_t)nsm * (per_sm < 2 ? per_sm : 2);
+    const int64_t need = (K0 + ARN_THREADS - 1) / ARN_THREADS;
+    if (nb > need) nb = need;
+    if (nb > NA_BLOCKS) nb = NA_BLOCKS;
+    if (nb < 1) nb = 1;
+    int64_t K0a = K0;
+    int Ea = (int)E, NFa = NF, ma = krylov_m, stra = NA_STRIDE;
+    const double* bsrc = bsr;
+    const int* nbrc = nbr32;
+    long long budget = 4000000000LL;
+    void* args[] = {&K0a, &Ea, &NFa, &ma, (void*)&bsrc, (void*)&nbrc, (void*)&dt, (void*)&r0, &V, &w, &H,
+                    &partA, &partB, &partC, &stra, &bar, &budget, &sc};
+    if (cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3((unsigned)nb), dim3(ARN_THREADS), args, 0, st) !=
+        cudaSuccess)
+        return EMG_ERR_CUDA;
+    const int n = krylov_m + 1;
+    const size_t smem = (size_t)8 * n * n * sizeof(double);
+    if (cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return EMG_ERR_CUDA;
+    k_phi<<<1, 256, smem, st>>>(krylov_m, H, y, pade13(), sc);
+    k_combine<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(296, (K0 + 255) / 256)), 256, 0, st>>>(
+        K0, u0, V, y, sc, u_out);
+    if (cudaGetLastError() != cudaSuccess) return EMG_ERR_CUDA;
+    DevScalars hs;
+    if (cudaMemcpyAsync(&hs, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return EMG_ERR_CUDA;
+    if (krylov_dim) *krylov_dim = hs.m_used;
+    if (hs.timeout) return EMG_ERR_TIMEOUT;
+    if (hs.nonfinite) return EMG_ERR_NONFINITE;
+    return EMG_OK;
+}
+
+namespace emg {
 }  // namespace emg
