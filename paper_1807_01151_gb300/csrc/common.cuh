@@ -67,6 +67,8 @@ struct LevelDev {
     float* fpsiL32 = nullptr;
     float* fpsiR32 = nullptr;
     float* blk32 = nullptr;    // [E][B][B]
+    float* fjl32 = nullptr;    // [F][QF][25]  face Jacobians for the FP32 blocks
+    float* fjr32 = nullptr;    // [F_int][QF][25]
 };
 
 // Small device-side scalars of the cycle (no host round trip inside a V-cycle).

@@ -1,8 +1,10 @@
 // Device physics: Euler flux (Eq. euler, omega = 0), Roe flux (Sec. 3.1, Roe 1981,
 // no entropy fix), slip-wall and Riemann-invariant far-field ghost states (Sec. 3.3),
 // all templated on the scalar so that the same code yields values (double) and exact
-// derivatives by forward-mode automatic differentiation (Dual<M>), as the paper does
-// for dF~/dU_L, dF~/dU_R and dU_ghost/dU_L.
+// derivatives by forward-mode automatic differentiation (Dual<M, S>), as the paper does
+// for dF~/dU_L, dF~/dU_R and dU_ghost/dU_L.  S is the dual's base type: double for the
+// FP64 form and for the p = 0 Jacobian, float for the preconditioner blocks of the FP32
+// block form.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -10,87 +12,88 @@
 namespace emg {
 
 // ---- forward-mode dual numbers ------------------------------------------------------
-template <int M>
+template <int M, class S = double>
 struct Dual {
-    double v;
-    double d[M];
+    S v;
+    S d[M];
 };
 
-template <int M>
-__device__ __forceinline__ Dual<M> dconst(double a) {
-    Dual<M> r;
-    r.v = a;
+template <int M, class S = double>
+__device__ __forceinline__ Dual<M, S> dconst(double a) {
+    Dual<M, S> r;
+    r.v = (S)a;
 #pragma unroll
-    for (int i = 0; i < M; ++i) r.d[i] = 0.0;
+    for (int i = 0; i < M; ++i) r.d[i] = (S)0;
     return r;
 }
 
-template <int M>
-__device__ __forceinline__ Dual<M> operator+(const Dual<M>& a, const Dual<M>& b) {
-    Dual<M> r;
+template <int M, class S>
+__device__ __forceinline__ Dual<M, S> operator+(const Dual<M, S>& a, const Dual<M, S>& b) {
+    Dual<M, S> r;
     r.v = a.v + b.v;
 #pragma unroll
     for (int i = 0; i < M; ++i) r.d[i] = a.d[i] + b.d[i];
     return r;
 }
-template <int M>
-__device__ __forceinline__ Dual<M> operator-(const Dual<M>& a, const Dual<M>& b) {
-    Dual<M> r;
+template <int M, class S>
+__device__ __forceinline__ Dual<M, S> operator-(const Dual<M, S>& a, const Dual<M, S>& b) {
+    Dual<M, S> r;
     r.v = a.v - b.v;
 #pragma unroll
     for (int i = 0; i < M; ++i) r.d[i] = a.d[i] - b.d[i];
     return r;
 }
-template <int M>
-__device__ __forceinline__ Dual<M> operator-(const Dual<M>& a) {
-    Dual<M> r;
+template <int M, class S>
+__device__ __forceinline__ Dual<M, S> operator-(const Dual<M, S>& a) {
+    Dual<M, S> r;
     r.v = -a.v;
 #pragma unroll
     for (int i = 0; i < M; ++i) r.d[i] = -a.d[i];
     return r;
 }
-template <int M>
-__device__ __forceinline__ Dual<M> operator*(const Dual<M>& a, const Dual<M>& b) {
-    Dual<M> r;
+template <int M, class S>
+__device__ __forceinline__ Dual<M, S> operator*(const Dual<M, S>& a, const Dual<M, S>& b) {
+    Dual<M, S> r;
     r.v = a.v * b.v;
 #pragma unroll
     for (int i = 0; i < M; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
     return r;
 }
-template <int M>
-__device__ __forceinline__ Dual<M> operator/(const Dual<M>& a, const Dual<M>& b) {
-    Dual<M> r;
-    const double ib = 1.0 / b.v;
+template <int M, class S>
+__device__ __forceinline__ Dual<M, S> operator/(const Dual<M, S>& a, const Dual<M, S>& b) {
+    Dual<M, S> r;
+    const S ib = (S)1 / b.v;
     r.v = a.v * ib;
 #pragma unroll
     for (int i = 0; i < M; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
     return r;
 }
-template <int M>
-__device__ __forceinline__ Dual<M> operator*(double a, const Dual<M>& b) {
-    Dual<M> r;
-    r.v = a * b.v;
+template <int M, class S>
+__device__ __forceinline__ Dual<M, S> operator*(double a, const Dual<M, S>& b) {
+    Dual<M, S> r;
+    const S s = (S)a;
+    r.v = s * b.v;
 #pragma unroll
-    for (int i = 0; i < M; ++i) r.d[i] = a * b.d[i];
+    for (int i = 0; i < M; ++i) r.d[i] = s * b.d[i];
     return r;
 }
-template <int M>
-__device__ __forceinline__ Dual<M> operator*(const Dual<M>& b, double a) { return a * b; }
-template <int M>
-__device__ __forceinline__ Dual<M> operator+(const Dual<M>& b, double a) {
-    Dual<M> r = b;
-    r.v += a;
+template <int M, class S>
+__device__ __forceinline__ Dual<M, S> operator*(const Dual<M, S>& b, double a) { return a * b; }
+template <int M, class S>
+__device__ __forceinline__ Dual<M, S> operator+(const Dual<M, S>& b, double a) {
+    Dual<M, S> r = b;
+    r.v += (S)a;
     return r;
 }
-template <int M>
-__device__ __forceinline__ Dual<M> operator-(const Dual<M>& b, double a) {
-    Dual<M> r = b;
-    r.v -= a;
+template <int M, class S>
+__device__ __forceinline__ Dual<M, S> operator-(const Dual<M, S>& b, double a) {
+    Dual<M, S> r = b;
+    r.v -= (S)a;
     return r;
 }
-template <int M>
-__device__ __forceinline__ Dual<M> operator-(double a, const Dual<M>& b) {
-    return dconst<M>(a) - b;
+template <int M, class S>
+__device__ __forceinline__ Dual<M, S> operator-(double a, const Dual<M, S>& b) {
+    return dconst<M, S>(a) - b;
 }
 
 __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
@@ -99,36 +102,36 @@ __device__ __forceinline__ double powr_(double a, double e) { return pow(a, e); 
 __device__ __forceinline__ double val(double a) { return a; }
 __device__ __forceinline__ double inv_(double a) { return 1.0 / a; }
 
-template <int M>
-__device__ __forceinline__ Dual<M> sqrt_(const Dual<M>& a) {
-    Dual<M> r;
+template <int M, class S>
+__device__ __forceinline__ Dual<M, S> sqrt_(const Dual<M, S>& a) {
+    Dual<M, S> r;
     r.v = sqrt(a.v);
-    const double h = 0.5 / r.v;
+    const S h = (S)0.5 / r.v;
 #pragma unroll
     for (int i = 0; i < M; ++i) r.d[i] = a.d[i] * h;
     return r;
 }
 // |x| with d|x|/dx = sign(x), sign(0) = +1 (matches the analytic continuation x*sign(Re x)).
-template <int M>
-__device__ __forceinline__ Dual<M> abs_(const Dual<M>& a) {
-    return a.v >= 0.0 ? a : -a;
+template <int M, class S>
+__device__ __forceinline__ Dual<M, S> abs_(const Dual<M, S>& a) {
+    return a.v >= (S)0 ? a : -a;
 }
-template <int M>
-__device__ __forceinline__ Dual<M> powr_(const Dual<M>& a, double e) {
-    Dual<M> r;
-    r.v = pow(a.v, e);
-    const double g = e * r.v / a.v;
+template <int M, class S>
+__device__ __forceinline__ Dual<M, S> powr_(const Dual<M, S>& a, double e) {
+    Dual<M, S> r;
+    r.v = pow(a.v, (S)e);
+    const S g = (S)e * r.v / a.v;
 #pragma unroll
     for (int i = 0; i < M; ++i) r.d[i] = a.d[i] * g;
     return r;
 }
-template <int M>
-__device__ __forceinline__ double val(const Dual<M>& a) { return a.v; }
-template <int M>
-__device__ __forceinline__ Dual<M> inv_(const Dual<M>& a) { return dconst<M>(1.0) / a; }
+template <int M, class S>
+__device__ __forceinline__ double val(const Dual<M, S>& a) { return (double)a.v; }
+template <int M, class S>
+__device__ __forceinline__ Dual<M, S> inv_(const Dual<M, S>& a) { return dconst<M, S>(1.0) / a; }
 __device__ __forceinline__ double dconst_like(double, double a) { return a; }
-template <int M>
-__device__ __forceinline__ Dual<M> dconst_like(const Dual<M>&, double a) { return dconst<M>(a); }
+template <int M, class S>
+__device__ __forceinline__ Dual<M, S> dconst_like(const Dual<M, S>&, double a) { return dconst<M, S>(a); }
 
 // ---- Euler ----------------------------------------------------------------------------
 // U = (rho, rho u, rho v, rho w, rho E); n has three components (n_z = 0 in 2-D).

@@ -18,67 +18,67 @@
 
 namespace emg {
 
-template <int D, int P>
+template <int D, int P, class S>
 __global__ void __launch_bounds__(128) k_face_jac(int F, int F_int, const int* __restrict__ fL,
                                                   const int* __restrict__ fR, const int* __restrict__ fbc,
                                                   const double* __restrict__ fnrm,
                                                   const double* __restrict__ famag,
-                                                  const double* __restrict__ fpsiL,
-                                                  const double* __restrict__ fpsiR,
+                                                  const S* __restrict__ fpsiL,
+                                                  const S* __restrict__ fpsiR,
                                                   const double* __restrict__ fwn,
                                                   const double* __restrict__ u, double g, U5 uinf,
-                                                  double* __restrict__ fjl, double* __restrict__ fjr) {
+                                                  S* __restrict__ fjl, S* __restrict__ fjr) {
     using L = Lv<D, P>;
     constexpr int N = L::N, QF = L::QF;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)F * QF) return;
     const int f = (int)(idx / QF);
     const double n[3] = {fnrm[idx * 3], fnrm[idx * 3 + 1], fnrm[idx * 3 + 2]};
-    const double am = famag[idx];
-    double UL[5], UR[5];
+    const S am = (S)famag[idx];
+    S UL[5];
     {
         const double* ue = u + (size_t)fL[f] * 5 * N;
-        const double* ps = fpsiL + idx * N;
+        const S* ps = fpsiL + idx * N;
         for (int a = 0; a < 5; ++a) {
-            double s = 0.0;
-            for (int i = 0; i < N; ++i) s += ue[a * N + i] * ps[i];
+            S s = (S)0;
+            for (int i = 0; i < N; ++i) s += (S)ue[a * N + i] * ps[i];
             UL[a] = s;
         }
     }
-    Dual<5> dL[5], dR[5], Fd[5];
+    Dual<5, S> dL[5], dR[5], Fd[5];
     for (int a = 0; a < 5; ++a) {
-        dL[a] = dconst<5>(UL[a]);
-        dL[a].d[a] = 1.0;
+        dL[a] = dconst<5, S>(UL[a]);
+        dL[a].d[a] = (S)1;
     }
     if (f < F_int) {
         const double* ur = u + (size_t)fR[f] * 5 * N;
-        const double* pr = fpsiR + idx * N;
+        const S* pr = fpsiR + idx * N;
+        S UR[5];
         for (int a = 0; a < 5; ++a) {
-            double s = 0.0;
-            for (int i = 0; i < N; ++i) s += ur[a * N + i] * pr[i];
+            S s = (S)0;
+            for (int i = 0; i < N; ++i) s += (S)ur[a * N + i] * pr[i];
             UR[a] = s;
-            dR[a] = dconst<5>(s);
+            dR[a] = dconst<5, S>(s);
         }
         roe_flux(dL, dR, n, g, Fd);
         for (int a = 0; a < 5; ++a)
             for (int b = 0; b < 5; ++b) fjl[idx * 25 + a * 5 + b] = am * Fd[a].d[b];
-        Dual<5> cL[5];
+        Dual<5, S> cL[5];
         for (int a = 0; a < 5; ++a) {
-            cL[a] = dconst<5>(UL[a]);
-            dR[a].d[a] = 1.0;
+            cL[a] = dconst<5, S>(UL[a]);
+            dR[a].d[a] = (S)1;
         }
         roe_flux(cL, dR, n, g, Fd);
         for (int a = 0; a < 5; ++a)
             for (int b = 0; b < 5; ++b) fjr[idx * 25 + a * 5 + b] = am * Fd[a].d[b];
     } else {
-        if (fbc[f] == EMG_BC_WALL)
-        {
+        if (fbc[f] == EMG_BC_WALL) {
             const int64_t bi = idx - (int64_t)F_int * QF;
             const double nw[3] = {fwn[bi * 3], fwn[bi * 3 + 1], fwn[bi * 3 + 2]};
             wall_ghost(dL, nw, dR);
-        }
-        else
+        } else {
             farfield_ghost(dL, n, uinf.v, g, dR);
+        }
         roe_flux(dL, dR, n, g, Fd);
         for (int a = 0; a < 5; ++a)
             for (int b = 0; b < 5; ++b) fjl[idx * 25 + a * 5 + b] = am * Fd[a].d[b];
@@ -141,7 +141,7 @@ __device__ __forceinline__ void flux_jac_k(const float U[5], float g, int k, flo
 
 template <int D, int P>
 struct DiagCfg {
-    static constexpr int QC = 32;  // volume points per shared-memory chunk
+    static constexpr int QC = D == 2 ? 32 : 16;  // volume points per shared-memory chunk
     static constexpr int THREADS = ((25 * Lv<D, P>::N + 31) / 32) * 32;
 };
 
@@ -152,7 +152,7 @@ template <int D, int P, class T>
 __global__ void __launch_bounds__(DiagCfg<D, P>::THREADS) k_diag_blocks(
     int E, int nmax, const double* __restrict__ u, const T* __restrict__ vpsi, const T* __restrict__ vgw,
     const int* __restrict__ elem_face, const T* __restrict__ fpsiL, const T* __restrict__ fpsiR,
-    const double* __restrict__ fjl, const double* __restrict__ fjr, const double* __restrict__ psic,
+    const T* __restrict__ fjl, const T* __restrict__ fjr, const double* __restrict__ psic,
     const double* __restrict__ hlen, const double* __restrict__ cfl_dev, double g, int shifted,
     T* __restrict__ out) {
     using L = Lv<D, P>;
@@ -162,6 +162,10 @@ __global__ void __launch_bounds__(DiagCfg<D, P>::THREADS) k_diag_blocks(
     __shared__ T us[B];
     __shared__ T As[QC][D][25];
     __shared__ T ps[QC][N];
+    __shared__ T gs[QC][D][N];
+    __shared__ T Us[QC][5];
+    __shared__ T fps[QF][N];
+    __shared__ T fjs[QF][25];
     __shared__ double s_dtau;
     const int e = blockIdx.x;
     const int tid = threadIdx.x;
@@ -195,43 +199,50 @@ __global__ void __launch_bounds__(DiagCfg<D, P>::THREADS) k_diag_blocks(
         for (int q0 = 0; q0 < Q; q0 += QC) {
             const int nq = (Q - q0) < QC ? (Q - q0) : QC;
             __syncthreads();
-            for (int t = tid; t < nq; t += blockDim.x) {
-                const T* pq = vpsi + ((size_t)e * Q + q0 + t) * N;
-                T U[5];
-                for (int c = 0; c < 5; ++c) {
-                    T s = (T)0;
-                    for (int m = 0; m < N; ++m) s += us[c * N + m] * pq[m];
-                    U[c] = s;
-                }
-                for (int k = 0; k < D; ++k) flux_jac_k(U, (T)g, k, As[t][k]);
+            // stage the chunk's psi and W grad psi, and build U at its points (all threads)
+            const T* pg = vpsi + ((size_t)e * Q + q0) * N;
+            for (int t = tid; t < nq * N; t += blockDim.x) ps[t / N][t % N] = pg[t];
+            for (int t = tid; t < D * nq * N; t += blockDim.x) {
+                const int k = t / (nq * N), r = t % (nq * N);
+                gs[r / N][k][r % N] = vgw[(((size_t)e * D + k) * Q + q0) * N + r];
             }
-            for (int t = tid; t < nq * N; t += blockDim.x) ps[t / N][t % N] = vpsi[((size_t)e * Q + q0) * N + t];
+            for (int t = tid; t < nq * 5; t += blockDim.x) {
+                const int q = t / 5, c = t % 5;
+                const T* pq = pg + (size_t)q * N;
+                T s = (T)0;
+                for (int m = 0; m < N; ++m) s += us[c * N + m] * pq[m];
+                Us[q][c] = s;
+            }
+            __syncthreads();
+            for (int t = tid; t < nq * D; t += blockDim.x) flux_jac_k(Us[t / D], (T)g, t % D, As[t / D][t % D]);
             __syncthreads();
             if (active) {
                 for (int t = 0; t < nq; ++t) {
                     T s = (T)0;
 #pragma unroll
-                    for (int k = 0; k < D; ++k) s += vgw[(((size_t)e * D + k) * Q + q0 + t) * N + i] * As[t][k][ab];
+                    for (int k = 0; k < D; ++k) s += gs[t][k][i] * As[t][k][ab];
 #pragma unroll
                     for (int j = 0; j < N; ++j) acc[j] += s * ps[t][j];
                 }
             }
         }
     }
-    if (active) {
-#pragma unroll
-        for (int lf = 0; lf < NF; ++lf) {
-            const int code = elem_face[(size_t)e * NF + lf];
-            const int f = code >> 1;
-            const bool rside = code & 1;
-            const T* pt = rside ? fpsiR : fpsiL;
-            const double* fj = rside ? fjr : fjl;
-            const T sg = rside ? (T)1 : (T)-1;
+    // faces, one at a time: stage psi at its points and the face Jacobians of this
+    // element's side (sign -1 on the L side, +1 on the R side)
+#pragma unroll 1
+    for (int lf = 0; lf < NF; ++lf) {
+        const int code = elem_face[(size_t)e * NF + lf];
+        const T* pt = ((code & 1) ? fpsiR : fpsiL) + ((size_t)(code >> 1) * QF) * N;
+        const T* fj = ((code & 1) ? fjr : fjl) + ((size_t)(code >> 1) * QF) * 25;
+        __syncthreads();
+        for (int t = tid; t < QF * N; t += blockDim.x) fps[t / N][t % N] = pt[t];
+        for (int t = tid; t < QF * 25; t += blockDim.x) fjs[t / 25][t % 25] = (code & 1) ? fj[t] : -fj[t];
+        __syncthreads();
+        if (active) {
             for (int t = 0; t < QF; ++t) {
-                const size_t pidx = (size_t)f * QF + t;
-                const T s = sg * pt[pidx * N + i] * (T)fj[pidx * 25 + ab];
+                const T s = fps[t][i] * fjs[t][ab];
 #pragma unroll
-                for (int j = 0; j < N; ++j) acc[j] += s * pt[pidx * N + j];
+                for (int j = 0; j < N; ++j) acc[j] += s * fps[t][j];
             }
         }
     }
@@ -295,7 +306,7 @@ emg_status launch_face_jacobian(emg_ctx* c, int p, const double* u) {
 #define EMG_FJ(DD, PP)                                                                                       \
     {                                                                                                        \
         const int64_t nf = (int64_t)F * Lv<DD, PP>::QF;                                                      \
-        { ProfScope _ps(c, PC_FACE_JAC); k_face_jac<DD, PP><<<(unsigned)((nf + 127) / 128), 128, 0, c->stream>>>(                             \
+        { ProfScope _ps(c, PC_FACE_JAC); k_face_jac<DD, PP, double><<<(unsigned)((nf + 127) / 128), 128, 0, c->stream>>>(                             \
             F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL, L.fpsiR, L.fwn, u, c->prm.gamma, ui, \
             L.fjl, L.fjr); }                                                                                   \
         EMG_CHECK_LAUNCH(c);                                                                                 \
@@ -323,9 +334,28 @@ emg_status launch_diag_blocks(emg_ctx* c, int p, const double* u, const double* 
     return EMG_OK;
 }
 
+emg_status launch_face_jacobian32(emg_ctx* c, int p, const double* u) {
+    LevelDev& L = c->lv[p];
+    const int F = (int)c->F, Fi = (int)c->F_int;
+    U5 ui;
+    for (int a = 0; a < 5; ++a) ui.v[a] = c->uinf[a];
+#define EMG_FJ32(DD, PP)                                                                                     \
+    {                                                                                                        \
+        const int64_t nf = (int64_t)F * Lv<DD, PP>::QF;                                                      \
+        ProfScope _ps(c, PC_FACE_JAC);                                                                       \
+        k_face_jac<DD, PP, float><<<(unsigned)((nf + 127) / 128), 128, 0, c->stream>>>(                      \
+            F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL32, L.fpsiR32, L.fwn, u,          \
+            c->prm.gamma, ui, L.fjl32, L.fjr32);                                                             \
+    }
+    EMG_DISPATCH_DP(c->dim, p, EMG_FJ32)
+#undef EMG_FJ32
+    EMG_CHECK_LAUNCH(c);
+    return EMG_OK;
+}
+
 emg_status launch_diag_blocks32(emg_ctx* c, int p, const double* u, const double* cfl_dev, int shifted,
                                 float* out) {
-    emg_status st = launch_face_jacobian(c, p, u);
+    emg_status st = launch_face_jacobian32(c, p, u);
     if (st != EMG_OK) return st;
     LevelDev& L = c->lv[p];
     if (!L.vpsi32) {
@@ -337,7 +367,7 @@ emg_status launch_diag_blocks32(emg_ctx* c, int p, const double* u, const double
     {                                                                                                       \
         ProfScope _ps(c, PC_DIAG);                                                                          \
         k_diag_blocks<DD, PP, float><<<(unsigned)c->E, DiagCfg<DD, PP>::THREADS, 0, c->stream>>>(           \
-            (int)c->E, nmax, u, L.vpsi32, L.vgw32, c->elem_face, L.fpsiL32, L.fpsiR32, L.fjl, L.fjr, c->psic, \
+            (int)c->E, nmax, u, L.vpsi32, L.vgw32, c->elem_face, L.fpsiL32, L.fpsiR32, L.fjl32, L.fjr32, c->psic, \
             c->h, cfl_dev, c->prm.gamma, shifted, out);                                                     \
     }
     EMG_DISPATCH_DP(c->dim, p, EMG_DB32)

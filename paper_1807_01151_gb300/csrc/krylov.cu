@@ -44,7 +44,7 @@ __device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned nblocks, long l
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(20);
             }
         }
         __threadfence();
@@ -54,7 +54,18 @@ __device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned nblocks, long l
     return *s_ok != 0;
 }
 
-constexpr int ARN_THREADS = 256;
+constexpr int ARN_THREADS = 512;
+constexpr int ARN_PER_THREAD = 4;   // Krylov entries per thread: few blocks keep the barriers short
+
+// Blocks of the persistent Arnoldi launch: about ARN_PER_THREAD entries per thread, at most
+// what is co-resident (per_sm per SM) and at most `cap`.
+static int64_t arnoldi_blocks(int64_t K0, int nsm, int per_sm, int64_t cap) {
+    int64_t nb = (K0 + (int64_t)ARN_THREADS * ARN_PER_THREAD - 1) / ((int64_t)ARN_THREADS * ARN_PER_THREAD);
+    const int64_t resident = (int64_t)nsm * (per_sm < 1 ? 1 : per_sm);
+    if (nb > resident) nb = resident;
+    if (nb > cap) nb = cap;
+    return nb < 1 ? 1 : nb;
+}
 constexpr int ARN_CHUNK = 8;  // vectors per dot-product sweep
 
 // Block-reduce v[0..n) (n <= ARN_CHUNK) and store into dst[0..n) from thread 0 (fixed order).
@@ -418,11 +429,7 @@ emg_status launch_exp1(emg_ctx* c, const double* u0, const double* tau0, const d
     int per_sm = 0, nsm = 0;
     EMG_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi, ARN_THREADS, 0));
     EMG_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
-    int64_t nb = (int64_t)nsm * (per_sm < 2 ? per_sm : 2);
-    const int64_t need = (K0 + ARN_THREADS - 1) / ARN_THREADS;
-    if (nb > need) nb = need;
-    if (nb > c->red_blocks) nb = c->red_blocks;
-    if (nb < 1) nb = 1;
+    const int64_t nb = arnoldi_blocks(K0, nsm, per_sm, c->red_blocks);
     const int stride = MAX_KRYLOV + 8;
     double* partA = c->partial;
     double* partB = partA + (size_t)c->red_blocks * stride;
@@ -545,11 +552,7 @@ extern "C" emg_status emg_exp1_step_noalloc(int32_t dim, int64_t n_elems, const 
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi, ARN_THREADS, 0) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return EMG_ERR_CUDA;
-    int64_t nb = (int64_t)nsm * (per_sm < 2 ? per_sm : 2);
-    const int64_t need = (K0 + ARN_THREADS - 1) / ARN_THREADS;
-    if (nb > need) nb = need;
-    if (nb > NA_BLOCKS) nb = NA_BLOCKS;
-    if (nb < 1) nb = 1;
+    const int64_t nb = arnoldi_blocks(K0, nsm, per_sm, NA_BLOCKS);
     int64_t K0a = K0;
     int Ea = (int)E, NFa = NF, ma = krylov_m, stra = NA_STRIDE;
     const double* bsrc = bsr;

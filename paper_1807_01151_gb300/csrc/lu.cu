@@ -63,10 +63,11 @@ __global__ void __launch_bounds__(256) k_lu(int E, T* __restrict__ blk, int* __r
         const T inv = (T)1 / a[k * LD + k];
         for (int r = k + 1 + tid; r < B; r += nth) a[r * LD + k] *= inv;
         __syncthreads();
-        const int m = B - k - 1;
-        for (int t = tid; t < m * m; t += nth) {
-            const int r = k + 1 + t / m, cc = k + 1 + t % m;
-            a[r * LD + cc] -= a[r * LD + k] * a[k * LD + cc];
+        // trailing update on a 32-wide column x 8-row thread grid (no index division)
+        const int tx = tid & 31, ty = tid >> 5;
+        for (int r = k + 1 + ty; r < B; r += 8) {
+            const T l = a[r * LD + k];
+            for (int cc = k + 1 + tx; cc < B; cc += 32) a[r * LD + cc] -= l * a[k * LD + cc];
         }
         __syncthreads();
     }
@@ -116,6 +117,124 @@ __global__ void __launch_bounds__(128) k_stage(int E, const T* __restrict__ lu, 
         __syncwarp();
     }
     for (int t = lane; t < B; t += 32) out[(size_t)e * B + t] = un[(size_t)e * B + t] + beta * (double)y[t];
+}
+
+// In-place Gauss-Jordan inversion with partial pivoting of every block (FP32 block form):
+// P_e^{-1} is written column-major, so that each PRK stage is a batched matrix-vector
+// product that streams the inverse once (k_stage_gemv), instead of two dependent
+// triangular sweeps.  Thread grid: 32 columns x 8 rows, no index division.
+template <int B, class T>
+__global__ void __launch_bounds__(256) k_gj_inverse(int E, T* __restrict__ blk) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* a = reinterpret_cast<T*>(smraw);
+    constexpr int LD = LuCfg<B, T>::LD;
+    __shared__ int s_piv;
+    __shared__ int ipiv[B];
+    __shared__ T fcol[B];
+    const int e = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int tx = tid & 31, ty = tid >> 5;
+    T* g = blk + (size_t)e * B * B;
+    for (int t = tid; t < B * B; t += 256) a[(t / B) * LD + (t % B)] = g[t];
+    __syncthreads();
+    for (int k = 0; k < B; ++k) {
+        if (tid < 32) {
+            T best = (T)-1;
+            int bi = k;
+            for (int r = k + tid; r < B; r += 32) {
+                const T v = fabs(a[r * LD + k]);
+                if (v > best) {
+                    best = v;
+                    bi = r;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (tid == 0) {
+                s_piv = bi;
+                ipiv[k] = bi;
+            }
+        }
+        __syncthreads();
+        const int pr = s_piv;
+        if (pr != k)
+            for (int cc = tid; cc < B; cc += 256) {
+                const T t0 = a[k * LD + cc];
+                a[k * LD + cc] = a[pr * LD + cc];
+                a[pr * LD + cc] = t0;
+            }
+        __syncthreads();
+        const T inv = (T)1 / a[k * LD + k];
+        // factors of column k (zero on the pivot row), then the scaled pivot row
+        for (int r = tid; r < B; r += 256) fcol[r] = r == k ? (T)0 : a[r * LD + k];
+        __syncthreads();
+        for (int cc = tid; cc < B; cc += 256) a[k * LD + cc] = cc == k ? inv : a[k * LD + cc] * inv;
+        __syncthreads();
+        for (int r = ty; r < B; r += 8) {
+            if (r == k) continue;
+            const T f = fcol[r];
+            for (int cc = tx; cc < B; cc += 32) {
+                const T base = cc == k ? (T)0 : a[r * LD + cc];
+                a[r * LD + cc] = base - f * a[k * LD + cc];
+            }
+        }
+        __syncthreads();
+    }
+    // undo the row interchanges as column interchanges, last first
+    for (int k = B - 1; k >= 0; --k) {
+        const int p = ipiv[k];
+        if (p != k)
+            for (int r = tid; r < B; r += 256) {
+                const T t0 = a[r * LD + k];
+                a[r * LD + k] = a[r * LD + p];
+                a[r * LD + p] = t0;
+            }
+        __syncthreads();
+    }
+    for (int t = tid; t < B * B; t += 256) {
+        const int cc = t / B, r = t % B;
+        g[t] = a[r * LD + cc];   // column-major
+    }
+}
+
+// u^(k) = u^n + beta P_e^{-1} r_e with P_e^{-1} column-major: one warp per element, each
+// lane owns rows lane, lane+32, ...; every column is a coalesced read.
+template <int B, class T>
+__global__ void __launch_bounds__(128) k_stage_gemv(int E, const T* __restrict__ inv, const double* __restrict__ r,
+                                                    const double* __restrict__ un, double beta,
+                                                    double* __restrict__ out) {
+    constexpr int RPL = (B + 31) / 32;
+    __shared__ T rs[4][B];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int e = blockIdx.x * 4 + warp;
+    if (e >= E) return;
+    for (int t = lane; t < B; t += 32) rs[warp][t] = (T)r[(size_t)e * B + t];
+    __syncwarp();
+    T acc[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) acc[t] = (T)0;
+    const T* M = inv + (size_t)e * B * B;
+#pragma unroll 4
+    for (int j = 0; j < B; ++j) {
+        const T rj = rs[warp][j];
+        const T* col = M + (size_t)j * B;
+#pragma unroll
+        for (int t = 0; t < RPL; ++t) {
+            const int i = lane + 32 * t;
+            if (i < B) acc[t] += __ldg(col + i) * rj;
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+        const int i = lane + 32 * t;
+        if (i < B) out[(size_t)e * B + i] = un[(size_t)e * B + i] + beta * (double)acc[t];
+    }
 }
 
 #define EMG_BSIZES(X) X(15) X(30) X(50) X(75) X(20) X(100) X(175)
@@ -169,7 +288,30 @@ static emg_status stage_dispatch(emg_ctx* c, int B, const T* lu, const int* piv,
 
 emg_status launch_lu(emg_ctx* c, int p) { return lu_dispatch<double>(c, c->lv[p].B, c->lv[p].blk, c->lv[p].piv); }
 
-emg_status launch_lu32(emg_ctx* c, int p) { return lu_dispatch<float>(c, c->lv[p].B, c->lv[p].blk32, c->lv[p].piv); }
+// FP32 block form: explicit inverse (Gauss-Jordan), applied by k_stage_gemv.
+emg_status launch_lu32(emg_ctx* c, int p) {
+    LevelDev& L = c->lv[p];
+    const unsigned E = (unsigned)c->E;
+    switch (L.B) {
+#define EMG_GJ_CASE(BB)                                                                                      \
+    case BB: {                                                                                               \
+        const size_t sm = LuCfg<BB, float>::SMEM;                                                            \
+        EMG_CUDA_TRY(c, cudaFuncSetAttribute(k_gj_inverse<BB, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)sm));                                                      \
+        {                                                                                                    \
+            ProfScope _ps(c, PC_LU);                                                                         \
+            k_gj_inverse<BB, float><<<E, 256, sm, c->stream>>>((int)E, L.blk32);                             \
+        }                                                                                                    \
+        EMG_CHECK_LAUNCH(c);                                                                                 \
+        return EMG_OK;                                                                                       \
+    }
+        EMG_BSIZES(EMG_GJ_CASE)
+#undef EMG_GJ_CASE
+        default:
+            c->err = "unsupported block size";
+            return EMG_ERR_ARG;
+    }
+}
 
 emg_status launch_stage(emg_ctx* c, int p, const double* r, const double* un, double beta, double* out) {
     LevelDev& L = c->lv[p];
@@ -178,7 +320,21 @@ emg_status launch_stage(emg_ctx* c, int p, const double* r, const double* un, do
 
 emg_status launch_stage32(emg_ctx* c, int p, const double* r, const double* un, double beta, double* out) {
     LevelDev& L = c->lv[p];
-    return stage_dispatch<float>(c, L.B, L.blk32, L.piv, r, un, beta, out);
+    const unsigned E = (unsigned)c->E;
+    switch (L.B) {
+#define EMG_GV_CASE(BB)                                                                                  \
+    case BB: {                                                                                           \
+        ProfScope _ps(c, PC_STAGE);                                                                      \
+        k_stage_gemv<BB, float><<<(E + 3) / 4, 128, 0, c->stream>>>((int)E, L.blk32, r, un, beta, out);  \
+    }                                                                                                    \
+        EMG_CHECK_LAUNCH(c);                                                                             \
+        return EMG_OK;
+        EMG_BSIZES(EMG_GV_CASE)
+#undef EMG_GV_CASE
+        default:
+            c->err = "unsupported block size";
+            return EMG_ERR_ARG;
+    }
 }
 
 }  // namespace emg

@@ -581,6 +581,8 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
                 EMG_ALLOC(L.vgw32, float, E * D * L.Q * L.N);
                 EMG_ALLOC(L.fpsiL32, float, F * L.QF * L.N);
                 EMG_ALLOC(L.fpsiR32, float, std::max<int64_t>(F_int, 1) * L.QF * L.N);
+                EMG_ALLOC(L.fjl32, float, F * L.QF * 25);
+                EMG_ALLOC(L.fjr32, float, std::max<int64_t>(F_int, 1) * L.QF * 25);
             } else {
                 EMG_ALLOC(L.blk, double, E * L.B * L.B);
             }
