@@ -54,8 +54,8 @@ __device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned nblocks, long l
     return *s_ok != 0;
 }
 
-constexpr int ARN_THREADS = 512;
-constexpr int ARN_PER_THREAD = 4;   // Krylov entries per thread: few blocks keep the barriers short
+constexpr int ARN_THREADS = 256;
+constexpr int ARN_PER_THREAD = 1;   // spread the FP64 work over every SM (FP64 is slow per SM)
 
 // Blocks of the persistent Arnoldi launch: about ARN_PER_THREAD entries per thread, at most
 // what is co-resident (per_sm per SM) and at most `cap`.
@@ -68,9 +68,14 @@ static int64_t arnoldi_blocks(int64_t K0, int nsm, int per_sm, int64_t cap) {
 }
 constexpr int ARN_CHUNK = 8;  // vectors per dot-product sweep
 
-// Block-reduce v[0..n) (n <= ARN_CHUNK) and store into dst[0..n) from thread 0 (fixed order).
+constexpr int ARN_MAXCOL = MAX_KRYLOV + 8;
+constexpr int ARN_WARPS = ARN_THREADS / 32;
+constexpr int ARN_SUB = 8;    // threads per column in the cross-block reduction
+
+// Block-reduce v[0..n) (n <= ARN_CHUNK): warp shuffles, then one barrier; dst[0..n) from
+// threads 0..n-1 (fixed order).
 __device__ __forceinline__ void block_reduce_store(double v[ARN_CHUNK], int n, double* dst,
-                                                   double (*sh)[ARN_CHUNK]) {
+                                                   double (*sh)[ARN_MAXCOL]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int i = 0; i < ARN_CHUNK; ++i) {
@@ -81,33 +86,34 @@ __device__ __forceinline__ void block_reduce_store(double v[ARN_CHUNK], int n, d
     __syncthreads();
     if (threadIdx.x < n) {
         double s = 0.0;
-        for (int w = 0; w < ARN_THREADS / 32; ++w) s += sh[w][threadIdx.x];
+        for (int w = 0; w < ARN_WARPS; ++w) s += sh[w][threadIdx.x];
         dst[threadIdx.x] = s;
     }
     __syncthreads();
 }
 
-// sum over blocks of part[b * stride + col], identical order in every block; result to all threads
+// out_sh[c] = sum over blocks b of part[b * stride + c], c < ncol, identical in every block:
+// ARN_SUB threads per column sum a fixed stride of blocks, then a fixed shuffle tree.
 __device__ __forceinline__ void reduce_cols(const double* part, int nb, int stride, int ncol, double* out_sh,
-                                            double (*sh)[ARN_CHUNK]) {
-    for (int c0 = 0; c0 < ncol; c0 += ARN_CHUNK) {
-        double v[ARN_CHUNK];
-#pragma unroll
-        for (int i = 0; i < ARN_CHUNK; ++i) v[i] = 0.0;
-        for (int b = threadIdx.x; b < nb; b += ARN_THREADS) {
-#pragma unroll
-            for (int i = 0; i < ARN_CHUNK; ++i)
-                if (c0 + i < ncol) v[i] += __ldcg(part + (size_t)b * stride + c0 + i);   // other blocks' data: L2
-        }
-        const int n = ncol - c0 < ARN_CHUNK ? ncol - c0 : ARN_CHUNK;
-        block_reduce_store(v, n, out_sh + c0, sh);
+                                            double (*sh)[ARN_MAXCOL]) {
+    const int sub = threadIdx.x % ARN_SUB;
+    for (int c0 = 0; c0 < ncol; c0 += ARN_THREADS / ARN_SUB) {
+        const int c = c0 + threadIdx.x / ARN_SUB;
+        double v = 0.0;
+        if (c < ncol)
+            for (int b = sub; b < nb; b += ARN_SUB) v += __ldcg(part + (size_t)b * stride + c);   // other blocks: L2
+        for (int o = ARN_SUB / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, ARN_SUB);
+        if (sub == 0 && c < ncol) out_sh[c] = v;
     }
+    __syncthreads();
 }
 
-// dots[i] (i < nv) = V[i] . w over this block's slice, plus w . w at index nv if with_ww
+// dst[i] (i < nv) = V[i] . w over this block's slice, plus w . w at index nv if with_ww
+// (warp shuffles per chunk of columns, one barrier for all of them).
 __device__ __forceinline__ void slice_dots(const double* V, const double* w, int64_t K0, int64_t k0, int64_t k1,
-                                           int nv, int with_ww, double* dst, double (*sh)[ARN_CHUNK]) {
+                                           int nv, int with_ww, double* dst, double (*sh)[ARN_MAXCOL]) {
     const int ncol = nv + with_ww;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int c0 = 0; c0 < ncol; c0 += ARN_CHUNK) {
         double v[ARN_CHUNK];
 #pragma unroll
@@ -121,8 +127,18 @@ __device__ __forceinline__ void slice_dots(const double* V, const double* w, int
                 else if (col == nv && with_ww) v[i] += wk * wk;
             }
         }
-        const int n = ncol - c0 < ARN_CHUNK ? ncol - c0 : ARN_CHUNK;
-        block_reduce_store(v, n, dst + c0, sh);
+#pragma unroll
+        for (int i = 0; i < ARN_CHUNK; ++i) {
+            double x = v[i];
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0 && c0 + i < ncol) sh[warp][c0 + i] = x;
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncol; c += ARN_THREADS) {
+        double s = 0.0;
+        for (int wv = 0; wv < ARN_WARPS; ++wv) s += sh[wv][c];
+        dst[c] = s;
     }
 }
 
@@ -133,8 +149,8 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
                                                          double* __restrict__ H, double* __restrict__ partA,
                                                          double* __restrict__ partB, double* __restrict__ partC,
                                                          int stride, GridBar* bar, long long budget, DevScalars* sc) {
-    __shared__ double sh[ARN_THREADS / 32][ARN_CHUNK];
-    __shared__ double h1[MAX_KRYLOV + 8], h2[MAX_KRYLOV + 8], red[8];
+    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
+    __shared__ double h1[ARN_MAXCOL], h2[ARN_MAXCOL], red[8];
     __shared__ int s_ok;
     const unsigned nb = gridDim.x;
     const int64_t chunk = (K0 + nb - 1) / nb;

@@ -203,6 +203,191 @@ __global__ void __launch_bounds__(256) k_gj_inverse(int E, T* __restrict__ blk) 
     }
 }
 
+// Register-tiled Gauss-Jordan inversion with partial pivoting (FP32 block form).
+// 256 threads = 32 (tx) x 8 (ty); thread (tx, ty) keeps rows ty + 8i and columns
+// tx + 32j of the block in registers for the whole elimination.  Per pivot step only the
+// pivot column (colk), the scaled pivot row (rowk) and, on a row interchange, the two
+// swapped rows pass through shared memory.  The inverse is written column-major through
+// a transposing shared tile so that the global stores are coalesced.
+template <int B>
+struct GjTile {
+    static constexpr int RS = (B + 7) / 8;    // row slots per thread
+    static constexpr int CS = (B + 31) / 32;  // column slots per thread
+    static constexpr int LD = (B % 2) ? B + 2 : B + 1;   // odd stride of the output tile
+    static constexpr size_t SMEM = (size_t)B * LD * sizeof(float);
+};
+
+template <int B>
+__global__ void __launch_bounds__(256) k_gj_tile(int E, float* __restrict__ blk) {
+    constexpr int RS = GjTile<B>::RS, CS = GjTile<B>::CS, LD = GjTile<B>::LD;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float* tile = reinterpret_cast<float*>(smraw);
+    __shared__ float colk[B], rowk[B], rowx[B], rowy[B];
+    __shared__ int s_p;
+    __shared__ int ipiv[B], colidx[B], pos[B];
+    const int e = blockIdx.x;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    float* g = blk + (size_t)e * B * B;
+    float a[RS][CS];
+#pragma unroll
+    for (int i = 0; i < RS; ++i)
+#pragma unroll
+        for (int j = 0; j < CS; ++j) {
+            const int r = ty + 8 * i, c = tx + 32 * j;
+            a[i][j] = (r < B && c < B) ? g[r * B + c] : 0.0f;
+        }
+    for (int k = 0; k < B; ++k) {
+        const int ki = k >> 3, kj = k >> 5;
+        // (1) the pivot column, from the lane that owns column k in every warp
+        if (tx == (k & 31)) {
+#pragma unroll
+            for (int i = 0; i < RS; ++i) {
+                const int r = ty + 8 * i;
+                float v = 0.0f;
+#pragma unroll
+                for (int j = 0; j < CS; ++j)
+                    if (j == kj) v = a[i][j];
+                if (r < B) colk[r] = v;
+            }
+        }
+        __syncthreads();
+        // (2) pivot: largest |colk[r]|, r >= k, lowest index on ties
+        if (threadIdx.x < 32) {
+            float best = -1.0f;
+            int bi = k;
+            for (int r = k + tx; r < B; r += 32) {
+                const float v = fabsf(colk[r]);
+                if (v > best) {
+                    best = v;
+                    bi = r;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (tx == 0) {
+                s_p = bi;
+                ipiv[k] = bi;
+            }
+        }
+        __syncthreads();
+        const int p = s_p;
+        // (3) interchange rows k and p
+        if (p != k) {
+            const int pi = p >> 3;
+            if (ty == (k & 7)) {
+#pragma unroll
+                for (int j = 0; j < CS; ++j) {
+                    float v = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < RS; ++i)
+                        if (i == ki) v = a[i][j];
+                    const int c = tx + 32 * j;
+                    if (c < B) rowx[c] = v;
+                }
+            }
+            if (ty == (p & 7)) {
+#pragma unroll
+                for (int j = 0; j < CS; ++j) {
+                    float v = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < RS; ++i)
+                        if (i == pi) v = a[i][j];
+                    const int c = tx + 32 * j;
+                    if (c < B) rowy[c] = v;
+                }
+            }
+            if (threadIdx.x == 0) {
+                const float t0 = colk[k];
+                colk[k] = colk[p];
+                colk[p] = t0;
+            }
+            __syncthreads();
+            if (ty == (k & 7)) {
+#pragma unroll
+                for (int j = 0; j < CS; ++j) {
+                    const int c = tx + 32 * j;
+                    const float v = c < B ? rowy[c] : 0.0f;
+#pragma unroll
+                    for (int i = 0; i < RS; ++i)
+                        if (i == ki) a[i][j] = v;
+                }
+            }
+            if (ty == (p & 7)) {
+#pragma unroll
+                for (int j = 0; j < CS; ++j) {
+                    const int c = tx + 32 * j;
+                    const float v = c < B ? rowx[c] : 0.0f;
+#pragma unroll
+                    for (int i = 0; i < RS; ++i)
+                        if (i == pi) a[i][j] = v;
+                }
+            }
+        }
+        // (4) the scaled pivot row (in-place Gauss-Jordan: column k becomes the inverse's)
+        const float inv = 1.0f / colk[k];
+        if (ty == (k & 7)) {
+#pragma unroll
+            for (int j = 0; j < CS; ++j) {
+                float v = 0.0f;
+#pragma unroll
+                for (int i = 0; i < RS; ++i)
+                    if (i == ki) v = a[i][j];
+                const int c = tx + 32 * j;
+                if (c < B) rowk[c] = (c == k ? 1.0f : v) * inv;
+            }
+        }
+        __syncthreads();
+        // (5) eliminate column k from every other row
+#pragma unroll
+        for (int i = 0; i < RS; ++i) {
+            const int r = ty + 8 * i;
+            if (r >= B) continue;
+            if (r == k) {
+#pragma unroll
+                for (int j = 0; j < CS; ++j) {
+                    const int c = tx + 32 * j;
+                    if (c < B) a[i][j] = rowk[c];
+                }
+            } else {
+                const float f = colk[r];
+#pragma unroll
+                for (int j = 0; j < CS; ++j) {
+                    const int c = tx + 32 * j;
+                    if (c < B) a[i][j] = (c == k ? 0.0f : a[i][j]) - f * rowk[c];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // Undo the row interchanges as column interchanges in reverse order: position j of the
+    // inverse holds working column colidx[j]; thread-owned column c goes to pos[c].
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < B; ++j) colidx[j] = j;
+        for (int k = B - 1; k >= 0; --k) {
+            const int t0 = colidx[k];
+            colidx[k] = colidx[ipiv[k]];
+            colidx[ipiv[k]] = t0;
+        }
+        for (int j = 0; j < B; ++j) pos[colidx[j]] = j;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RS; ++i)
+#pragma unroll
+        for (int j = 0; j < CS; ++j) {
+            const int r = ty + 8 * i, c = tx + 32 * j;
+            if (r < B && c < B) tile[pos[c] * LD + r] = a[i][j];
+        }
+    __syncthreads();
+    for (int t = threadIdx.x; t < B * B; t += 256) g[t] = tile[(t / B) * LD + (t % B)];
+}
+
 // u^(k) = u^n + beta P_e^{-1} r_e with P_e^{-1} column-major: one warp per element, each
 // lane owns rows lane, lane+32, ...; every column is a coalesced read.
 template <int B, class T>
@@ -295,12 +480,11 @@ emg_status launch_lu32(emg_ctx* c, int p) {
     switch (L.B) {
 #define EMG_GJ_CASE(BB)                                                                                      \
     case BB: {                                                                                               \
-        const size_t sm = LuCfg<BB, float>::SMEM;                                                            \
-        EMG_CUDA_TRY(c, cudaFuncSetAttribute(k_gj_inverse<BB, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                             (int)sm));                                                      \
+        const size_t sm = GjTile<BB>::SMEM;                                                                  \
+        EMG_CUDA_TRY(c, cudaFuncSetAttribute(k_gj_tile<BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
         {                                                                                                    \
             ProfScope _ps(c, PC_LU);                                                                         \
-            k_gj_inverse<BB, float><<<E, 256, sm, c->stream>>>((int)E, L.blk32);                             \
+            k_gj_tile<BB><<<E, 256, sm, c->stream>>>((int)E, L.blk32);                                       \
         }                                                                                                    \
         EMG_CHECK_LAUNCH(c);                                                                                 \
         return EMG_OK;                                                                                       \
