@@ -88,6 +88,9 @@ typedef struct {
     int32_t pre_smooth;    /* PRK steps per level on the down leg (default 2)                 */
     int32_t prec;          /* emg_prec                                                         */
     void* cuda_stream;     /* cudaStream_t to run on; NULL = a stream owned by the context     */
+    int32_t lag_blocks;    /* 1: factor P_e once per level per V-cycle and reuse it for every
+                              PRK step of that level (a lagged preconditioner; the fixed point
+                              R = 0 is unchanged); 0 (default): P(u^n) at every step         */
 } emg_params;
 
 typedef struct {

@@ -25,7 +25,7 @@ class ParamsC(C.Structure):
     _fields_ = [("gamma", C.c_double), ("mach", C.c_double), ("alpha_deg", C.c_double),
                 ("p_max", C.c_int32), ("rk_stages", C.c_int32), ("krylov_m", C.c_int32),
                 ("cfl_max", C.c_double), ("exp_dt_factor", C.c_double), ("pre_smooth", C.c_int32),
-                ("prec", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("prec", C.c_int32), ("cuda_stream", C.c_void_p), ("lag_blocks", C.c_int32)]
 
 
 class CycleInfoC(C.Structure):
@@ -114,7 +114,7 @@ class Solver:
     """One eMG context (device-resident mesh, basis tables, state and work arrays)."""
 
     def __init__(self, mesh, p_max=2, mach=0.3, alpha_deg=0.0, gamma=1.4, rk_stages=4, krylov_m=30,
-                 cfl_max=100.0, exp_dt_factor=0.0, pre_smooth=2, prec=0, stream=None):
+                 cfl_max=100.0, exp_dt_factor=0.0, pre_smooth=2, prec=0, stream=None, lag_blocks=0):
         self.lib = load()
         self.dim = int(mesh.dim)
         self.E = int(mesh.n_elems)
@@ -134,6 +134,7 @@ class Solver:
         prm.p_max, prm.rk_stages, prm.krylov_m = p_max, rk_stages, krylov_m
         prm.cfl_max, prm.exp_dt_factor, prm.pre_smooth, prm.prec = cfl_max, exp_dt_factor, pre_smooth, prec
         prm.cuda_stream = C.c_void_p(stream) if stream else None
+        prm.lag_blocks = int(lag_blocks)
         h = C.c_void_p()
         st = self.lib.emg_create_mesh(C.byref(d), C.byref(prm), C.byref(h))
         self.h = h

@@ -58,17 +58,21 @@ __global__ void k_set_cfl(DevScalars* sc, double cfl) { sc->cfl = cfl; }
 __global__ void k_set_ref(DevScalars* sc, double ref) { sc->res_ref = ref; }
 
 // One PRK step (Eq. prk_scalar) on level p: u^n = L.v on entry, result in L.v.
-// r_first: R~_p(u^n) if already available (else computed here).
-static emg_status prk_step(emg_ctx* c, int p, const double* tau, const double* r_first) {
+// r_first: R~_p(u^n) if already available (else computed here).  reuse_blocks: apply the
+// factors of the previous step of this level instead of P(u^n) (lagged preconditioner).
+static emg_status prk_step(emg_ctx* c, int p, const double* tau, const double* r_first, bool reuse_blocks = false) {
     LevelDev& L = c->lv[p];
     const int64_t S = c->E * L.B;
     EMG_CUDA_TRY(c, cudaMemcpyAsync(L.un, L.v, S * 8, cudaMemcpyDeviceToDevice, c->stream));
     const bool f32 = c->prm.prec == EMG_PREC_FP32_BLOCKS;
-    emg_status st = f32 ? launch_diag_blocks32(c, p, L.un, &c->sc->cfl, 1, L.blk32)
-                        : launch_diag_blocks(c, p, L.un, &c->sc->cfl, 1, L.blk);
-    if (st != EMG_OK) return st;
-    st = f32 ? launch_lu32(c, p) : launch_lu(c, p);
-    if (st != EMG_OK) return st;
+    emg_status st = EMG_OK;
+    if (!reuse_blocks) {
+        st = f32 ? launch_diag_blocks32(c, p, L.un, &c->sc->cfl, 1, L.blk32)
+                 : launch_diag_blocks(c, p, L.un, &c->sc->cfl, 1, L.blk);
+        if (st != EMG_OK) return st;
+        st = f32 ? launch_lu32(c, p) : launch_lu(c, p);
+        if (st != EMG_OK) return st;
+    }
     const int s = c->prm.rk_stages;
     for (int k = 1; k <= s; ++k) {
         const double beta = 1.0 / (double)(s - k + 1);
@@ -116,7 +120,7 @@ static emg_status vcycle_body(emg_ctx* c) {
                     rfirst = L.r;
                 }
             }
-            st = prk_step(c, p, tau, rfirst);
+            st = prk_step(c, p, tau, rfirst, c->prm.lag_blocks != 0 && sm > 0);
             if (st != EMG_OK) return st;
         }
         // restriction of the smoothed state and of its residual, FAS forcing of level p-1

@@ -119,90 +119,6 @@ __global__ void __launch_bounds__(128) k_stage(int E, const T* __restrict__ lu, 
     for (int t = lane; t < B; t += 32) out[(size_t)e * B + t] = un[(size_t)e * B + t] + beta * (double)y[t];
 }
 
-// In-place Gauss-Jordan inversion with partial pivoting of every block (FP32 block form):
-// P_e^{-1} is written column-major, so that each PRK stage is a batched matrix-vector
-// product that streams the inverse once (k_stage_gemv), instead of two dependent
-// triangular sweeps.  Thread grid: 32 columns x 8 rows, no index division.
-template <int B, class T>
-__global__ void __launch_bounds__(256) k_gj_inverse(int E, T* __restrict__ blk) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T* a = reinterpret_cast<T*>(smraw);
-    constexpr int LD = LuCfg<B, T>::LD;
-    __shared__ int s_piv;
-    __shared__ int ipiv[B];
-    __shared__ T fcol[B];
-    const int e = blockIdx.x;
-    const int tid = threadIdx.x;
-    const int tx = tid & 31, ty = tid >> 5;
-    T* g = blk + (size_t)e * B * B;
-    for (int t = tid; t < B * B; t += 256) a[(t / B) * LD + (t % B)] = g[t];
-    __syncthreads();
-    for (int k = 0; k < B; ++k) {
-        if (tid < 32) {
-            T best = (T)-1;
-            int bi = k;
-            for (int r = k + tid; r < B; r += 32) {
-                const T v = fabs(a[r * LD + k]);
-                if (v > best) {
-                    best = v;
-                    bi = r;
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) {
-                    best = ob;
-                    bi = oi;
-                }
-            }
-            if (tid == 0) {
-                s_piv = bi;
-                ipiv[k] = bi;
-            }
-        }
-        __syncthreads();
-        const int pr = s_piv;
-        if (pr != k)
-            for (int cc = tid; cc < B; cc += 256) {
-                const T t0 = a[k * LD + cc];
-                a[k * LD + cc] = a[pr * LD + cc];
-                a[pr * LD + cc] = t0;
-            }
-        __syncthreads();
-        const T inv = (T)1 / a[k * LD + k];
-        // factors of column k (zero on the pivot row), then the scaled pivot row
-        for (int r = tid; r < B; r += 256) fcol[r] = r == k ? (T)0 : a[r * LD + k];
-        __syncthreads();
-        for (int cc = tid; cc < B; cc += 256) a[k * LD + cc] = cc == k ? inv : a[k * LD + cc] * inv;
-        __syncthreads();
-        for (int r = ty; r < B; r += 8) {
-            if (r == k) continue;
-            const T f = fcol[r];
-            for (int cc = tx; cc < B; cc += 32) {
-                const T base = cc == k ? (T)0 : a[r * LD + cc];
-                a[r * LD + cc] = base - f * a[k * LD + cc];
-            }
-        }
-        __syncthreads();
-    }
-    // undo the row interchanges as column interchanges, last first
-    for (int k = B - 1; k >= 0; --k) {
-        const int p = ipiv[k];
-        if (p != k)
-            for (int r = tid; r < B; r += 256) {
-                const T t0 = a[r * LD + k];
-                a[r * LD + k] = a[r * LD + p];
-                a[r * LD + p] = t0;
-            }
-        __syncthreads();
-    }
-    for (int t = tid; t < B * B; t += 256) {
-        const int cc = t / B, r = t % B;
-        g[t] = a[r * LD + cc];   // column-major
-    }
-}
-
 // Register-tiled Gauss-Jordan inversion with partial pivoting (FP32 block form).
 // 256 threads = 32 (tx) x 8 (ty); thread (tx, ty) keeps rows ty + 8i and columns
 // tx + 32j of the block in registers for the whole elimination.  Per pivot step only the
@@ -220,9 +136,10 @@ struct GjTile {
 template <int B>
 __global__ void __launch_bounds__(256) k_gj_tile(int E, float* __restrict__ blk) {
     constexpr int RS = GjTile<B>::RS, CS = GjTile<B>::CS, LD = GjTile<B>::LD;
+    constexpr int RP = 8 * RS, CP = 32 * CS;   // zero-padded extents: no bounds checks inside
     extern __shared__ __align__(16) unsigned char smraw[];
     float* tile = reinterpret_cast<float*>(smraw);
-    __shared__ float colk[B], rowk[B], rowx[B], rowy[B];
+    __shared__ float colk[RP], rowk[CP], rowx[CP], rowy[CP];
     __shared__ int s_p;
     __shared__ int ipiv[B], colidx[B], pos[B];
     const int e = blockIdx.x;
@@ -236,6 +153,13 @@ __global__ void __launch_bounds__(256) k_gj_tile(int E, float* __restrict__ blk)
             const int r = ty + 8 * i, c = tx + 32 * j;
             a[i][j] = (r < B && c < B) ? g[r * B + c] : 0.0f;
         }
+    for (int t = threadIdx.x; t < RP; t += 256) colk[t] = 0.0f;
+    for (int t = threadIdx.x; t < CP; t += 256) rowk[t] = rowx[t] = rowy[t] = 0.0f;
+    __syncthreads();
+    // fully unrolled for B <= 100: k, its row slot and column slot are compile-time,
+    // so the register tile is indexed without runtime selects
+    constexpr int UNR = B <= 100 ? B : 1;
+#pragma unroll UNR
     for (int k = 0; k < B; ++k) {
         const int ki = k >> 3, kj = k >> 5;
         // (1) the pivot column, from the lane that owns column k in every warp
@@ -246,8 +170,11 @@ __global__ void __launch_bounds__(256) k_gj_tile(int E, float* __restrict__ blk)
                 float v = 0.0f;
 #pragma unroll
                 for (int j = 0; j < CS; ++j)
-                    if (j == kj) v = a[i][j];
-                if (r < B) colk[r] = v;
+                    if (j == kj) {
+                        v = a[i][j];
+                        a[i][j] = 0.0f;   // column k is rebuilt by the update (in-place scheme)
+                    }
+                colk[r] = v;
             }
         }
         __syncthreads();
@@ -287,8 +214,7 @@ __global__ void __launch_bounds__(256) k_gj_tile(int E, float* __restrict__ blk)
 #pragma unroll
                     for (int i = 0; i < RS; ++i)
                         if (i == ki) v = a[i][j];
-                    const int c = tx + 32 * j;
-                    if (c < B) rowx[c] = v;
+                    rowx[tx + 32 * j] = v;
                 }
             }
             if (ty == (p & 7)) {
@@ -298,8 +224,7 @@ __global__ void __launch_bounds__(256) k_gj_tile(int E, float* __restrict__ blk)
 #pragma unroll
                     for (int i = 0; i < RS; ++i)
                         if (i == pi) v = a[i][j];
-                    const int c = tx + 32 * j;
-                    if (c < B) rowy[c] = v;
+                    rowy[tx + 32 * j] = v;
                 }
             }
             if (threadIdx.x == 0) {
@@ -311,8 +236,7 @@ __global__ void __launch_bounds__(256) k_gj_tile(int E, float* __restrict__ blk)
             if (ty == (k & 7)) {
 #pragma unroll
                 for (int j = 0; j < CS; ++j) {
-                    const int c = tx + 32 * j;
-                    const float v = c < B ? rowy[c] : 0.0f;
+                    const float v = rowy[tx + 32 * j];
 #pragma unroll
                     for (int i = 0; i < RS; ++i)
                         if (i == ki) a[i][j] = v;
@@ -321,8 +245,7 @@ __global__ void __launch_bounds__(256) k_gj_tile(int E, float* __restrict__ blk)
             if (ty == (p & 7)) {
 #pragma unroll
                 for (int j = 0; j < CS; ++j) {
-                    const int c = tx + 32 * j;
-                    const float v = c < B ? rowx[c] : 0.0f;
+                    const float v = rowx[tx + 32 * j];
 #pragma unroll
                     for (int i = 0; i < RS; ++i)
                         if (i == pi) a[i][j] = v;
@@ -339,28 +262,23 @@ __global__ void __launch_bounds__(256) k_gj_tile(int E, float* __restrict__ blk)
                 for (int i = 0; i < RS; ++i)
                     if (i == ki) v = a[i][j];
                 const int c = tx + 32 * j;
-                if (c < B) rowk[c] = (c == k ? 1.0f : v) * inv;
+                rowk[c] = (c == k ? 1.0f : v) * inv;
             }
         }
         __syncthreads();
-        // (5) eliminate column k from every other row
+        // (5) eliminate column k from every other row (padded rows have colk = 0)
+        float rk[CS];
+#pragma unroll
+        for (int j = 0; j < CS; ++j) rk[j] = rowk[tx + 32 * j];
 #pragma unroll
         for (int i = 0; i < RS; ++i) {
-            const int r = ty + 8 * i;
-            if (r >= B) continue;
-            if (r == k) {
+            if (ty + 8 * i == k) {
 #pragma unroll
-                for (int j = 0; j < CS; ++j) {
-                    const int c = tx + 32 * j;
-                    if (c < B) a[i][j] = rowk[c];
-                }
+                for (int j = 0; j < CS; ++j) a[i][j] = rk[j];
             } else {
-                const float f = colk[r];
+                const float f = colk[ty + 8 * i];
 #pragma unroll
-                for (int j = 0; j < CS; ++j) {
-                    const int c = tx + 32 * j;
-                    if (c < B) a[i][j] = (c == k ? 0.0f : a[i][j]) - f * rowk[c];
-                }
+                for (int j = 0; j < CS; ++j) a[i][j] -= f * rk[j];
             }
         }
         __syncthreads();
