@@ -100,8 +100,19 @@ __device__ __forceinline__ void reduce_cols(const double* part, int nb, int stri
     for (int c0 = 0; c0 < ncol; c0 += ARN_THREADS / ARN_SUB) {
         const int c = c0 + threadIdx.x / ARN_SUB;
         double v = 0.0;
-        if (c < ncol)
-            for (int b = sub; b < nb; b += ARN_SUB) v += __ldcg(part + (size_t)b * stride + c);   // other blocks: L2
+        if (c < ncol) {
+            // four independent chains (loads in flight together), combined in a fixed order
+            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+            int b = sub;
+            for (; b + 3 * ARN_SUB < nb; b += 4 * ARN_SUB) {
+                v0 += __ldcg(part + (size_t)b * stride + c);   // other blocks' data: L2
+                v1 += __ldcg(part + (size_t)(b + ARN_SUB) * stride + c);
+                v2 += __ldcg(part + (size_t)(b + 2 * ARN_SUB) * stride + c);
+                v3 += __ldcg(part + (size_t)(b + 3 * ARN_SUB) * stride + c);
+            }
+            for (; b < nb; b += ARN_SUB) v0 += __ldcg(part + (size_t)b * stride + c);
+            v = (v0 + v1) + (v2 + v3);
+        }
         for (int o = ARN_SUB / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, ARN_SUB);
         if (sub == 0 && c < ncol) out_sh[c] = v;
     }
@@ -142,10 +153,51 @@ __device__ __forceinline__ void slice_dots(const double* V, const double* w, int
     }
 }
 
+// out[k] = scale * dt_e * (J_0 x)_k for this block's rows; x may belong to other blocks
+// (read through L2) and is either a vector or, when xr != nullptr, dt .* xr computed on the fly.
+__device__ __forceinline__ void spmv_rows(int64_t k0, int64_t k1, int NF, const double* __restrict__ bsr,
+                                          const int* __restrict__ nbr, const double* __restrict__ dt,
+                                          const double* x, const double* __restrict__ xr, double scale,
+                                          double* __restrict__ out) {
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
+        const int e = (int)(k / 5), a = (int)(k % 5);
+        const double* row = bsr + (size_t)e * (1 + NF) * 25;
+        double s = 0.0;
+        if (xr) {
+            const double de = dt[e];
+#pragma unroll
+            for (int b = 0; b < 5; ++b) s += row[a * 5 + b] * (de * xr[(size_t)e * 5 + b]);
+            for (int lf = 0; lf < NF; ++lf) {
+                const int n = nbr[(size_t)e * NF + lf];
+                if (n < 0) continue;
+                const double dn = dt[n];
+                const double* blk = row + (1 + lf) * 25;
+#pragma unroll
+                for (int b = 0; b < 5; ++b) s += blk[a * 5 + b] * (dn * xr[(size_t)n * 5 + b]);
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < 5; ++b) s += row[a * 5 + b] * __ldcg(x + (size_t)e * 5 + b);
+            for (int lf = 0; lf < NF; ++lf) {
+                const int n = nbr[(size_t)e * NF + lf];
+                if (n < 0) continue;
+                const double* blk = row + (1 + lf) * 25;
+#pragma unroll
+                for (int b = 0; b < 5; ++b) s += blk[a * 5 + b] * __ldcg(x + (size_t)n * 5 + b);   // other blocks
+            }
+        }
+        out[k] = dt[e] * (scale * s);
+    }
+}
+
+// Three grid barriers per Krylov step: after the first dot sweep, after the second, and
+// after the norm.  The next step's product A v_{j+1} is taken as (A w)/h_{j+1,j} from the
+// neighbours' w (final before the third barrier) into the other half of w, so v_{j+1}
+// need not be published before it is used.
 __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int NF, int m,
                                                          const double* __restrict__ bsr, const int* __restrict__ nbr,
                                                          const double* __restrict__ dt, const double* __restrict__ r,
-                                                         double* __restrict__ V, double* __restrict__ w,
+                                                         double* __restrict__ V, double* __restrict__ wbuf,
                                                          double* __restrict__ H, double* __restrict__ partA,
                                                          double* __restrict__ partB, double* __restrict__ partC,
                                                          int stride, GridBar* bar, long long budget, DevScalars* sc) {
@@ -161,7 +213,6 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
         double v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
             const double x = dt[k / 5] * r[k];
-            V[k] = x;
             v[0] += x * x;
         }
         block_reduce_store(v, 1, partA + (size_t)blockIdx.x * stride, sh);
@@ -176,30 +227,12 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
         if (!isfinite(beta)) sc->nonfinite = 1;
     }
     if (beta == 0.0 || !isfinite(beta)) return;   // uniform across blocks
-    {
-        const double ib = 1.0 / beta;
-        for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) V[k] *= ib;
-    }
-    if (!grid_sync(bar, nb, budget, sc, &s_ok)) return;
+    const double ib = 1.0 / beta;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) V[k] = dt[k / 5] * r[k] * ib;
+    double* w = wbuf;
+    spmv_rows(k0, k1, NF, bsr, nbr, dt, nullptr, r, ib, w);   // A v_1 from the inputs: no barrier
+    __syncthreads();
     for (int j = 0; j < m; ++j) {
-        const double* vj = V + (size_t)j * K0;
-        // SpMV on this block's rows, w = dt * (J_0 v_j)
-        for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
-            const int e = (int)(k / 5), a = (int)(k % 5);
-            const double* row = bsr + (size_t)e * (1 + NF) * 25;
-            double s = 0.0;
-#pragma unroll
-            for (int b = 0; b < 5; ++b) s += row[a * 5 + b] * __ldcg(vj + (size_t)e * 5 + b);
-            for (int lf = 0; lf < NF; ++lf) {
-                const int n = nbr[(size_t)e * NF + lf];
-                if (n < 0) continue;
-                const double* blk = row + (1 + lf) * 25;
-#pragma unroll
-                for (int b = 0; b < 5; ++b) s += blk[a * 5 + b] * __ldcg(vj + (size_t)n * 5 + b);   // written by other blocks
-            }
-            w[k] = dt[e] * s;
-        }
-        __syncthreads();
         // CGS pass 1: h1 = V^T w and w.w
         slice_dots(V, w, K0, k0, k1, j + 1, 1, partA + (size_t)blockIdx.x * stride, sh);
         if (!grid_sync(bar, nb, budget, sc, &s_ok)) return;
@@ -242,7 +275,10 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
         const double ih = 1.0 / hn;
         double* vn = V + (size_t)(j + 1) * K0;
         for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) vn[k] = w[k] * ih;
-        if (!grid_sync(bar, nb, budget, sc, &s_ok)) return;
+        double* wn = wbuf + (size_t)((j + 1) & 1) * K0;
+        spmv_rows(k0, k1, NF, bsr, nbr, dt, w, nullptr, ih, wn);
+        __syncthreads();
+        w = wn;
     }
 }
 
@@ -500,7 +536,7 @@ constexpr int NA_STRIDE = MAX_KRYLOV + 8;
 constexpr int64_t NA_K0 = 5 * NA_MAX_ELEMS;
 constexpr size_t NA_OFF_V = 0;
 constexpr size_t NA_OFF_W = NA_OFF_V + (size_t)(NA_MAX_M + 1) * NA_K0;
-constexpr size_t NA_OFF_BSR = NA_OFF_W + (size_t)NA_K0;
+constexpr size_t NA_OFF_BSR = NA_OFF_W + 2 * (size_t)NA_K0;
 constexpr size_t NA_OFF_NBR = NA_OFF_BSR + (size_t)NA_MAX_ELEMS * (1 + NA_MAX_NF) * 25;
 constexpr size_t NA_OFF_H = NA_OFF_NBR + (size_t)NA_MAX_ELEMS * NA_MAX_NF / 2;
 constexpr size_t NA_OFF_Y = NA_OFF_H + (size_t)(NA_MAX_M + 1) * NA_MAX_M;

@@ -410,7 +410,7 @@ int64_t estimate_bytes(int dim, int64_t E, int64_t F, int64_t F_int, int p_max, 
         if (p > 0) b += E * (int64_t)B * B * 8 + E * (int64_t)B * 4;
     }
     const int64_t K0 = 5 * E;
-    b += E * (1 + nf) * 25 * 8 + (m + 2) * K0 * 8 + E * 8;
+    b += E * (1 + nf) * 25 * 8 + (m + 3) * K0 * 8 + E * 8;
     const int Bmax = 5 * nmax;
     b += E * (int64_t)Bmax * Bmax * 8 + 3 * E * 5 * nmax * 8;
     return b;
@@ -594,7 +594,7 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
     EMG_ALLOC(c->dt, double, E);
     EMG_ALLOC(c->bsr, double, E * (1 + nf) * 25);
     EMG_ALLOC(c->V, double, (m_kr + 1) * K0);
-    EMG_ALLOC(c->w, double, K0);
+    EMG_ALLOC(c->w, double, 2 * K0);
     EMG_ALLOC(c->H, double, (m_kr + 1) * m_kr);
     EMG_ALLOC(c->hcol, double, m_kr + 2);
     EMG_ALLOC(c->y, double, m_kr + 1);
