@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--prec", default="both", choices=["both", "fp64", "mixed"])
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-10 solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--serve", action="store_true",
+                    help="run the seeded stream of served cylinder solves through the request loop instead")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--max-active", type=int, default=8)
     return ap.parse_args()
 
 
@@ -248,8 +252,64 @@ def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks):
     return out
 
 
+def run_serve(args, rank, world, local):
+    """The served stream: 64 cylinder solves (seed 1807, Poisson arrivals at 4/s, O-grids
+    32x16..256x128, p in 1..4, Ma in [0.1, 0.5]) through the library's request loop, mixed
+    form.  Replicas only: with N ranks every rank serves its own copy of the stream."""
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1807_01151_gb300 import serving
+    from workloads import ogrid, request_stream
+    reqs = request_stream(n=args.serve_requests)
+    cache = {}
+
+    def make_mesh(rq):
+        key = (rq.n_theta, rq.n_r)
+        if key not in cache:
+            cache[key] = ogrid(*key)
+        return cache[key]
+
+    for rq in reqs:
+        make_mesh(rq)
+    if world > 1:
+        torch.distributed.barrier()
+    outdir = os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ROOT
+    clocks = Clocks(local, os.path.join(outdir, f"clocks_rank{rank}_serve.csv"))
+    out, summ = serving.serve_stream(reqs, make_mesh, max_active=args.max_active, prec=1)
+    clk = clocks.stop()
+    span = summ["makespan_s"]
+    if world > 1:
+        t = torch.tensor([span], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        span = float(t.item())
+    if rank == 0:
+        line = {
+            "metric": "served steady solves to a 1e-10 drop: solves/s, p50/p99 time-to-converge",
+            "value": world * summ["converged"] / span, "unit": "solves/s", "n_gpus": world,
+            "steps": len(reqs), "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": f"served_cylinder_stream_{len(reqs)}", "seed": 1807, "arrivals": "Poisson, 4/s",
+                       "grids": "32x16, 64x32, 128x64, 256x128", "p": "1..4", "mach": "U[0.1, 0.5]",
+                       "form": "fp32_blocks", "max_active": args.max_active,
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "makespan_s": span,
+            "converged": summ["converged"], "requests": summ["requests"], "peak_active": summ["peak_active"],
+            "cycles_total": summ["cycles_total"], "clocks": clk,
+            "failed": [dict(id=r["id"], status=r["status_name"]) for r in out if r["status"] != 0],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
+    if args.serve and args.impl == "emg":
+        rank, world, local = dist_info()
+        return run_serve(args, rank, world, local)
     W = WORKLOADS[args.workload]
     rank, world, local = dist_info()
     if args.impl == "reference":

@@ -82,7 +82,7 @@ typedef struct {
     double alpha_deg;      /* free-stream angle in the x-y plane                              */
     int32_t p_max;         /* finest DG degree, 0..4                                          */
     int32_t rk_stages;     /* s of Eq. prk_scalar (paper: 4)                                  */
-    int32_t krylov_m;      /* Krylov dimension of the EXP1 step (paper: 30), <= 64            */
+    int32_t krylov_m;      /* Krylov dimension of the EXP1 step (paper: 30), 1..40             */
     double cfl_max;        /* CFL_max of Eq. cfl (paper: 100 for eMG)                         */
     double exp_dt_factor;  /* EXP1 step = factor * dtau(p_max); <= 0 selects p_max + 1 (Sec. 4) */
     int32_t pre_smooth;    /* PRK steps per level on the down leg (default 2)                 */
@@ -91,6 +91,11 @@ typedef struct {
     int32_t lag_blocks;    /* 1: factor P_e once per level per V-cycle and reuse it for every
                               PRK step of that level (a lagged preconditioner; the fixed point
                               R = 0 is unchanged); 0 (default): P(u^n) at every step         */
+    int32_t use_graph;     /* 1 (default): the V-cycle body (every level's smoother, transfers,
+                              EXP1) is captured once into a CUDA graph and replayed each cycle;
+                              0: launched kernel by kernel.  The same kernels run either way and
+                              give bitwise the same result.  The event profiler, when on, uses
+                              the kernel-by-kernel path. */
 } emg_params;
 
 typedef struct {
@@ -211,8 +216,12 @@ emg_status emg_element_geometry(emg_ctx* ctx, double* vol, double* h);
 emg_status emg_profile_enable(emg_ctx* ctx, int32_t on);
 emg_status emg_profile_read(emg_ctx* ctx, int32_t cls, double* total_ms, int64_t* launches);
 const char* emg_profile_class_name(int32_t cls);
-/* Number of kernels the context has launched since creation. */
+/* Number of kernels the context has launched since creation (a graph replay counts the
+ * kernels it holds). */
 int64_t emg_launch_count(const emg_ctx* ctx);
+/* Kernels in the captured V-cycle graph; 0 before the first cycle, with use_graph = 0, or
+ * if the capture failed (then the body runs kernel by kernel). */
+int64_t emg_graph_kernels(const emg_ctx* ctx);
 
 /* ---- failure detection (no counterpart in the paper) ----
  * Every device-side wait (the grid barriers of the persistent Arnoldi kernel) gives up
@@ -221,6 +230,70 @@ int64_t emg_launch_count(const emg_ctx* ctx);
  * block at a barrier that expects two, so the wait runs out (~0.1 s); it returns
  * EMG_ERR_TIMEOUT when the bounded wait works and clears the flag afterwards. */
 emg_status emg_selftest_wait_timeout(emg_ctx* ctx);
+
+/* Device bytes emg_create_mesh would allocate for this mesh and these parameters (the
+ * admission estimate; equal to emg_device_bytes of the context it creates).  Host only. */
+emg_status emg_estimate_device_bytes(const emg_mesh_desc* mesh, const emg_params* params, int64_t* bytes);
+
+/* ---- request loop with continuous batching (no counterpart in the paper) ----
+ * A server runs many steady solves (emg_solve_steady semantics: V-cycles until
+ * ||R(rho)|| <= drop * ||R(rho)|| of the first cycle) of different meshes, orders and
+ * Mach numbers as they arrive.  Requests wait in submission order; the head request is
+ * admitted when one of max_active slots is free and its footprint
+ * (emg_estimate_device_bytes) fits in what the memory budget has left.  An admitted solve
+ * owns a context (its own stream; state, blocks and Krylov arrays resident on the device
+ * until it ends) and keeps one V-cycle in flight; emg_server_step only polls events and
+ * enqueues the next cycle of every solve whose residual check has arrived, so the cycles
+ * of different solves overlap on the device.  A solve ends converged (EMG_OK), at
+ * max_cycles (EMG_ERR_NOT_CONVERGED), or with its own failure status; the others carry
+ * on.  The arithmetic of a solve depends on nothing outside its context (fixed-order
+ * reductions, no atomics), so its result is bitwise the same alone and in the mix.
+ * The caller's arrays are copied by emg_server_submit.  One host thread drives a server
+ * (not thread-safe); different servers are independent. */
+typedef struct emg_server emg_server;
+
+typedef struct {
+    int64_t mem_budget;  /* device bytes the active solves may hold together; <= 0: 90 % of free memory */
+    int32_t max_active;  /* slots: solves in flight at once, >= 1 */
+    double drop;         /* relative drop of ||R(rho)|| that ends a solve (> 0), e.g. 1e-10 */
+    int64_t max_cycles;  /* V-cycles per solve (>= 0) */
+    int32_t keep_state;  /* 1: keep each converged state on the host for emg_server_take_state */
+    int64_t stall_cycles; /* > 0: a solve whose ||R(rho)|| has set no new minimum for this many
+                             cycles ends with EMG_ERR_NOT_CONVERGED; 0: only max_cycles ends it */
+} emg_server_params;
+
+typedef struct {
+    int64_t id;           /* from emg_server_submit */
+    emg_status status;    /* EMG_OK = converged; EMG_ERR_OOM = does not fit the budget; ... */
+    int64_t cycles;       /* V-cycles done */
+    double res0;          /* ||R(rho)|| at the first cycle */
+    double res_final;     /* ||R(rho)|| at the last check */
+    double t_submit;      /* seconds on the server clock (emg_server_clock) */
+    double t_admit;
+    double t_done;
+    int64_t device_bytes; /* the admission estimate */
+} emg_request_result;
+
+emg_status emg_server_create(const emg_server_params* params, emg_server** out);
+/* Waits for and frees the active solves; queued requests are dropped. */
+emg_status emg_server_destroy(emg_server* srv);
+const char* emg_server_last_error(const emg_server* srv);
+/* Seconds since the server's creation (host steady clock). */
+double emg_server_clock(const emg_server* srv);
+/* Queue one solve.  mesh and params as for emg_create_mesh (params->cuda_stream is
+ * ignored: each solve gets its own stream); U0 [n_elems][5][N_pmax] on the host, or NULL
+ * for the free stream.  id receives the request id (0, 1, 2, ... per server). */
+emg_status emg_server_submit(emg_server* srv, const emg_mesh_desc* mesh, const emg_params* params,
+                             const double* U0, int64_t* id);
+/* One scheduling round, without waiting: advance every solve whose last residual check
+ * has arrived, retire the finished ones, admit queued requests.  Returns the number of
+ * active and queued requests. */
+emg_status emg_server_step(emg_server* srv, int32_t* n_active, int32_t* n_queued);
+/* Move up to capacity finished requests' results (in completion order) into out. */
+emg_status emg_server_results(emg_server* srv, emg_request_result* out, int32_t capacity, int32_t* n_out);
+/* Copy the kept converged state of request id ([n_elems][5][N_pmax], n doubles) to host
+ * memory and release it.  EMG_ERR_ARG if none is kept or n does not match. */
+emg_status emg_server_take_state(emg_server* srv, int64_t id, double* U, int64_t n);
 
 /* Build identification string (architecture and kernel variants). */
 const char* emg_build_info(void);

@@ -25,7 +25,8 @@ class ParamsC(C.Structure):
     _fields_ = [("gamma", C.c_double), ("mach", C.c_double), ("alpha_deg", C.c_double),
                 ("p_max", C.c_int32), ("rk_stages", C.c_int32), ("krylov_m", C.c_int32),
                 ("cfl_max", C.c_double), ("exp_dt_factor", C.c_double), ("pre_smooth", C.c_int32),
-                ("prec", C.c_int32), ("cuda_stream", C.c_void_p), ("lag_blocks", C.c_int32)]
+                ("prec", C.c_int32), ("cuda_stream", C.c_void_p), ("lag_blocks", C.c_int32),
+                ("use_graph", C.c_int32)]
 
 
 class CycleInfoC(C.Structure):
@@ -36,6 +37,17 @@ class CycleInfoC(C.Structure):
 class SolveReportC(C.Structure):
     _fields_ = [("cycles", C.c_int64), ("res0", C.c_double), ("res_final", C.c_double),
                 ("converged", C.c_int32)]
+
+
+class ServerParamsC(C.Structure):
+    _fields_ = [("mem_budget", C.c_int64), ("max_active", C.c_int32), ("drop", C.c_double),
+                ("max_cycles", C.c_int64), ("keep_state", C.c_int32), ("stall_cycles", C.c_int64)]
+
+
+class RequestResultC(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int), ("cycles", C.c_int64), ("res0", C.c_double),
+                ("res_final", C.c_double), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("device_bytes", C.c_int64)]
 
 
 EXPORTS = {
@@ -63,10 +75,21 @@ EXPORTS = {
     "emg_profile_read": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "emg_profile_class_name": (C.c_char_p, [C.c_int32]),
     "emg_launch_count": (C.c_int64, [C.c_void_p]),
+    "emg_graph_kernels": (C.c_int64, [C.c_void_p]),
     "emg_selftest_wait_timeout": (C.c_int, [C.c_void_p]),
     "emg_exp1_step_noalloc": (C.c_int, [C.c_int32, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                         C.POINTER(C.c_int32)]),
+    "emg_estimate_device_bytes": (C.c_int, [C.POINTER(MeshDescC), C.POINTER(ParamsC), C.POINTER(C.c_int64)]),
+    "emg_server_create": (C.c_int, [C.POINTER(ServerParamsC), C.POINTER(C.c_void_p)]),
+    "emg_server_destroy": (C.c_int, [C.c_void_p]),
+    "emg_server_last_error": (C.c_char_p, [C.c_void_p]),
+    "emg_server_clock": (C.c_double, [C.c_void_p]),
+    "emg_server_submit": (C.c_int, [C.c_void_p, C.POINTER(MeshDescC), C.POINTER(ParamsC), C.c_void_p,
+                                    C.POINTER(C.c_int64)]),
+    "emg_server_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "emg_server_results": (C.c_int, [C.c_void_p, C.POINTER(RequestResultC), C.c_int32, C.POINTER(C.c_int32)]),
+    "emg_server_take_state": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]),
     "emg_build_info": (C.c_char_p, []),
 }
 
@@ -110,31 +133,58 @@ def _ptr(a):
     raise TypeError("expected a numpy array or a CUDA tensor")
 
 
+def mesh_desc(mesh):
+    """emg_mesh_desc of a workloads.MeshDesc; returns (desc, arrays it points into)."""
+    xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+    en = np.ascontiguousarray(mesh.elem_nodes, dtype=np.int64)
+    fb = np.ascontiguousarray(mesh.face_bc, dtype=np.int32)
+    wn = getattr(mesh, "wall_normal", None)
+    wn = None if wn is None else np.ascontiguousarray(wn, dtype=np.float64)
+    d = MeshDescC(int(mesh.dim), xyz.shape[1], xyz.ctypes.data_as(C.POINTER(C.c_double)), int(mesh.n_elems),
+                  en.ctypes.data_as(C.POINTER(C.c_int64)), fb.ctypes.data_as(C.POINTER(C.c_int32)),
+                  None if wn is None else wn.ctypes.data_as(C.POINTER(C.c_double)))
+    return d, (xyz, en, fb, wn)
+
+
+def make_params(p_max=2, mach=0.3, alpha_deg=0.0, gamma=1.4, rk_stages=4, krylov_m=30, cfl_max=100.0,
+                exp_dt_factor=0.0, pre_smooth=2, prec=0, stream=None, lag_blocks=0, use_graph=1):
+    prm = ParamsC()
+    load().emg_default_params(C.byref(prm))
+    prm.gamma, prm.mach, prm.alpha_deg = gamma, mach, alpha_deg
+    prm.p_max, prm.rk_stages, prm.krylov_m = p_max, rk_stages, krylov_m
+    prm.cfl_max, prm.exp_dt_factor, prm.pre_smooth, prm.prec = cfl_max, exp_dt_factor, pre_smooth, prec
+    prm.cuda_stream = C.c_void_p(stream) if stream else None
+    prm.lag_blocks = int(lag_blocks)
+    prm.use_graph = int(use_graph)
+    return prm
+
+
+def estimate_device_bytes(mesh, **params):
+    """Device bytes a Solver of this mesh and these parameters would hold (host-only call)."""
+    d, keep = mesh_desc(mesh)
+    prm = make_params(**params)
+    b = C.c_int64()
+    st = load().emg_estimate_device_bytes(C.byref(d), C.byref(prm), C.byref(b))
+    if st != 0:
+        raise EmgError(st, "emg_estimate_device_bytes")
+    return b.value
+
+
 class Solver:
     """One eMG context (device-resident mesh, basis tables, state and work arrays)."""
 
     def __init__(self, mesh, p_max=2, mach=0.3, alpha_deg=0.0, gamma=1.4, rk_stages=4, krylov_m=30,
-                 cfl_max=100.0, exp_dt_factor=0.0, pre_smooth=2, prec=0, stream=None, lag_blocks=0):
+                 cfl_max=100.0, exp_dt_factor=0.0, pre_smooth=2, prec=0, stream=None, lag_blocks=0,
+                 use_graph=1):
         self.lib = load()
         self.dim = int(mesh.dim)
         self.E = int(mesh.n_elems)
         self.p_max = int(p_max)
-        self._xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
-        self._en = np.ascontiguousarray(mesh.elem_nodes, dtype=np.int64)
-        self._fb = np.ascontiguousarray(mesh.face_bc, dtype=np.int32)
-        wn = getattr(mesh, "wall_normal", None)
-        self._wn = None if wn is None else np.ascontiguousarray(wn, dtype=np.float64)
-        d = MeshDescC(self.dim, self._xyz.shape[1], self._xyz.ctypes.data_as(C.POINTER(C.c_double)),
-                      self.E, self._en.ctypes.data_as(C.POINTER(C.c_int64)),
-                      self._fb.ctypes.data_as(C.POINTER(C.c_int32)),
-                      None if self._wn is None else self._wn.ctypes.data_as(C.POINTER(C.c_double)))
-        prm = ParamsC()
-        self.lib.emg_default_params(C.byref(prm))
-        prm.gamma, prm.mach, prm.alpha_deg = gamma, mach, alpha_deg
-        prm.p_max, prm.rk_stages, prm.krylov_m = p_max, rk_stages, krylov_m
-        prm.cfl_max, prm.exp_dt_factor, prm.pre_smooth, prm.prec = cfl_max, exp_dt_factor, pre_smooth, prec
-        prm.cuda_stream = C.c_void_p(stream) if stream else None
-        prm.lag_blocks = int(lag_blocks)
+        d, self._keep = mesh_desc(mesh)
+        prm = make_params(p_max=p_max, mach=mach, alpha_deg=alpha_deg, gamma=gamma, rk_stages=rk_stages,
+                          krylov_m=krylov_m, cfl_max=cfl_max, exp_dt_factor=exp_dt_factor,
+                          pre_smooth=pre_smooth, prec=prec, stream=stream, lag_blocks=lag_blocks,
+                          use_graph=use_graph)
         h = C.c_void_p()
         st = self.lib.emg_create_mesh(C.byref(d), C.byref(prm), C.byref(h))
         self.h = h
@@ -270,11 +320,90 @@ class Solver:
     def launch_count(self):
         return int(self.lib.emg_launch_count(self.h))
 
+    @property
+    def graph_kernels(self):
+        return int(self.lib.emg_graph_kernels(self.h))
+
     def element_geometry(self):
         vol = np.empty(self.E)
         h = np.empty(self.E)
         self._check(self.lib.emg_element_geometry(self.h, _ptr(vol)[0], _ptr(h)[0]))
         return vol, h
+
+
+class Server:
+    """Request loop with continuous batching (emg_server_*): solves of different meshes,
+    orders and Mach numbers run concurrently, each in a context of its own."""
+
+    def __init__(self, max_active=8, mem_budget=0, drop=1e-10, max_cycles=2000, keep_state=False, stall_cycles=0):
+        self.lib = load()
+        sp = ServerParamsC(int(mem_budget), int(max_active), float(drop), int(max_cycles), int(bool(keep_state)),
+                           int(stall_cycles))
+        h = C.c_void_p()
+        st = self.lib.emg_server_create(C.byref(sp), C.byref(h))
+        if st != 0:
+            raise EmgError(st, "emg_server_create")
+        self.h = h
+        self._shape = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.emg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != 0:
+            raise EmgError(st, self.lib.emg_server_last_error(self.h).decode())
+
+    def clock(self):
+        return float(self.lib.emg_server_clock(self.h))
+
+    def submit(self, mesh, U0=None, **params):
+        """Queue one steady solve; returns its request id."""
+        d, keep = mesh_desc(mesh)
+        prm = make_params(**params)
+        u = None
+        if U0 is not None:
+            u = np.ascontiguousarray(U0, dtype=np.float64)
+        rid = C.c_int64()
+        self._check(self.lib.emg_server_submit(self.h, C.byref(d), C.byref(prm),
+                                               None if u is None else C.c_void_p(u.ctypes.data), C.byref(rid)))
+        p = int(params.get("p_max", 2))
+        nm = (p + 1) * (p + 2) // 2 if mesh.dim == 2 else (p + 1) * (p + 2) * (p + 3) // 6
+        self._shape[rid.value] = (int(mesh.n_elems), 5, nm)
+        return rid.value
+
+    def step(self):
+        """One non-blocking scheduling round; returns (active, queued)."""
+        a, q = C.c_int32(), C.c_int32()
+        self._check(self.lib.emg_server_step(self.h, C.byref(a), C.byref(q)))
+        return a.value, q.value
+
+    def results(self):
+        """Finished requests since the last call, as dicts, in completion order."""
+        out = []
+        buf = (RequestResultC * 64)()
+        while True:
+            n = C.c_int32()
+            self._check(self.lib.emg_server_results(self.h, buf, 64, C.byref(n)))
+            for k in range(n.value):
+                r = buf[k]
+                out.append(dict(id=r.id, status=r.status, status_name=STATUS.get(r.status, str(r.status)),
+                                cycles=r.cycles, res0=r.res0, res_final=r.res_final, t_submit=r.t_submit,
+                                t_admit=r.t_admit, t_done=r.t_done, device_bytes=r.device_bytes))
+            if n.value < 64:
+                return out
+
+    def take_state(self, rid):
+        U = np.empty(self._shape[rid])
+        self._check(self.lib.emg_server_take_state(self.h, int(rid), C.c_void_p(U.ctypes.data), U.size))
+        return U
 
 
 def exp1_step_noalloc(dim, diag, off, nbr, r0, dt, u0, u_out, krylov_m=30, stream=None):

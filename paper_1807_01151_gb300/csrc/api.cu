@@ -3,7 +3,9 @@
 // file only sequences launches on the context's stream.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
@@ -32,6 +34,20 @@ emg_status copy_in(emg_ctx* c, double* dst, const double* src, int64_t n, int on
     return EMG_OK;
 }
 
+// Output staging of the component calls, grown on demand (a full set of FP64 blocks of the
+// top level is only needed by emg_jacobian_diag with host output).
+emg_status stage_out(emg_ctx* c, int64_t n, double** out) {
+    if (c->stage_out_n < n) {
+        if (c->stage_out) EMG_CUDA_TRY(c, cudaFreeAsync(c->stage_out, c->stream));
+        c->stage_out = nullptr;
+        c->stage_out_n = 0;
+        EMG_CUDA_TRY(c, cudaMallocAsync((void**)&c->stage_out, (size_t)n * sizeof(double), c->stream));
+        c->stage_out_n = n;
+    }
+    *out = c->stage_out;
+    return EMG_OK;
+}
+
 emg_status copy_out(emg_ctx* c, double* dst, const double* src, int64_t n, int on_device) {
     EMG_CUDA_TRY(c, cudaMemcpyAsync(dst, src, n * sizeof(double),
                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
@@ -56,6 +72,8 @@ __global__ void k_set_freestream(int64_t E, int N, const double* __restrict__ vo
 
 __global__ void k_set_cfl(DevScalars* sc, double cfl) { sc->cfl = cfl; }
 __global__ void k_set_ref(DevScalars* sc, double ref) { sc->res_ref = ref; }
+__global__ void k_set_cycle(DevScalars* sc, long long n) { sc->cycle = n; }
+__global__ void k_advance_cycle(DevScalars* sc) { sc->cycle += 1; }
 
 // One PRK step (Eq. prk_scalar) on level p: u^n = L.v on entry, result in L.v.
 // r_first: R~_p(u^n) if already available (else computed here).  reuse_blocks: apply the
@@ -90,15 +108,17 @@ static emg_status prk_step(emg_ctx* c, int p, const double* tau, const double* r
     return EMG_OK;
 }
 
-// Entry of V-cycle n: R_pmax(v), ||R(rho)||, CFL_n and the EXP1 steps dt_e.
-static emg_status vcycle_entry(emg_ctx* c, int64_t n) {
+// Entry of V-cycle n (n kept on the device): R_pmax(v), ||R(rho)|| and CFL_n.
+emg_status vcycle_entry(emg_ctx* c) {
     LevelDev& T = c->lv[c->p_max];
     emg_status st = launch_residual(c, c->p_max, T.v, nullptr, T.r);
     if (st != EMG_OK) return st;
-    return launch_norm_cfl(c, T.r, n, 1);
+    return launch_norm_cfl(c, T.r, 1);
 }
 
-static emg_status vcycle_body(emg_ctx* c) {
+// First part of the cycle body: the down leg (PRK smoothing, restriction and FAS forcing on
+// every level p >= 1, Sec. 2.3 steps 1-4) and the EXP1 inputs on p = 0.
+emg_status vcycle_body_down(emg_ctx* c) {
     const int P = c->p_max;
     const double fac = c->prm.exp_dt_factor > 0.0 ? c->prm.exp_dt_factor : (double)(P + 1);
     emg_status st = launch_dtau(c, P, c->lv[P].v, &c->sc->cfl, fac, c->dt);
@@ -135,18 +155,106 @@ static emg_status vcycle_body(emg_ctx* c) {
         if (st != EMG_OK) return st;
     }
     LevelDev& L0 = c->lv[0];
-    if (P == 0) {
-        EMG_CUDA_TRY(c, cudaMemcpyAsync(L0.v0, L0.v, c->E * 5 * 8, cudaMemcpyDeviceToDevice, c->stream));
-        st = launch_exp1(c, L0.v0, nullptr, c->dt, L0.v);
-    } else {
-        st = launch_exp1(c, L0.v0, L0.tau, c->dt, L0.v);
-    }
+    if (P == 0) EMG_CUDA_TRY(c, cudaMemcpyAsync(L0.v0, L0.v, c->E * 5 * 8, cudaMemcpyDeviceToDevice, c->stream));
+    return launch_exp1_prepare(c, L0.v0, P == 0 ? nullptr : L0.tau);
+}
+
+// Second part of the cycle body: the EXP1 Krylov step on p = 0, then prolongation and
+// correction up to p_max (Sec. 2.3 steps 5-6), and the cycle counter.
+emg_status vcycle_body_up(emg_ctx* c) {
+    const int P = c->p_max;
+    LevelDev& L0 = c->lv[0];
+    emg_status st = launch_exp1_krylov(c, L0.v0, c->dt, L0.v);
     if (st != EMG_OK) return st;
     for (int p = 1; p <= P; ++p) {
         st = launch_prolong(c, p, c->lv[p].v, c->lv[p - 1].v, c->lv[p - 1].v0);
         if (st != EMG_OK) return st;
     }
+    { ProfScope _ps(c, PC_CONTROL); k_advance_cycle<<<1, 1, 0, c->stream>>>(c->sc); }
+    EMG_CHECK_LAUNCH(c);
     return EMG_OK;
+}
+
+emg_status vcycle_body(emg_ctx* c) {
+    emg_status st = vcycle_body_down(c);
+    if (st != EMG_OK) return st;
+    return vcycle_body_up(c);
+}
+
+// Capture one part of the body into an executable graph (nothing runs during a capture).
+static emg_status capture(emg_ctx* c, emg_status (*part)(emg_ctx*), cudaGraphExec_t* exec, int64_t* kernels) {
+    const int64_t l0 = c->launches;
+    EMG_CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    const emg_status st = part(c);
+    c->capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    cudaError_t ei = cudaErrorUnknown;
+    if (st == EMG_OK && e == cudaSuccess && g) ei = cudaGraphInstantiate(exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    *kernels = c->launches - l0;   // kernels recorded, none launched yet
+    c->launches = l0;
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        *exec = nullptr;
+        return EMG_ERR_CUDA;
+    }
+    return EMG_OK;
+}
+
+// The cycle body as two CUDA graphs, captured on first use and then replayed (the host
+// sequence has no data-dependent branch: every decision of the cycle is on the device).
+// The split sits before the cooperative Arnoldi kernel, whose replay is ordered with the
+// cooperative launches of other contexts.
+emg_status run_body(emg_ctx* c) {
+    if (!c->prm.use_graph || c->graph_failed || c->prof.on) return vcycle_body(c);
+    if (!c->body_exec || !c->krylov_exec) {
+        int64_t k1 = 0, k2 = 0;
+        if (capture(c, vcycle_body_down, &c->body_exec, &k1) != EMG_OK ||
+            capture(c, vcycle_body_up, &c->krylov_exec, &k2) != EMG_OK) {
+            if (c->body_exec) cudaGraphExecDestroy(c->body_exec);
+            if (c->krylov_exec) cudaGraphExecDestroy(c->krylov_exec);
+            c->body_exec = c->krylov_exec = nullptr;
+            c->graph_failed = true;   // run kernel by kernel from now on (same kernels)
+            return vcycle_body(c);
+        }
+        c->body_kernels = k1 + k2;
+    }
+    EMG_CUDA_TRY(c, cudaGraphLaunch(c->body_exec, c->stream));
+    cudaGraphExec_t kx = c->krylov_exec;
+    emg_status st = coop_ordered(c->device, c->stream, [kx, c]() { return cudaGraphLaunch(kx, c->stream); }, &c->err);
+    if (st != EMG_OK) return st;
+    c->launches += c->body_kernels;
+    return EMG_OK;
+}
+
+// Page-locked host slots for the per-context device scalars, taken from chunks that live
+// as long as the process: creating and destroying contexts then never frees page-locked
+// memory, which would wait for the whole device.
+namespace {
+std::mutex g_pin_mu;
+std::vector<DevScalars*> g_pin_free;
+}  // namespace
+
+DevScalars* pinned_scalars_acquire() {
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    if (g_pin_free.empty()) {
+        constexpr int kChunk = 64;
+        DevScalars* chunk = nullptr;
+        if (cudaMallocHost(&chunk, kChunk * sizeof(DevScalars)) != cudaSuccess) return nullptr;
+        for (int i = kChunk - 1; i >= 0; --i) g_pin_free.push_back(chunk + i);
+    }
+    DevScalars* p = g_pin_free.back();
+    g_pin_free.pop_back();
+    std::memset(p, 0, sizeof(DevScalars));
+    return p;
+}
+
+void pinned_scalars_release(DevScalars* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
 }
 
 void prof_flush(emg_ctx* c) {
@@ -162,7 +270,7 @@ void prof_flush(emg_ctx* c) {
     c->prof.used = 0;
 }
 
-static emg_status check_flags(emg_ctx* c) {
+emg_status check_flags(emg_ctx* c) {
     if (c->sc_host->timeout) return fail(c, EMG_ERR_TIMEOUT, "a grid barrier wait in the Arnoldi kernel timed out");
     if (c->sc_host->nonfinite) return fail(c, EMG_ERR_NONFINITE, "non-finite residual or Krylov quantity");
     if (c->sc_host->pad) return fail(c, EMG_ERR_UNPHYSICAL, "non-positive density or pressure at a cell centre");
@@ -187,6 +295,7 @@ void emg_default_params(emg_params* p) {
     p->pre_smooth = 2;
     p->prec = EMG_PREC_FP64;
     p->cuda_stream = nullptr;
+    p->use_graph = 1;
 }
 
 const char* emg_build_info(void) {
@@ -237,10 +346,13 @@ emg_status emg_create_mesh(const emg_mesh_desc* m, const emg_params* prm, emg_ct
 
 emg_status emg_destroy(emg_ctx* c) {
     if (!c) return EMG_OK;
+    if (c->body_exec) cudaGraphExecDestroy(c->body_exec);
+    if (c->krylov_exec) cudaGraphExecDestroy(c->krylov_exec);
+    for (void* p : c->allocs) cudaFreeAsync(p, c->stream);
+    if (c->stage_out) cudaFreeAsync(c->stage_out, c->stream);
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& e : c->prof.ev) cudaEventDestroy(e);
-    for (void* p : c->allocs) cudaFree(p);
-    if (c->sc_host) cudaFreeHost(c->sc_host);
+    pinned_scalars_release(c->sc_host);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return EMG_OK;
@@ -263,6 +375,8 @@ emg_status emg_set_state(emg_ctx* c, const double* U, int32_t on_device) {
         EMG_CHECK_LAUNCH(c);
     }
     EMG_CUDA_TRY(c, cudaMemsetAsync(c->sc, 0, sizeof(DevScalars), c->stream));
+    { ProfScope _ps(c, PC_CONTROL); k_set_cycle<<<1, 1, 0, c->stream>>>(c->sc, 1); }
+    EMG_CHECK_LAUNCH(c);
     emg_status st = launch_check_state(c, T.v, n);
     if (st != EMG_OK) return st;
     st = read_scalars(c);
@@ -284,6 +398,8 @@ emg_status emg_set_cycle(emg_ctx* c, int64_t n, double res_ref) {
     c->cycle_n = n;
     { ProfScope _ps(c, PC_CONTROL); k_set_ref<<<1, 1, 0, c->stream>>>(c->sc, res_ref > 0.0 ? res_ref : 0.0); }
     EMG_CHECK_LAUNCH(c);
+    { ProfScope _ps(c, PC_CONTROL); k_set_cycle<<<1, 1, 0, c->stream>>>(c->sc, (long long)n); }
+    EMG_CHECK_LAUNCH(c);
     return EMG_OK;
 }
 
@@ -299,9 +415,9 @@ emg_status emg_get_cycle(emg_ctx* c, int64_t* n, double* res_ref) {
 emg_status emg_vcycle(emg_ctx* c, emg_cycle_info* info) {
     if (!c) return EMG_ERR_ARG;
     const int64_t n = c->cycle_n;
-    emg_status st = vcycle_entry(c, n);
+    emg_status st = vcycle_entry(c);
     if (st != EMG_OK) return st;
-    st = vcycle_body(c);
+    st = run_body(c);
     if (st != EMG_OK) return st;
     c->cycle_n = n + 1;
     if (info) {
@@ -323,7 +439,7 @@ emg_status emg_solve_steady(emg_ctx* c, double drop, int64_t max_cycles, emg_sol
     int64_t done = 0;
     for (int64_t k = 0; k <= max_cycles; ++k) {
         const int64_t n = c->cycle_n;
-        emg_status st = vcycle_entry(c, n);
+        emg_status st = vcycle_entry(c);
         if (st != EMG_OK) return st;
         st = read_scalars(c);
         if (st != EMG_OK) return st;
@@ -332,7 +448,7 @@ emg_status emg_solve_steady(emg_ctx* c, double drop, int64_t max_cycles, emg_sol
         res = c->sc_host->res;
         if (r0 < 0.0) r0 = res;
         if (res <= drop * r0 || k == max_cycles) break;
-        st = vcycle_body(c);
+        st = run_body(c);
         if (st != EMG_OK) return st;
         c->cycle_n = n + 1;
         ++done;
@@ -352,7 +468,7 @@ emg_status emg_residual_norm(emg_ctx* c, double* res_rho, double* res5) {
     LevelDev& T = c->lv[c->p_max];
     emg_status st = launch_residual(c, c->p_max, T.v, nullptr, T.r2);
     if (st != EMG_OK) return st;
-    st = launch_norm_cfl(c, T.r2, c->cycle_n, 0);
+    st = launch_norm_cfl(c, T.r2, 0);
     if (st != EMG_OK) return st;
     st = read_scalars(c);
     if (st != EMG_OK) return st;
@@ -371,7 +487,8 @@ emg_status emg_residual(emg_ctx* c, int32_t p, const double* u, double* R, int32
         emg_status st = copy_in(c, c->stage_in, u, n, 0);
         if (st != EMG_OK) return st;
         ud = c->stage_in;
-        Rd = c->stage_out;
+        st = stage_out(c, n, &Rd);
+        if (st != EMG_OK) return st;
     }
     emg_status st = launch_residual(c, p, ud, nullptr, Rd);
     if (st != EMG_OK) return st;
@@ -389,7 +506,8 @@ emg_status emg_jacobian_diag(emg_ctx* c, int32_t p, const double* u, double* D, 
         emg_status st = copy_in(c, c->stage_in, u, n, 0);
         if (st != EMG_OK) return st;
         ud = c->stage_in;
-        Dd = c->stage_out;
+        st = stage_out(c, n * B, &Dd);
+        if (st != EMG_OK) return st;
     }
     emg_status st = launch_diag_blocks(c, p, ud, &c->sc->cfl, 0, Dd);
     if (st != EMG_OK) return st;
@@ -471,10 +589,13 @@ emg_status emg_exp1_step(emg_ctx* c, const double* u0, const double* tau0, const
     }
     st = copy_in(c, c->stage_small, dt, c->E, on_device);
     if (st != EMG_OK) return st;
-    st = launch_exp1(c, c->stage_in, tau0 ? c->stage_in2 : nullptr, c->stage_small, c->stage_out);
+    double* so = nullptr;
+    st = stage_out(c, n, &so);
+    if (st != EMG_OK) return st;
+    st = launch_exp1(c, c->stage_in, tau0 ? c->stage_in2 : nullptr, c->stage_small, so);
     if (st != EMG_OK) return st;
     (void)L;
-    st = copy_out(c, u_out, c->stage_out, n, on_device);
+    st = copy_out(c, u_out, so, n, on_device);
     if (st != EMG_OK) return st;
     st = read_scalars(c);
     if (st != EMG_OK) return st;
@@ -516,6 +637,8 @@ const char* emg_profile_class_name(int32_t cls) {
 }
 
 int64_t emg_launch_count(const emg_ctx* c) { return c ? c->launches : 0; }
+
+int64_t emg_graph_kernels(const emg_ctx* c) { return c && c->body_exec ? c->body_kernels : 0; }
 
 emg_status emg_selftest_wait_timeout(emg_ctx* c) {
     if (!c) return EMG_ERR_ARG;

@@ -7,6 +7,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -85,6 +86,7 @@ struct DevScalars {
     int nonfinite;       // non-finite residual seen
     int pad;             // non-positive density or pressure seen
     int timeout;         // a bounded device-side wait gave up
+    long long cycle;     // V-cycle index n of Eq. cfl (advanced on the device by every cycle body)
 };
 
 // Kernel classes of the event profiler (emg_profile_*).
@@ -151,12 +153,18 @@ struct emg_ctx {
     emg::DevScalars* sc_host = nullptr;   // pinned
     double* stage_in = nullptr;  // staging for component calls, [E][5][Nmax]
     double* stage_in2 = nullptr;
-    double* stage_out = nullptr; // [E][B][B] max for jacobian output
+    double* stage_out = nullptr; // output staging of the component calls, grown on demand
+    int64_t stage_out_n = 0;
     double* stage_small = nullptr; // [E] (dt input)
     int64_t cycle_n = 1;
     double res_ref = 0.0;
     emg::Prof prof;
     int64_t launches = 0;            // kernels launched by this context
+    cudaGraphExec_t body_exec = nullptr;  // captured V-cycle body up to the Arnoldi kernel
+    cudaGraphExec_t krylov_exec = nullptr; // the rest of the body, from the Arnoldi kernel on
+    int64_t body_kernels = 0;        // kernels in both
+    bool capturing = false;          // a graph capture is in progress on the stream
+    bool graph_failed = false;       // capture or instantiation failed: launch kernel by kernel
 };
 
 namespace emg {
@@ -209,11 +217,24 @@ emg_status build_float_tables(emg_ctx* c);
 emg_status selftest_barrier_timeout(emg_ctx* c, int* timed_out);
 emg_status launch_bsr0(emg_ctx* c);
 emg_status launch_exp1(emg_ctx* c, const double* u0, const double* tau0, const double* dt, double* out);
+emg_status launch_exp1_prepare(emg_ctx* c, const double* u0, const double* tau0);
+emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, double* out);
+emg_status coop_ordered(int device, cudaStream_t st, const std::function<cudaError_t()>& launch, std::string* err);
 emg_status launch_restrict(emg_ctx* c, int p_fine, const double* fine, double* coarse);
 emg_status launch_tau(emg_ctx* c, int p_coarse, const double* rfine, const double* rcoarse, double* tau);
 emg_status launch_prolong(emg_ctx* c, int p_fine, double* fine, const double* vc, const double* v0c);
-emg_status launch_norm_cfl(emg_ctx* c, const double* R, int64_t n, int update_cfl);
+emg_status launch_norm_cfl(emg_ctx* c, const double* R, int update_cfl);
 emg_status launch_dtau(emg_ctx* c, int p, const double* u, const double* cfl_dev, double factor, double* dt);
 emg_status launch_axpby(emg_ctx* c, int64_t n, double a, const double* x, double b, const double* y, double* out);
 emg_status launch_check_state(emg_ctx* c, const double* u, int64_t n);
+// V-cycle pieces (api.cu), shared with the request loop (server.cu)
+emg_status vcycle_entry(emg_ctx* c);
+emg_status vcycle_body_down(emg_ctx* c);
+emg_status vcycle_body_up(emg_ctx* c);
+emg_status vcycle_body(emg_ctx* c);
+emg_status run_body(emg_ctx* c);
+emg_status check_flags(emg_ctx* c);
+int64_t estimate_bytes(int dim, int64_t E, int64_t F, int64_t F_int, int p_max, int m, int prec);
+DevScalars* pinned_scalars_acquire();
+void pinned_scalars_release(DevScalars* p);
 }  // namespace emg

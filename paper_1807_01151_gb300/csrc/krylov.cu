@@ -10,6 +10,9 @@
 #include <algorithm>
 #include <cmath>
 
+#include <functional>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace emg {
@@ -467,16 +470,58 @@ static Pade13 pade13() {
     return p;
 }
 
-emg_status launch_exp1(emg_ctx* c, const double* u0, const double* tau0, const double* dt, double* out) {
-    LevelDev& L = c->lv[0];
-    const int64_t K0 = 5 * c->E;
-    const int m = c->prm.krylov_m;
-    emg_status st = launch_residual(c, 0, u0, tau0, L.r);
+// ---- ordering of cooperative launches across contexts ---------------------------------------
+// The Arnoldi kernel spins at grid barriers until every one of its blocks is resident.  Two
+// such kernels of different contexts (streams) running at once could each hold part of the
+// device while waiting for the rest.  All cooperative launches on a device are therefore
+// chained through one event: each waits for the previous one before it starts.
+namespace {
+struct CoopGate {
+    std::mutex mu;
+    cudaEvent_t ev = nullptr;
+    bool recorded = false;
+};
+CoopGate g_gate[64];
+}  // namespace
+
+emg_status coop_ordered(int device, cudaStream_t st, const std::function<cudaError_t()>& launch, std::string* err) {
+    CoopGate& g = g_gate[device & 63];
+    std::lock_guard<std::mutex> lk(g.mu);
+    cudaError_t e = cudaSuccess;
+    if (!g.ev) e = cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming);
+    if (e == cudaSuccess && g.recorded) e = cudaStreamWaitEvent(st, g.ev, 0);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(g.ev, st);
+    if (e != cudaSuccess) {
+        if (err) *err = std::string("cooperative launch: ") + cudaGetErrorString(e);
+        return EMG_ERR_CUDA;
+    }
+    g.recorded = true;
+    return EMG_OK;
+}
+
+// EXP1 inputs on p = 0: R~_0(u0) and the block rows of J_0.
+emg_status launch_exp1_prepare(emg_ctx* c, const double* u0, const double* tau0) {
+    emg_status st = launch_residual(c, 0, u0, tau0, c->lv[0].r);
     if (st != EMG_OK) return st;
     st = launch_face_jacobian(c, 0, u0);
     if (st != EMG_OK) return st;
-    st = launch_bsr0(c);
+    return launch_bsr0(c);
+}
+
+emg_status launch_exp1(emg_ctx* c, const double* u0, const double* tau0, const double* dt, double* out) {
+    emg_status st = launch_exp1_prepare(c, u0, tau0);
     if (st != EMG_OK) return st;
+    return launch_exp1_krylov(c, u0, dt, out);
+}
+
+// Arnoldi (one persistent cooperative kernel), phi_1 of the Hessenberg matrix, combination.
+// While a graph is being captured the ordering of cooperative launches is left to the
+// caller (the graph replay is ordered as a whole).
+emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, double* out) {
+    LevelDev& L = c->lv[0];
+    const int64_t K0 = 5 * c->E;
+    const int m = c->prm.krylov_m;
     // one cooperative launch: every block must be co-resident for the grid barriers
     int per_sm = 0, nsm = 0;
     EMG_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi, ARN_THREADS, 0));
@@ -502,8 +547,16 @@ emg_status launch_exp1(emg_ctx* c, const double* u0, const double* tau0, const d
                     &partA, &partB, &partC, &stra, &bar, &budget, &scp};
     {
         ProfScope _ps(c, PC_ARNOLDI);
-        EMG_CUDA_TRY(c, cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3((unsigned)nb), dim3(ARN_THREADS),
-                                                    args, 0, c->stream));
+        auto launch = [&]() {
+            return cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3((unsigned)nb), dim3(ARN_THREADS), args, 0,
+                                               c->stream);
+        };
+        if (c->capturing) {
+            EMG_CUDA_TRY(c, launch());
+        } else {
+            emg_status so = coop_ordered(c->device, c->stream, launch, &c->err);
+            if (so != EMG_OK) return so;
+        }
     }
     const int n = m + 1;
     const size_t smem = (size_t)8 * n * n * sizeof(double);
@@ -543,6 +596,7 @@ constexpr size_t NA_OFF_Y = NA_OFF_H + (size_t)(NA_MAX_M + 1) * NA_MAX_M;
 constexpr size_t NA_OFF_PART = NA_OFF_Y + NA_MAX_M + 8;
 constexpr size_t NA_OFF_SC = NA_OFF_PART + (size_t)3 * NA_BLOCKS * NA_STRIDE;
 constexpr size_t NA_OFF_BAR = NA_OFF_SC + 16;
+static_assert(sizeof(DevScalars) <= 16 * sizeof(double), "cycle scalars outgrew their slot");
 constexpr size_t NA_DOUBLES = NA_OFF_BAR + 8;   // about 26 MB
 
 static __device__ __align__(256) double g_exp1_scratch[NA_DOUBLES];
@@ -612,9 +666,10 @@ extern "C" emg_status emg_exp1_step_noalloc(int32_t dim, int64_t n_elems, const 
     long long budget = 4000000000LL;
     void* args[] = {&K0a, &Ea, &NFa, &ma, (void*)&bsrc, (void*)&nbrc, (void*)&dt, (void*)&r0, &V, &w, &H,
                     &partA, &partB, &partC, &stra, &bar, &budget, &sc};
-    if (cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3((unsigned)nb), dim3(ARN_THREADS), args, 0, st) !=
-        cudaSuccess)
-        return EMG_ERR_CUDA;
+    auto launch = [&]() {
+        return cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3((unsigned)nb), dim3(ARN_THREADS), args, 0, st);
+    };
+    if (coop_ordered(dev, st, launch, nullptr) != EMG_OK) return EMG_ERR_CUDA;
     const int n = krylov_m + 1;
     const size_t smem = (size_t)8 * n * n * sizeof(double);
     if (cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)

@@ -67,7 +67,7 @@ __global__ void k_norm_partial(int64_t E, int N, const double* __restrict__ R, d
     }
 }
 
-__global__ void k_norm_final(int nb, const double* __restrict__ partial, double inv_vol, int64_t n, int p_max,
+__global__ void k_norm_final(int nb, const double* __restrict__ partial, double inv_vol, int p_max,
                              double cfl_max, int update_cfl, DevScalars* sc) {
     if (threadIdx.x != 0) return;
     double s[5] = {0, 0, 0, 0, 0};
@@ -81,7 +81,7 @@ __global__ void k_norm_final(int nb, const double* __restrict__ partial, double 
     if (bad) sc->nonfinite = 1;
     if (update_cfl) {
         if (!(sc->res_ref > 0.0)) sc->res_ref = res;
-        const double ramp = 1.0 + (double)(n - 1) / (2 * p_max + 1);
+        const double ramp = 1.0 + (double)(sc->cycle - 1) / (2 * p_max + 1);
         const double inv = res > 0.0 ? sc->res_ref / res : INFINITY;
         sc->cfl = fmin(cfl_max, fmax(inv, ramp));
     }
@@ -145,11 +145,11 @@ emg_status launch_axpby(emg_ctx* c, int64_t n, double a, const double* x, double
     return EMG_OK;
 }
 
-emg_status launch_norm_cfl(emg_ctx* c, const double* R, int64_t n, int update_cfl) {
+emg_status launch_norm_cfl(emg_ctx* c, const double* R, int update_cfl) {
     const int nb = 152;
     { ProfScope _ps(c, PC_CONTROL); k_norm_partial<<<nb, NORM_THREADS, 0, c->stream>>>(c->E, c->lv[c->p_max].N, R, c->partial); }
     EMG_CHECK_LAUNCH(c);
-    { ProfScope _ps(c, PC_CONTROL); k_norm_final<<<1, 32, 0, c->stream>>>(nb, c->partial, 1.0 / c->domain_volume, n, c->p_max, c->prm.cfl_max,
+    { ProfScope _ps(c, PC_CONTROL); k_norm_final<<<1, 32, 0, c->stream>>>(nb, c->partial, 1.0 / c->domain_volume, c->p_max, c->prm.cfl_max,
                                           update_cfl, c->sc); }
     EMG_CHECK_LAUNCH(c);
     return EMG_OK;

@@ -356,7 +356,8 @@ template <class T>
 static T* dalloc(emg_ctx* c, size_t count) {
     void* p = nullptr;
     if (count == 0) count = 1;
-    if (cudaMalloc(&p, count * sizeof(T)) != cudaSuccess) return nullptr;
+    // stream-ordered: neither this nor the free in emg_destroy waits for other streams' work
+    if (cudaMallocAsync(&p, count * sizeof(T), c->stream) != cudaSuccess) return nullptr;
     cudaMemsetAsync(p, 0, count * sizeof(T), c->stream);
     c->allocs.push_back(p);
     c->bytes += (int64_t)(count * sizeof(T));
@@ -396,23 +397,30 @@ static emg_status build_tables(emg_ctx* c, int nmax, const int* exps_d) {
     return EMG_OK;
 }
 
-int64_t estimate_bytes(int dim, int64_t E, int64_t F, int64_t F_int, int p_max, int m) {
-    int64_t b = 0;
-    const int nf = 2 * dim;
+// Device bytes that setup_device_mesh allocates, item by item (admission control).
+int64_t estimate_bytes(int dim, int64_t E, int64_t F, int64_t F_int, int p_max, int m, int prec) {
+    const int nf = 2 * dim, nn = 1 << dim;
     const int nmax = n_modes(dim, p_max);
-    b += E * ((1 << dim) * dim + 3 + 3 + 3 + nmax * nmax + nmax + 2 * nf) * 8;
-    b += F * 4 * 4;
+    const int64_t Fi1 = std::max<int64_t>(F_int, 1), Fb1 = std::max<int64_t>(F - F_int, 1);
+    int64_t b = 4 * F * 4 + 2 * E * nf * 4 + 2 * E * nn * dim * 8;           // faces, element maps, x, body normals
+    b += E * (3 + 3 + 1 + 1 + 1 + (int64_t)nmax * nmax + nmax) * 8 + 8 * 16 * 8 + (int64_t)nmax * 3 * 4;
     for (int p = 0; p <= p_max; ++p) {
-        const int N = n_modes(dim, p), q = p + 2, Q = ipow(q, dim), QF = ipow(q, dim - 1), B = 5 * N;
-        b += E * (int64_t)Q * N * (1 + dim) * 8;
-        b += F * (int64_t)QF * (3 + 1 + N + 5 + 25) * 8 + F_int * (int64_t)QF * (N + 25) * 8;
-        b += E * (int64_t)5 * N * 6 * 8;
-        if (p > 0) b += E * (int64_t)B * B * 8 + E * (int64_t)B * 4;
+        const int64_t N = n_modes(dim, p), q = p + 2, Q = ipow((int)q, dim), QF = ipow((int)q, dim - 1), B = 5 * N;
+        b += E * Q * N * (1 + dim) * 8;                                         // vpsi, vgw
+        b += F * QF * (3 + 1 + N + 5 + 25) * 8 + Fi1 * QF * (N + 25) * 8 + Fb1 * QF * 3 * 8;
+        b += 6 * E * B * 8;                                                     // v, v0, tau, un, r, r2
+        if (p > 0) {
+            if (prec == EMG_PREC_FP32_BLOCKS)
+                b += E * B * B * 4 + E * Q * N * (1 + dim) * 4 + F * QF * (N + 25) * 4 + Fi1 * QF * (N + 25) * 4;
+            else
+                b += E * B * B * 8;
+            b += E * B * 4;                                                     // pivots
+        }
     }
     const int64_t K0 = 5 * E;
-    b += E * (1 + nf) * 25 * 8 + (m + 3) * K0 * 8 + E * 8;
-    const int Bmax = 5 * nmax;
-    b += E * (int64_t)Bmax * Bmax * 8 + 3 * E * 5 * nmax * 8;
+    b += E * 8 + E * (1 + nf) * 25 * 8 + (m + 1) * K0 * 8 + 2 * K0 * 8 + ((int64_t)(m + 1) * m + 2 * m + 3) * 8;
+    b += 3 * 2 * 160 * (MAX_KRYLOV + 8) * 8 + 16 + (int64_t)sizeof(DevScalars);
+    b += 2 * E * 5 * nmax * 8 + E * 8;                                          // staging for component calls
     return b;
 }
 
@@ -485,7 +493,7 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
     c->dim = D;
     // -- admission --
     const int m_kr = c->prm.krylov_m;
-    const int64_t need = estimate_bytes(D, E, F, F_int, c->p_max, m_kr);
+    const int64_t need = estimate_bytes(D, E, F, F_int, c->p_max, m_kr, c->prm.prec);
     size_t fr = 0, tot = 0;
     EMG_CUDA_TRY(c, cudaMemGetInfo(&fr, &tot));
     if (need > (int64_t)fr) {
@@ -602,11 +610,14 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
     EMG_ALLOC(c->partial, double, 3 * c->red_blocks * (MAX_KRYLOV + 8));
     EMG_ALLOC(c->bar, unsigned int, 4);
     EMG_ALLOC(c->sc, DevScalars, 1);
-    EMG_CUDA_TRY(c, cudaMallocHost(&c->sc_host, sizeof(DevScalars)));
+    c->sc_host = pinned_scalars_acquire();
+    if (!c->sc_host) {
+        c->err = "page-locked host memory for the cycle scalars";
+        return EMG_ERR_OOM;
+    }
     const int Bmax = 5 * nmax;
     EMG_ALLOC(c->stage_in, double, E * Bmax);
     EMG_ALLOC(c->stage_in2, double, E * Bmax);
-    EMG_ALLOC(c->stage_out, double, E * (int64_t)Bmax * Bmax);
     EMG_ALLOC(c->stage_small, double, E);
     // -- device geometry, basis, tables --
     const int qg = c->p_max + 2;

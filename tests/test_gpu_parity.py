@@ -315,3 +315,25 @@ def test_fullsize_vcycles_keep_mirror_symmetry(c2):
     perm = np.array([l * nt + (nt - 1 - k) % nt for l in range(nr) for k in range(nt)])
     sgn = np.array([1.0, 1.0, -1.0, 1.0, 1.0])[:, None] * ((-1.0) ** exponents(2, 4)[:, 1])[None, :]
     assert np.abs(u[perm] * sgn[None] - u).max() < 1e-11 * np.abs(u).max()
+
+
+@pytest.mark.gpu
+def test_graph_replayed_cycles_are_bitwise_the_kernel_by_kernel_cycles():
+    """The V-cycle body captured as a CUDA graph runs the same kernels as the direct
+    launches: the states after several cycles are identical bit for bit, and so are the
+    launch counts."""
+    from paper_1807_01151_gb300 import Solver
+    from workloads import ogrid
+    out = {}
+    for g in (0, 1):
+        for prec in (0, 1):
+            s = Solver(ogrid(16, 8), p_max=3, prec=prec, use_graph=g)
+            l0 = s.launch_count
+            infos = [s.vcycle() for _ in range(6)]
+            out[g, prec] = (s.get_state(), [i["cfl"] for i in infos], s.launch_count - l0, s.graph_kernels)
+            s.close()
+    for prec in (0, 1):
+        np.testing.assert_array_equal(out[0, prec][0], out[1, prec][0])
+        assert out[0, prec][1] == out[1, prec][1]            # CFL_n from the device cycle counter
+        assert out[0, prec][2] == out[1, prec][2]
+        assert out[0, prec][3] == 0 and out[1, prec][3] > 50

@@ -8,6 +8,8 @@ oracle and the CUDA path share nothing but their inputs.
 from .meshes import (BC_INTERIOR, BC_WALL, BC_FARFIELD, BC_EXACT, MeshDesc,
                      ogrid, box, cubed_sphere_shell, named_config)
 from .states import standard_normal_modes
+from .requests import SolveRequest, request_stream
 
 __all__ = ["BC_INTERIOR", "BC_WALL", "BC_FARFIELD", "BC_EXACT", "MeshDesc", "ogrid",
-           "box", "cubed_sphere_shell", "named_config", "standard_normal_modes"]
+           "box", "cubed_sphere_shell", "named_config", "standard_normal_modes",
+           "SolveRequest", "request_stream"]
