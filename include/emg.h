@@ -96,6 +96,10 @@ typedef struct {
                               0: launched kernel by kernel.  The same kernels run either way and
                               give bitwise the same result.  The event profiler, when on, uses
                               the kernel-by-kernel path. */
+    int32_t autotune;      /* 1 (default): at creation, time the variants of the tuned kernels
+                              (FP32 Gauss-Jordan: pivot-loop unrolling) per block size on this
+                              device and use the fastest (cached per process); 0: the first
+                              variant.  Variants compute identically: results do not change. */
 } emg_params;
 
 typedef struct {
@@ -219,6 +223,8 @@ const char* emg_profile_class_name(int32_t cls);
 /* Number of kernels the context has launched since creation (a graph replay counts the
  * kernels it holds). */
 int64_t emg_launch_count(const emg_ctx* ctx);
+/* The tuner's choices and timings for this context (empty when nothing was tuned). */
+const char* emg_tuning(const emg_ctx* ctx);
 /* Kernels in the captured V-cycle graph; 0 before the first cycle, with use_graph = 0, or
  * if the capture failed (then the body runs kernel by kernel). */
 int64_t emg_graph_kernels(const emg_ctx* ctx);

@@ -296,6 +296,7 @@ void emg_default_params(emg_params* p) {
     p->prec = EMG_PREC_FP64;
     p->cuda_stream = nullptr;
     p->use_graph = 1;
+    p->autotune = 1;
 }
 
 const char* emg_build_info(void) {
@@ -637,6 +638,8 @@ const char* emg_profile_class_name(int32_t cls) {
 }
 
 int64_t emg_launch_count(const emg_ctx* c) { return c ? c->launches : 0; }
+
+const char* emg_tuning(const emg_ctx* c) { return c ? c->tuning.c_str() : ""; }
 
 int64_t emg_graph_kernels(const emg_ctx* c) { return c && c->body_exec ? c->body_kernels : 0; }
 

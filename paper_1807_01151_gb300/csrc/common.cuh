@@ -70,6 +70,7 @@ struct LevelDev {
     float* blk32 = nullptr;    // [E][B][B]
     float* fjl32 = nullptr;    // [F][QF][25]  face Jacobians for the FP32 blocks
     float* fjr32 = nullptr;    // [F_int][QF][25]
+    int gj_variant = 0;        // tuned variant of the FP32 Gauss-Jordan kernel
 };
 
 // Small device-side scalars of the cycle (no host round trip inside a V-cycle).
@@ -164,6 +165,7 @@ struct emg_ctx {
     cudaGraphExec_t krylov_exec = nullptr; // the rest of the body, from the Arnoldi kernel on
     int64_t body_kernels = 0;        // kernels in both
     bool capturing = false;          // a graph capture is in progress on the stream
+    std::string tuning;              // variants chosen by the tuner, with their times
     bool graph_failed = false;       // capture or instantiation failed: launch kernel by kernel
 };
 
@@ -214,6 +216,7 @@ emg_status launch_diag_blocks32(emg_ctx* c, int p, const double* u, const double
 emg_status launch_lu32(emg_ctx* c, int p);
 emg_status launch_stage32(emg_ctx* c, int p, const double* r, const double* un, double beta, double* out);
 emg_status build_float_tables(emg_ctx* c);
+emg_status tune_gj(emg_ctx* c);
 emg_status selftest_barrier_timeout(emg_ctx* c, int* timed_out);
 emg_status launch_bsr0(emg_ctx* c);
 emg_status launch_exp1(emg_ctx* c, const double* u0, const double* tau0, const double* dt, double* out);

@@ -6,6 +6,11 @@
 //    upper backward substitution), u^(k) = u^n + beta_k y.
 // T is the block precision (double for the FP64 form, float for the FP32 block form);
 // the residual r, u^n and u^(k) are always double.
+#include <algorithm>
+#include <cstdio>
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace emg {
@@ -121,10 +126,13 @@ __global__ void __launch_bounds__(128) k_stage(int E, const T* __restrict__ lu, 
 
 // Register-tiled Gauss-Jordan inversion with partial pivoting (FP32 block form).
 // 256 threads = 32 (tx) x 8 (ty); thread (tx, ty) keeps rows ty + 8i and columns
-// tx + 32j of the block in registers for the whole elimination.  Per pivot step only the
-// pivot column (colk), the scaled pivot row (rowk) and, on a row interchange, the two
-// swapped rows pass through shared memory.  The inverse is written column-major through
-// a transposing shared tile so that the global stores are coalesced.
+// tx + 32j of the block in registers for the whole elimination.  Pivoting is implicit:
+// rows never move; step k takes the unused row p with the largest |a_pk| (lowest index on
+// ties) as its pivot row, and the permutation is applied when the inverse is stored.  Per
+// step only the pivot column and the scaled pivot row pass through shared memory, double
+// buffered, so a step needs two barriers.  Every warp finds the pivot itself from the
+// shared column (the same data in the same order, hence the same row).  The inverse is
+// written column-major through a transposing shared tile so that the stores coalesce.
 template <int B>
 struct GjTile {
     static constexpr int RS = (B + 7) / 8;    // row slots per thread
@@ -133,15 +141,15 @@ struct GjTile {
     static constexpr size_t SMEM = (size_t)B * LD * sizeof(float);
 };
 
-template <int B>
+template <int B, int UNR>
 __global__ void __launch_bounds__(256) k_gj_tile(int E, float* __restrict__ blk) {
     constexpr int RS = GjTile<B>::RS, CS = GjTile<B>::CS, LD = GjTile<B>::LD;
     constexpr int RP = 8 * RS, CP = 32 * CS;   // zero-padded extents: no bounds checks inside
+    constexpr int MW = (B + 31) / 32;          // words of the used-row mask
     extern __shared__ __align__(16) unsigned char smraw[];
     float* tile = reinterpret_cast<float*>(smraw);
-    __shared__ float colk[RP], rowk[CP], rowx[CP], rowy[CP];
-    __shared__ int s_p;
-    __shared__ int ipiv[B], colidx[B], pos[B];
+    __shared__ float colk[2][RP], rowk[2][CP];
+    __shared__ int perm[B], invp[B];
     const int e = blockIdx.x;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     float* g = blk + (size_t)e * B * B;
@@ -153,154 +161,112 @@ __global__ void __launch_bounds__(256) k_gj_tile(int E, float* __restrict__ blk)
             const int r = ty + 8 * i, c = tx + 32 * j;
             a[i][j] = (r < B && c < B) ? g[r * B + c] : 0.0f;
         }
-    for (int t = threadIdx.x; t < RP; t += 256) colk[t] = 0.0f;
-    for (int t = threadIdx.x; t < CP; t += 256) rowk[t] = rowx[t] = rowy[t] = 0.0f;
-    __syncthreads();
-    // fully unrolled for B <= 100: k, its row slot and column slot are compile-time,
-    // so the register tile is indexed without runtime selects
-    constexpr int UNR = B <= 100 ? B : 1;
+    unsigned used[MW];
+#pragma unroll
+    for (int m = 0; m < MW; ++m) used[m] = 0u;
+    // UNR steps per unrolled body: a variant parameter (the arithmetic is the same for every
+    // UNR; full unrolling makes k compile-time but the code can outgrow the instruction cache)
 #pragma unroll UNR
     for (int k = 0; k < B; ++k) {
-        const int ki = k >> 3, kj = k >> 5;
-        // (1) the pivot column, from the lane that owns column k in every warp
+        const int kb = k & 1, kj = k >> 5;
+        float* ck = colk[kb];
+        float* rk_s = rowk[kb];
+        // (1) the pivot column, from the lane that owns column k (column k is then rebuilt
+        //     by the update: in-place scheme)
         if (tx == (k & 31)) {
 #pragma unroll
             for (int i = 0; i < RS; ++i) {
-                const int r = ty + 8 * i;
                 float v = 0.0f;
 #pragma unroll
                 for (int j = 0; j < CS; ++j)
                     if (j == kj) {
                         v = a[i][j];
-                        a[i][j] = 0.0f;   // column k is rebuilt by the update (in-place scheme)
+                        a[i][j] = 0.0f;
                     }
-                colk[r] = v;
+                ck[ty + 8 * i] = v;
             }
         }
         __syncthreads();
-        // (2) pivot: largest |colk[r]|, r >= k, lowest index on ties
-        if (threadIdx.x < 32) {
-            float best = -1.0f;
-            int bi = k;
-            for (int r = k + tx; r < B; r += 32) {
-                const float v = fabsf(colk[r]);
+        // (2) every warp: the pivot row p among the unused rows
+        float best = -1.0f;
+        int bi = B;
+#pragma unroll
+        for (int m = 0; m < MW; ++m) {
+            const int r = tx + 32 * m;
+            if (r < B && !((used[m] >> tx) & 1u)) {
+                const float v = fabsf(ck[r]);
                 if (v > best) {
                     best = v;
                     bi = r;
                 }
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) {
-                    best = ob;
-                    bi = oi;
-                }
-            }
-            if (tx == 0) {
-                s_p = bi;
-                ipiv[k] = bi;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
             }
         }
-        __syncthreads();
-        const int p = s_p;
-        // (3) interchange rows k and p
-        if (p != k) {
+        if (bi >= B) {
+            // no comparable candidate (a non-finite column): the lowest unused row, so that
+            // every index stays inside the block; the non-finite values propagate
+#pragma unroll
+            for (int m = MW - 1; m >= 0; --m) {
+                const int nv = B - 32 * m < 32 ? B - 32 * m : 32;
+                const unsigned fr = ~used[m] & (nv == 32 ? 0xffffffffu : ((1u << nv) - 1u));
+                if (fr) bi = 32 * m + __ffs((int)fr) - 1;
+            }
+        }
+        const int p = bi;
+#pragma unroll
+        for (int m = 0; m < MW; ++m)
+            if (m == (p >> 5)) used[m] |= 1u << (p & 31);
+        const float inv = 1.0f / ck[p];
+        // (3) the warp that holds row p publishes it scaled (column k of it becomes 1/a_pk)
+        if (ty == (p & 7)) {
             const int pi = p >> 3;
-            if (ty == (k & 7)) {
-#pragma unroll
-                for (int j = 0; j < CS; ++j) {
-                    float v = 0.0f;
-#pragma unroll
-                    for (int i = 0; i < RS; ++i)
-                        if (i == ki) v = a[i][j];
-                    rowx[tx + 32 * j] = v;
-                }
-            }
-            if (ty == (p & 7)) {
-#pragma unroll
-                for (int j = 0; j < CS; ++j) {
-                    float v = 0.0f;
-#pragma unroll
-                    for (int i = 0; i < RS; ++i)
-                        if (i == pi) v = a[i][j];
-                    rowy[tx + 32 * j] = v;
-                }
-            }
-            if (threadIdx.x == 0) {
-                const float t0 = colk[k];
-                colk[k] = colk[p];
-                colk[p] = t0;
-            }
-            __syncthreads();
-            if (ty == (k & 7)) {
-#pragma unroll
-                for (int j = 0; j < CS; ++j) {
-                    const float v = rowy[tx + 32 * j];
-#pragma unroll
-                    for (int i = 0; i < RS; ++i)
-                        if (i == ki) a[i][j] = v;
-                }
-            }
-            if (ty == (p & 7)) {
-#pragma unroll
-                for (int j = 0; j < CS; ++j) {
-                    const float v = rowx[tx + 32 * j];
-#pragma unroll
-                    for (int i = 0; i < RS; ++i)
-                        if (i == pi) a[i][j] = v;
-                }
-            }
-        }
-        // (4) the scaled pivot row (in-place Gauss-Jordan: column k becomes the inverse's)
-        const float inv = 1.0f / colk[k];
-        if (ty == (k & 7)) {
 #pragma unroll
             for (int j = 0; j < CS; ++j) {
                 float v = 0.0f;
 #pragma unroll
                 for (int i = 0; i < RS; ++i)
-                    if (i == ki) v = a[i][j];
+                    if (i == pi) v = a[i][j];
                 const int c = tx + 32 * j;
-                rowk[c] = (c == k ? 1.0f : v) * inv;
+                rk_s[c] = (c == k ? 1.0f : v) * inv;
             }
         }
+        if (threadIdx.x == 0) perm[k] = p;
         __syncthreads();
-        // (5) eliminate column k from every other row (padded rows have colk = 0)
+        // (4) eliminate column k from every other row (padded rows have a zero column entry)
         float rk[CS];
 #pragma unroll
-        for (int j = 0; j < CS; ++j) rk[j] = rowk[tx + 32 * j];
+        for (int j = 0; j < CS; ++j) rk[j] = rk_s[tx + 32 * j];
 #pragma unroll
         for (int i = 0; i < RS; ++i) {
-            if (ty + 8 * i == k) {
+            if (ty + 8 * i == p) {
 #pragma unroll
                 for (int j = 0; j < CS; ++j) a[i][j] = rk[j];
             } else {
-                const float f = colk[ty + 8 * i];
+                const float f = ck[ty + 8 * i];
 #pragma unroll
                 for (int j = 0; j < CS; ++j) a[i][j] -= f * rk[j];
             }
         }
-        __syncthreads();
     }
-    // Undo the row interchanges as column interchanges in reverse order: position j of the
-    // inverse holds working column colidx[j]; thread-owned column c goes to pos[c].
-    if (threadIdx.x == 0) {
-        for (int j = 0; j < B; ++j) colidx[j] = j;
-        for (int k = B - 1; k >= 0; --k) {
-            const int t0 = colidx[k];
-            colidx[k] = colidx[ipiv[k]];
-            colidx[ipiv[k]] = t0;
-        }
-        for (int j = 0; j < B; ++j) pos[colidx[j]] = j;
-    }
+    // Row r of the working matrix holds row invp[r] of the inverse, and its column k holds
+    // column perm[k] (perm[k] = pivot row of step k, invp its inverse permutation).
+    __syncthreads();
+    for (int k = threadIdx.x; k < B; k += 256) invp[perm[k]] = k;
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < RS; ++i)
 #pragma unroll
         for (int j = 0; j < CS; ++j) {
             const int r = ty + 8 * i, c = tx + 32 * j;
-            if (r < B && c < B) tile[pos[c] * LD + r] = a[i][j];
+            if (r < B && c < B) tile[perm[c] * LD + invp[r]] = a[i][j];
         }
     __syncthreads();
     for (int t = threadIdx.x; t < B * B; t += 256) g[t] = tile[(t / B) * LD + (t % B)];
@@ -391,28 +357,149 @@ static emg_status stage_dispatch(emg_ctx* c, int B, const T* lu, const int* piv,
 
 emg_status launch_lu(emg_ctx* c, int p) { return lu_dispatch<double>(c, c->lv[p].B, c->lv[p].blk, c->lv[p].piv); }
 
-// FP32 block form: explicit inverse (Gauss-Jordan), applied by k_stage_gemv.
-emg_status launch_lu32(emg_ctx* c, int p) {
-    LevelDev& L = c->lv[p];
-    const unsigned E = (unsigned)c->E;
-    switch (L.B) {
-#define EMG_GJ_CASE(BB)                                                                                      \
-    case BB: {                                                                                               \
-        const size_t sm = GjTile<BB>::SMEM;                                                                  \
-        EMG_CUDA_TRY(c, cudaFuncSetAttribute(k_gj_tile<BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
-        {                                                                                                    \
-            ProfScope _ps(c, PC_LU);                                                                         \
-            k_gj_tile<BB><<<E, 256, sm, c->stream>>>((int)E, L.blk32);                                       \
-        }                                                                                                    \
-        EMG_CHECK_LAUNCH(c);                                                                                 \
-        return EMG_OK;                                                                                       \
+// ---- variants of the FP32 Gauss-Jordan kernel and their tuning --------------------------------
+// Variant v unrolls the pivot loop kGjUnroll[v] times (0 = fully, only for B <= 100).  The
+// variants do the same arithmetic in the same order, so the choice never changes a result.
+constexpr int kGjUnroll[] = {1, 4, 16, 0};
+constexpr int kGjVariants = 4;
+
+template <int B>
+static bool gj_variant_valid(int v) {
+    return v >= 0 && v < kGjVariants && (kGjUnroll[v] != 0 || B <= 100);
+}
+
+template <int B, int U>
+static cudaError_t gj_go(unsigned E, float* blk, cudaStream_t st) {
+    const size_t sm = GjTile<B>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k_gj_tile<B, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_gj_tile<B, U><<<E, 256, sm, st>>>((int)E, blk);
+    return cudaGetLastError();
+}
+
+template <int B>
+static cudaError_t gj_launch(int v, unsigned E, float* blk, cudaStream_t st) {
+    switch (v) {
+        case 1: return gj_go<B, 4>(E, blk, st);
+        case 2: return gj_go<B, 16>(E, blk, st);
+        case 3: return gj_go<B, (B <= 100 ? B : 1)>(E, blk, st);
+        default: return gj_go<B, 1>(E, blk, st);
     }
+}
+
+static cudaError_t gj_dispatch(int B, int v, unsigned E, float* blk, cudaStream_t st, bool* ok) {
+    *ok = true;
+    switch (B) {
+#define EMG_GJ_CASE(BB) \
+    case BB:            \
+        return gj_variant_valid<BB>(v) ? gj_launch<BB>(v, E, blk, st) : gj_launch<BB>(0, E, blk, st);
         EMG_BSIZES(EMG_GJ_CASE)
 #undef EMG_GJ_CASE
         default:
-            c->err = "unsupported block size";
-            return EMG_ERR_ARG;
+            *ok = false;
+            return cudaSuccess;
     }
+}
+
+static bool gj_valid(int B, int v) {
+    switch (B) {
+#define EMG_GJ_CASE(BB) \
+    case BB:            \
+        return gj_variant_valid<BB>(v);
+        EMG_BSIZES(EMG_GJ_CASE)
+#undef EMG_GJ_CASE
+        default:
+            return false;
+    }
+}
+
+// Deterministic, diagonally dominant stand-in blocks for timing the variants.
+__global__ void k_fill_tuning_blocks(int64_t n, int B, float* __restrict__ blk) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * B * B) return;
+    const int c = (int)(t % B), r = (int)((t / B) % B);
+    const uint32_t h = (uint32_t)(t * 2654435761ull) ^ (uint32_t)(t >> 13);
+    blk[t] = (r == c ? (float)B : 0.0f) + ((float)(h & 0xffffu) / 65536.0f - 0.5f);
+}
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_gj_best;   // (device, B) -> variant
+}  // namespace
+
+// Times every valid variant on min(E, 2048) stand-in blocks per block size of the FP32 levels
+// and keeps the fastest, once per (device, B) for the process.
+emg_status tune_gj(emg_ctx* c) {
+    if (c->prm.prec != EMG_PREC_FP32_BLOCKS) return EMG_OK;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (int p = 1; p <= c->p_max; ++p) {
+        LevelDev& L = c->lv[p];
+        const auto key = std::make_pair(c->device, L.B);
+        if (!c->prm.autotune) {
+            L.gj_variant = 0;
+            continue;
+        }
+        auto it = g_gj_best.find(key);
+        if (it != g_gj_best.end()) {
+            L.gj_variant = it->second;
+            c->tuning += "gj B=" + std::to_string(L.B) + ": unroll " + std::to_string(kGjUnroll[it->second]) +
+                         " (tuned earlier in this process); ";
+            continue;
+        }
+        const int64_t n = std::min<int64_t>(c->E, 2048);
+        float* scratch = nullptr;
+        EMG_CUDA_TRY(c, cudaMallocAsync((void**)&scratch, (size_t)n * L.B * L.B * sizeof(float), c->stream));
+        k_fill_tuning_blocks<<<(unsigned)((n * L.B * L.B + 255) / 256), 256, 0, c->stream>>>(n, L.B, scratch);
+        cudaEvent_t e0, e1;
+        EMG_CUDA_TRY(c, cudaEventCreate(&e0));
+        EMG_CUDA_TRY(c, cudaEventCreate(&e1));
+        int best = 0;
+        float best_ms = 1e30f;
+        std::string note = "gj B=" + std::to_string(L.B) + ":";
+        for (int v = 0; v < kGjVariants; ++v) {
+            if (!gj_valid(L.B, v)) continue;
+            bool ok = true;
+            float ms = 1e30f;
+            for (int rep = 0; rep < 3 && ok; ++rep) {
+                EMG_CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+                EMG_CUDA_TRY(c, gj_dispatch(L.B, v, (unsigned)n, scratch, c->stream, &ok));
+                EMG_CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+                EMG_CUDA_TRY(c, cudaEventSynchronize(e1));
+                float t = 0.0f;
+                EMG_CUDA_TRY(c, cudaEventElapsedTime(&t, e0, e1));
+                if (rep > 0) ms = std::min(ms, t);   // the first run warms up
+            }
+            char buf[64];
+            std::snprintf(buf, sizeof(buf), " unroll %d %.3f ms", kGjUnroll[v], ms);
+            note += buf;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = v;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        EMG_CUDA_TRY(c, cudaFreeAsync(scratch, c->stream));
+        g_gj_best[key] = best;
+        L.gj_variant = best;
+        c->tuning += note + " -> unroll " + std::to_string(kGjUnroll[best]) + "; ";
+    }
+    return EMG_OK;
+}
+
+// FP32 block form: explicit inverse (Gauss-Jordan), applied by k_stage_gemv.
+emg_status launch_lu32(emg_ctx* c, int p) {
+    LevelDev& L = c->lv[p];
+    bool ok = true;
+    {
+        ProfScope _ps(c, PC_LU);
+        EMG_CUDA_TRY(c, gj_dispatch(L.B, L.gj_variant, (unsigned)c->E, L.blk32, c->stream, &ok));
+    }
+    if (!ok) {
+        c->err = "unsupported block size";
+        return EMG_ERR_ARG;
+    }
+    return EMG_OK;
 }
 
 emg_status launch_stage(emg_ctx* c, int p, const double* r, const double* un, double beta, double* out) {

@@ -62,79 +62,108 @@ __global__ void __launch_bounds__(128) k_face_flux(int F, int F_int, const int* 
     for (int a = 0; a < 5; ++a) fhat[idx * 5 + a] = am * Fl[a];
 }
 
+// k_volume: a block holds ET elements.  Thread (element, mode i) accumulates the five
+// variables of R_{e,a,i} in registers, so one table value feeds five FMAs.  The point
+// fluxes are staged in shared memory QC points at a time (all Q in 2-D; chunks in 3-D),
+// so that 3-D elements still fill the block.
 template <int D, int P>
 struct VolCfg {
     using L = Lv<D, P>;
-    static constexpr int per = L::Q * D * 5 * 8 + L::B * 8;
-    static constexpr int ET = (24576 / per) < 1 ? 1 : ((24576 / per) > 8 ? 8 : (24576 / per));
+    static constexpr int THREADS = L::N >= 20 ? 256 : 128;
+    static constexpr int ET = THREADS / L::N;                        // elements per block
+    static constexpr int FS = 6;                                       // padded variable stride
+    static constexpr int QC0 = 36864 / (ET * D * FS * 8);
+    static constexpr int QC = P == 0 ? 1 : (QC0 < L::Q ? (QC0 < 1 ? 1 : QC0) : L::Q);   // points per chunk
 };
 
 template <int D, int P>
-__global__ void __launch_bounds__(128) k_volume(int E, const double* __restrict__ u, const double* __restrict__ vpsi,
-                                                const double* __restrict__ vgw, const int* __restrict__ elem_face,
-                                                const double* __restrict__ fpsiL, const double* __restrict__ fpsiR,
-                                                const double* __restrict__ fhat, const double* __restrict__ tau,
-                                                double g, double* __restrict__ R) {
+__global__ void __launch_bounds__(VolCfg<D, P>::THREADS) k_volume(
+    int E, const double* __restrict__ u, const double* __restrict__ vpsi, const double* __restrict__ vgw,
+    const int* __restrict__ elem_face, const double* __restrict__ fpsiL, const double* __restrict__ fpsiR,
+    const double* __restrict__ fhat, const double* __restrict__ tau, double g, double* __restrict__ R) {
     using L = Lv<D, P>;
+    using CF = VolCfg<D, P>;
     constexpr int N = L::N, Q = L::Q, QF = L::QF, B = L::B, NF = L::NF;
-    constexpr int ET = VolCfg<D, P>::ET;
+    constexpr int ET = CF::ET, QC = CF::QC, FS = CF::FS, T = CF::THREADS;
     __shared__ double us[ET][B];
-    __shared__ double Fs[ET][Q][D][5];
+    __shared__ __align__(16) double Fs[ET][QC][D][FS];
     const int e0 = blockIdx.x * ET;
-    for (int t = threadIdx.x; t < ET * B; t += blockDim.x) {
+    for (int t = threadIdx.x; t < ET * B; t += T) {
         const int el = t / B, r = t % B, e = e0 + el;
         us[el][r] = e < E ? u[(size_t)e * B + r] : 0.0;
     }
-    __syncthreads();
+    const int el2 = threadIdx.x / N, i2 = threadIdx.x % N;   // this thread's (element, mode)
+    const int e2 = e0 + el2;
+    const bool own = el2 < ET && e2 < E;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     if (P > 0) {
-        for (int t = threadIdx.x; t < ET * Q; t += blockDim.x) {
-            const int el = t / Q, q = t % Q, e = e0 + el;
-            if (e >= E) continue;
-            const double* ps = vpsi + ((size_t)e * Q + q) * N;
-            double U[5];
+        for (int q0 = 0; q0 < Q; q0 += QC) {
+            const int nq = (Q - q0) < QC ? (Q - q0) : QC;
+            __syncthreads();   // us staged / previous chunk consumed
+            // (1) U_h and the Euler flux at the chunk's points
+            for (int t = threadIdx.x; t < ET * nq; t += T) {
+                const int el = t / nq, qq = t % nq, e = e0 + el;
+                if (e >= E) continue;
+                const double* ps = vpsi + ((size_t)e * Q + q0 + qq) * N;
+                double U[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-            for (int a = 0; a < 5; ++a) {
-                double s = 0.0;
+                for (int i = 0; i < N; ++i) {
+                    const double w = ps[i];
 #pragma unroll
-                for (int i = 0; i < N; ++i) s += us[el][a * N + i] * ps[i];
-                U[a] = s;
+                    for (int a = 0; a < 5; ++a) U[a] += us[el][a * N + i] * w;
+                }
+                double Fk[3][5];
+                flux_k(U, g, Fk);
+#pragma unroll
+                for (int k = 0; k < D; ++k)
+#pragma unroll
+                    for (int a = 0; a < 5; ++a) Fs[el][qq][k][a] = Fk[k][a];
             }
-            double Fk[3][5];
-            flux_k(U, g, Fk);
+            __syncthreads();
+            // (2) projection on the gradients: acc_a += sum_q sum_k W_q d_k psi_i F_k,a
+            if (own) {
 #pragma unroll
-            for (int k = 0; k < D; ++k)
-#pragma unroll
-                for (int a = 0; a < 5; ++a) Fs[el][q][k][a] = Fk[k][a];
-        }
-        __syncthreads();
-    }
-    for (int t = threadIdx.x; t < ET * B; t += blockDim.x) {
-        const int el = t / B, r = t % B, e = e0 + el;
-        if (e >= E) continue;
-        const int a = r / N, i = r % N;
-        double acc = 0.0;
-        if (P > 0) {
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                const double* gw = vgw + (((size_t)e * D + k) * Q) * N + i;
+                for (int k = 0; k < D; ++k) {
+                    const double* gw = vgw + (((size_t)e2 * D + k) * Q + q0) * N + i2;
 #pragma unroll 4
-                for (int q = 0; q < Q; ++q) acc += gw[(size_t)q * N] * Fs[el][q][k][a];
+                    for (int qq = 0; qq < nq; ++qq) {
+                        const double w = gw[(size_t)qq * N];
+                        const double* f = Fs[el2][qq][k];
+                        const double2 f01 = *reinterpret_cast<const double2*>(f);
+                        const double2 f23 = *reinterpret_cast<const double2*>(f + 2);
+                        acc[0] += w * f01.x;
+                        acc[1] += w * f01.y;
+                        acc[2] += w * f23.x;
+                        acc[3] += w * f23.y;
+                        acc[4] += w * f[4];
+                    }
+                }
             }
         }
-#pragma unroll
-        for (int lf = 0; lf < NF; ++lf) {
-            const int code = elem_face[(size_t)e * NF + lf];
-            const int f = code >> 1;
-            const double* ps = (code & 1) ? fpsiR : fpsiL;
-            double s = 0.0;
-#pragma unroll
-            for (int t2 = 0; t2 < QF; ++t2)
-                s += ps[((size_t)f * QF + t2) * N + i] * fhat[((size_t)f * QF + t2) * 5 + a];
-            acc += (code & 1) ? s : -s;
-        }
-        if (tau) acc += tau[(size_t)e * B + r];
-        R[(size_t)e * B + r] = acc;
     }
+    if (!own) return;
+    // (3) faces: -(L side) / +(R side) sum_t psi_i(x_t) w|n dS| F~_a
+#pragma unroll
+    for (int lf = 0; lf < NF; ++lf) {
+        const int code = elem_face[(size_t)e2 * NF + lf];
+        const int f = code >> 1;
+        const double* ps = ((code & 1) ? fpsiR : fpsiL) + (size_t)f * QF * N + i2;
+        const double* fh = fhat + (size_t)f * QF * 5;
+        double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll 2
+        for (int t2 = 0; t2 < QF; ++t2) {
+            const double w = ps[(size_t)t2 * N];
+#pragma unroll
+            for (int a = 0; a < 5; ++a) s[a] += w * fh[t2 * 5 + a];
+        }
+        const double sg = (code & 1) ? 1.0 : -1.0;
+#pragma unroll
+        for (int a = 0; a < 5; ++a) acc[a] += sg * s[a];
+    }
+    double* Re = R + (size_t)e2 * B + i2;
+    const double* te = tau ? tau + (size_t)e2 * B + i2 : nullptr;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) Re[a * N] = te ? acc[a] + te[a * N] : acc[a];
 }
 
 emg_status launch_residual(emg_ctx* c, int p, const double* u, const double* tau, double* R) {
@@ -150,7 +179,7 @@ emg_status launch_residual(emg_ctx* c, int p, const double* u, const double* tau
             F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL, L.fpsiR, L.fwn, u, g, ui, L.fhat); }     \
         EMG_CHECK_LAUNCH(c);                                                                                   \
         constexpr int ET = VolCfg<DD, PP>::ET;                                                                 \
-        { ProfScope _ps(c, PC_RES_VOL); k_volume<DD, PP><<<(unsigned)((E + ET - 1) / ET), 128, 0, c->stream>>>(                                \
+        { ProfScope _ps(c, PC_RES_VOL); k_volume<DD, PP><<<(unsigned)((E + ET - 1) / ET), VolCfg<DD, PP>::THREADS, 0, c->stream>>>(    \
             E, u, L.vpsi, L.vgw, c->elem_face, L.fpsiL, L.fpsiR, L.fhat, tau, g, R); }                           \
         EMG_CHECK_LAUNCH(c);                                                                                   \
     }

@@ -653,6 +653,8 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
     if (c->prm.prec == EMG_PREC_FP32_BLOCKS) {
         st = build_float_tables(c);
         if (st != EMG_OK) return st;
+        st = tune_gj(c);
+        if (st != EMG_OK) return st;
     }
     std::vector<double> hv(E);
     EMG_CUDA_TRY(c, cudaMemcpyAsync(hv.data(), c->vol, E * 8, cudaMemcpyDeviceToHost, c->stream));

@@ -337,3 +337,20 @@ def test_graph_replayed_cycles_are_bitwise_the_kernel_by_kernel_cycles():
         assert out[0, prec][1] == out[1, prec][1]            # CFL_n from the device cycle counter
         assert out[0, prec][2] == out[1, prec][2]
         assert out[0, prec][3] == 0 and out[1, prec][3] > 50
+
+
+@pytest.mark.gpu
+def test_tuned_kernel_variants_give_bitwise_the_same_cycles():
+    """The tuner only picks among variants that compute identically."""
+    from paper_1807_01151_gb300 import Solver
+    from workloads import ogrid
+    out, notes = [], []
+    for at in (0, 1):
+        s = Solver(ogrid(16, 8), p_max=4, prec=1, autotune=at)
+        for _ in range(4):
+            s.vcycle(info=False)
+        out.append(s.get_state())
+        notes.append(s.tuning)
+        s.close()
+    np.testing.assert_array_equal(out[0], out[1])
+    assert notes[0] == "" and "gj B=75" in notes[1] and "gj B=15" in notes[1]
