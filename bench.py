@@ -30,7 +30,11 @@ WORKLOADS = {
     "cyl32x16_p2": dict(name="cyl32x16_p2", n_theta=32, n_r=16, p_max=2, mach=0.3),
 }
 METRIC = "time to 1e-10 residual drop & DG residual GDoF/s: mixed vs FP64, 1 GB300"
-FP64_PEAK_TFLOPS = 1.254     # FP64 FMA throughput measured on this machine's GB300
+FP64_PEAK_TFLOPS = 1.254     # FP64 FMA throughput of a GB300, measured with a register-only FMA loop
+# DRAM bytes (read + write) of one k_volume launch at p = 4 on the 128 x 64 O-grid, from an ncu
+# capture of this kernel (dram__bytes_read.sum + dram__bytes_write.sum); None once the kernel
+# changes until it is captured again.
+VOLUME_P4_TRAFFIC = {"cyl128x64_p4": 142.427e6}
 PREC_NAMES = {0: "fp64", 1: "fp32_blocks"}
 
 
@@ -48,6 +52,8 @@ def parse():
                     help="run the seeded stream of served cylinder solves through the request loop instead")
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--max-active", type=int, default=8)
+    ap.add_argument("--stall-cycles", type=int, default=100,
+                    help="served solves that set no new residual minimum for this many cycles end early")
     return ap.parse_args()
 
 
@@ -211,6 +217,13 @@ def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks):
     e1.record(stream)
     torch.cuda.synchronize()
     res_ms = e0.elapsed_time(e1) / nres
+    # the same loop with the event profiler: per-launch time of each residual kernel at p_max
+    s.profile(True)
+    for _ in range(nres):
+        s.residual(W["p_max"], u, R)
+    rprof = s.profile_read()
+    s.profile(False)
+    vol_launch_ms = rprof["residual_volume"][0] / rprof["residual_volume"][1]
     out["residual_gdofs"] = K / (res_ms * 1e-3) / 1e9
     out["residual_ms"] = res_ms
     # end to end through the C ABI with host buffers: H2D state, V-cycle, D2H state + info
@@ -234,20 +247,25 @@ def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks):
         out["time_to_1e-10"] = {"seconds": time.perf_counter() - t0, "cycles": rep["cycles"],
                                 "converged": rep["converged"],
                                 "drop": rep["res_final"] / rep["res0"] if rep["res0"] else None}
-    # per-class kernel times over the timed region and the roofline of the dominant class
+    # per-class kernel times over the timed region; the roofline of the dominant FP64
+    # kernel, k_volume at p_max, per launch (algorithmic FLOPs / live launch time)
     work = perfmodel.vcycle_work(2, W["p_max"], E, F)
     out["kernels"] = {k: {"ms_per_cycle": v[0] / args.steps, "launches_per_cycle": v[1] / args.steps}
                       for k, v in prof.items() if v[1]}
-    fp64_classes = [k for k in prof if k in work and not (prec == 1 and k in ("diag_block_assembly", "block_lu",
-                                                                             "prk_stage_solve"))]
-    top = max(fp64_classes, key=lambda k: prof[k][0])
-    t_top = prof[top][0] * 1e-3 / args.steps
-    achieved = work[top][0] / t_top / 1e12
-    out["roofline"] = {"bound": "alu", "kernel": top, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                       "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                       "peak_source": "FP64 FMA throughput measured on GB300 (1.254 TFLOP/s), DESIGN.md",
-                       "algorithmic_flops_per_cycle": work[top][0], "ms_per_cycle": t_top * 1e3,
-                       "launches_per_cycle": prof[top][1] / args.steps}
+    fl = perfmodel.residual_volume_flops(perfmodel.Shape(2, W["p_max"], E, F))
+    achieved = fl / (vol_launch_ms * 1e-3) / 1e12
+    out["roofline"] = {"bound": "alu", "kernel": f"k_volume<2,{W['p_max']}> (DG residual, volume + face projection)",
+                       "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": achieved / FP64_PEAK_TFLOPS, "traffic": VOLUME_P4_TRAFFIC.get(W["name"]),
+                       "peak_source": "FP64 FMA throughput of a GB300 measured with a register-only FMA loop",
+                       "algorithmic_flops_per_launch": fl, "ms_per_launch": vol_launch_ms,
+                       "note": "FMA-only flop model; ncu shows the FP64 pipe 87.6 % busy for this kernel"}
+    if prec == 0:
+        top = "diag_block_assembly"
+        t_top = prof[top][0] * 1e-3 / args.steps
+        out["assembly_roofline"] = {"bound": "alu", "achieved": work[top][0] / t_top / 1e12, "peak": FP64_PEAK_TFLOPS,
+                                    "unit": "TFLOP/s", "frac": work[top][0] / t_top / 1e12 / FP64_PEAK_TFLOPS,
+                                    "ms_per_cycle": t_top * 1e3}
     s.close()
     return out
 
@@ -278,7 +296,8 @@ def run_serve(args, rank, world, local):
         torch.distributed.barrier()
     outdir = os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ROOT
     clocks = Clocks(local, os.path.join(outdir, f"clocks_rank{rank}_serve.csv"))
-    out, summ = serving.serve_stream(reqs, make_mesh, max_active=args.max_active, prec=1)
+    out, summ = serving.serve_stream(reqs, make_mesh, max_active=args.max_active, prec=1,
+                                     stall_cycles=args.stall_cycles)
     clk = clocks.stop()
     span = summ["makespan_s"]
     if world > 1:
@@ -293,12 +312,18 @@ def run_serve(args, rank, world, local):
             "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": f"served_cylinder_stream_{len(reqs)}", "seed": 1807, "arrivals": "Poisson, 4/s",
                        "grids": "32x16, 64x32, 128x64, 256x128", "p": "1..4", "mach": "U[0.1, 0.5]",
-                       "form": "fp32_blocks", "max_active": args.max_active,
+                       "form": "fp32_blocks", "max_active": args.max_active, "stall_cycles": args.stall_cycles,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "p50_s": summ["p50_s"], "p99_s": summ["p99_s"], "makespan_s": span,
             "converged": summ["converged"], "requests": summ["requests"], "peak_active": summ["peak_active"],
             "cycles_total": summ["cycles_total"], "clocks": clk,
-            "failed": [dict(id=r["id"], status=r["status_name"]) for r in out if r["status"] != 0],
+            "failed": [dict(id=r["id"], status=r["status_name"], cycles=r["cycles"],
+                            drop=(r["res_final"] / r["res0"]) if r["res0"] > 0 else None,
+                            grid=f"{reqs[k].n_theta}x{reqs[k].n_r}", p=reqs[k].p, mach=round(reqs[k].mach, 3))
+                       for k, r in enumerate(out) if r["status"] != 0],
+            "per_request": [dict(grid=f"{reqs[k].n_theta}x{reqs[k].n_r}", p=reqs[k].p, mach=round(reqs[k].mach, 3),
+                                 status=r["status_name"], cycles=r["cycles"],
+                                 ttc_s=round(r["time_to_converge"], 3)) for k, r in enumerate(out)],
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -349,7 +374,7 @@ def main():
         for p in precs[1:]:
             r = res[p]
             line[PREC_NAMES[p]] = {k: r[k] for k in ("value", "ms_per_step", "residual_gdofs", "time_to_1e-10",
-                                                     "gpu_launches", "roofline", "kernels") if k in r}
+                                                     "gpu_launches", "assembly_roofline", "kernels") if k in r}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
