@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <map>
 #include <mutex>
+#include <string>
 
 #include "common.cuh"
 
@@ -357,15 +358,153 @@ static emg_status stage_dispatch(emg_ctx* c, int B, const T* lu, const int* piv,
 
 emg_status launch_lu(emg_ctx* c, int p) { return lu_dispatch<double>(c, c->lv[p].B, c->lv[p].blk, c->lv[p].piv); }
 
+// Column-owner form of the same Gauss-Jordan inversion: W warps per element; lane tx owns
+// rows tx + 32i, warp w owns columns w + W j.  At step k only the warp owning column k
+// searches for the pivot (its lanes hold the whole column) and publishes the column and
+// the pivot row index; every warp then takes the pivot row's entries for its own columns
+// from lane (p mod 32) by shuffles.  One barrier per step (the published column is double
+// buffered).  Pivot choice, tie rule and every multiply-add are those of k_gj_tile, so
+// both forms give bitwise the same inverse.
+template <int B, int W>
+struct GjCols {
+    static constexpr int RS = (B + 31) / 32;   // row slots per thread
+    static constexpr int CS = (B + W - 1) / W; // column slots per thread
+    static constexpr int LD = (B % 2) ? B + 2 : B + 1;
+    static constexpr size_t SMEM = (size_t)B * LD * sizeof(float);
+};
+
+template <int B, int W>
+__global__ void __launch_bounds__(32 * W) k_gj_cols(int E, float* __restrict__ blk) {
+    using G = GjCols<B, W>;
+    constexpr int RS = G::RS, CS = G::CS, LD = G::LD, T = 32 * W;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float* tile = reinterpret_cast<float*>(smraw);
+    __shared__ float colk[2][32 * RS];
+    __shared__ int s_p[2];
+    __shared__ int perm[B], invp[B];
+    const int e = blockIdx.x;
+    const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float* g = blk + (size_t)e * B * B;
+    for (int t = threadIdx.x; t < B * B; t += T) tile[(t / B) * LD + (t % B)] = g[t];
+    __syncthreads();
+    float a[RS][CS];
+#pragma unroll
+    for (int i = 0; i < RS; ++i)
+#pragma unroll
+        for (int j = 0; j < CS; ++j) {
+            const int r = tx + 32 * i, c = w + W * j;
+            a[i][j] = (r < B && c < B) ? tile[r * LD + c] : 0.0f;
+        }
+    unsigned used = 0u;   // bit i: row tx + 32 i has been a pivot row
+#pragma unroll 1
+    for (int k = 0; k < B; ++k) {
+        const int kb = k & 1, wk = k % W, jk = k / W;
+        if (w == wk) {
+            // (1) column k (then zeroed: in-place scheme), pivot among the unused rows
+            float v[RS];
+            float best = -1.0f;
+            int bi = B, lo = B;
+#pragma unroll
+            for (int i = 0; i < RS; ++i) {
+                float x = 0.0f;
+#pragma unroll
+                for (int j = 0; j < CS; ++j)
+                    if (j == jk) {
+                        x = a[i][j];
+                        a[i][j] = 0.0f;
+                    }
+                v[i] = x;
+                const int r = tx + 32 * i;
+                if (r < B && !((used >> i) & 1u)) {
+                    const float m = fabsf(x);
+                    if (m > best) {
+                        best = m;
+                        bi = r;
+                    }
+                    if (r < lo) lo = r;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                const int ol = __shfl_xor_sync(0xffffffffu, lo, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+                lo = ol < lo ? ol : lo;
+            }
+            // no comparable candidate (a non-finite column): the lowest unused row
+            const int p = bi < B ? bi : lo;
+#pragma unroll
+            for (int i = 0; i < RS; ++i) colk[kb][tx + 32 * i] = v[i];
+            if (tx == 0) {
+                s_p[kb] = p;
+                perm[k] = p;
+            }
+        }
+        __syncthreads();
+        // (2) every warp: the scaled pivot row on its own columns, then the elimination
+        const int p = s_p[kb];
+        const float inv = 1.0f / colk[kb][p];
+        const int pl = p & 31, pi = p >> 5;
+        if (tx == pl) used |= 1u << pi;
+        float f[RS];
+#pragma unroll
+        for (int i = 0; i < RS; ++i) f[i] = colk[kb][tx + 32 * i];
+#pragma unroll
+        for (int j = 0; j < CS; ++j) {
+            float x = 0.0f;
+#pragma unroll
+            for (int i = 0; i < RS; ++i)
+                if (i == pi) x = a[i][j];
+            x = __shfl_sync(0xffffffffu, x, pl);
+            const float rk = (w + W * j == k ? 1.0f : x) * inv;
+#pragma unroll
+            for (int i = 0; i < RS; ++i) {
+                if (tx + 32 * i == p)
+                    a[i][j] = rk;
+                else
+                    a[i][j] -= f[i] * rk;
+            }
+        }
+    }
+    // Row r of the working matrix holds row invp[r] of the inverse, and its column k holds
+    // column perm[k]; written column-major through the shared tile.
+    __syncthreads();
+    for (int t = threadIdx.x; t < B; t += T) invp[perm[t]] = t;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RS; ++i)
+#pragma unroll
+        for (int j = 0; j < CS; ++j) {
+            const int r = tx + 32 * i, c = w + W * j;
+            if (r < B && c < B) tile[perm[c] * LD + invp[r]] = a[i][j];
+        }
+    __syncthreads();
+    for (int t = threadIdx.x; t < B * B; t += T) g[t] = tile[(t / B) * LD + (t % B)];
+}
+
 // ---- variants of the FP32 Gauss-Jordan kernel and their tuning --------------------------------
 // Variant v unrolls the pivot loop kGjUnroll[v] times (0 = fully, only for B <= 100).  The
 // variants do the same arithmetic in the same order, so the choice never changes a result.
+// Variants 4..8 are the column-owner form with kGjWarps[v - 4] warps per element (valid
+// while a thread's share of the block stays at most 128 values).
 constexpr int kGjUnroll[] = {1, 4, 16, 0};
-constexpr int kGjVariants = 4;
+constexpr int kGjWarps[] = {1, 2, 4, 8, 16};
+constexpr int kGjVariants = 9;
 
 template <int B>
 static bool gj_variant_valid(int v) {
-    return v >= 0 && v < kGjVariants && (kGjUnroll[v] != 0 || B <= 100);
+    if (v < 0 || v >= kGjVariants) return false;
+    if (v < 4) return kGjUnroll[v] != 0 || B <= 100;
+    const int W = kGjWarps[v - 4];
+    return ((B + 31) / 32) * ((B + W - 1) / W) <= 128 && W <= (B + 31) / 32 * 8;
+}
+
+static std::string gj_variant_name(int v) {
+    return v < 4 ? "tile unroll " + std::to_string(kGjUnroll[v]) : "cols " + std::to_string(kGjWarps[v - 4]) + " warps";
 }
 
 template <int B, int U>
@@ -377,9 +516,23 @@ static cudaError_t gj_go(unsigned E, float* blk, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <int B, int W>
+static cudaError_t gj_cols_go(unsigned E, float* blk, cudaStream_t st) {
+    const size_t sm = GjCols<B, W>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k_gj_cols<B, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_gj_cols<B, W><<<E, 32 * W, sm, st>>>((int)E, blk);
+    return cudaGetLastError();
+}
+
 template <int B>
 static cudaError_t gj_launch(int v, unsigned E, float* blk, cudaStream_t st) {
     switch (v) {
+        case 4: return gj_cols_go<B, 1>(E, blk, st);
+        case 5: return gj_cols_go<B, 2>(E, blk, st);
+        case 6: return gj_cols_go<B, 4>(E, blk, st);
+        case 7: return gj_cols_go<B, 8>(E, blk, st);
+        case 8: return gj_cols_go<B, 16>(E, blk, st);
         case 1: return gj_go<B, 4>(E, blk, st);
         case 2: return gj_go<B, 16>(E, blk, st);
         case 3: return gj_go<B, (B <= 100 ? B : 1)>(E, blk, st);
@@ -442,7 +595,7 @@ emg_status tune_gj(emg_ctx* c) {
         auto it = g_gj_best.find(key);
         if (it != g_gj_best.end()) {
             L.gj_variant = it->second;
-            c->tuning += "gj B=" + std::to_string(L.B) + ": unroll " + std::to_string(kGjUnroll[it->second]) +
+            c->tuning += "gj B=" + std::to_string(L.B) + ": " + gj_variant_name(it->second) +
                          " (tuned earlier in this process); ";
             continue;
         }
@@ -470,8 +623,8 @@ emg_status tune_gj(emg_ctx* c) {
                 if (rep > 0) ms = std::min(ms, t);   // the first run warms up
             }
             char buf[64];
-            std::snprintf(buf, sizeof(buf), " unroll %d %.3f ms", kGjUnroll[v], ms);
-            note += buf;
+            std::snprintf(buf, sizeof(buf), " %.3f ms, ", ms);
+            note += " " + gj_variant_name(v) + buf;
             if (ms < best_ms) {
                 best_ms = ms;
                 best = v;
@@ -482,7 +635,7 @@ emg_status tune_gj(emg_ctx* c) {
         EMG_CUDA_TRY(c, cudaFreeAsync(scratch, c->stream));
         g_gj_best[key] = best;
         L.gj_variant = best;
-        c->tuning += note + " -> unroll " + std::to_string(kGjUnroll[best]) + "; ";
+        c->tuning += note + "-> " + gj_variant_name(best) + "; ";
     }
     return EMG_OK;
 }
