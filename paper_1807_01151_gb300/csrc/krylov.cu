@@ -70,21 +70,53 @@ static int64_t arnoldi_blocks(int64_t K0, int nsm, int per_sm, int64_t cap) {
     return nb < 1 ? 1 : nb;
 }
 constexpr int ARN_CHUNK = 8;  // vectors per dot-product sweep
+static_assert(ARN_CHUNK == 8, "warp_sum8 reduces eight columns");
 
 constexpr int ARN_MAXCOL = MAX_KRYLOV + 8;
 constexpr int ARN_WARPS = ARN_THREADS / 32;
 constexpr int ARN_SUB = 8;    // threads per column in the cross-block reduction
+
+// Warp sums of the 8 values v[0..8) of every lane with 9 shuffle-adds per lane: at each of
+// the first three levels a lane keeps half of its columns and receives its partner's
+// partial sums of them (a transposing butterfly), then two plain levels.  Afterwards lane l
+// holds the warp sum of column 4 b4(l) + 2 b3(l) + b2(l) (b_k = bit k of l); returns it.
+// The order of the additions is fixed.
+__device__ __forceinline__ double warp_sum8(const double v[8], int lane, int* col) {
+    const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+    double a[4], b[2];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const double send = u16 ? v[c] : v[c + 4];
+        const double keep = u16 ? v[c + 4] : v[c];
+        a[c] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        const double send = u8 ? a[c] : a[c + 2];
+        const double keep = u8 ? a[c + 2] : a[c];
+        b[c] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const double send = u4 ? b[0] : b[1];
+    double x = (u4 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    *col = (u16 ? 4 : 0) + (u8 ? 2 : 0) + (u4 ? 1 : 0);
+    return x;
+}
 
 // Block-reduce v[0..n) (n <= ARN_CHUNK): warp shuffles, then one barrier; dst[0..n) from
 // threads 0..n-1 (fixed order).
 __device__ __forceinline__ void block_reduce_store(double v[ARN_CHUNK], int n, double* dst,
                                                    double (*sh)[ARN_MAXCOL]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-    for (int i = 0; i < ARN_CHUNK; ++i) {
-        double x = v[i];
+    if (n == 1) {
+        double x = v[0];
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) sh[warp][i] = x;
+        if (lane == 0) sh[warp][0] = x;
+    } else {
+        int c = 0;
+        const double x = warp_sum8(v, lane, &c);
+        if ((lane & 3) == 0) sh[warp][c] = x;
     }
     __syncthreads();
     if (threadIdx.x < n) {
@@ -141,12 +173,9 @@ __device__ __forceinline__ void slice_dots(const double* V, const double* w, int
                 else if (col == nv && with_ww) v[i] += wk * wk;
             }
         }
-#pragma unroll
-        for (int i = 0; i < ARN_CHUNK; ++i) {
-            double x = v[i];
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == 0 && c0 + i < ncol) sh[warp][c0 + i] = x;
-        }
+        int c = 0;
+        const double x = warp_sum8(v, lane, &c);
+        if ((lane & 3) == 0 && c0 + c < ncol) sh[warp][c0 + c] = x;
     }
     __syncthreads();
     for (int c = threadIdx.x; c < ncol; c += ARN_THREADS) {
