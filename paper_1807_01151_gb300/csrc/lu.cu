@@ -486,25 +486,154 @@ __global__ void __launch_bounds__(32 * W) k_gj_cols(int E, float* __restrict__ b
     for (int t = threadIdx.x; t < B * B; t += T) g[t] = tile[(t / B) * LD + (t % B)];
 }
 
+// Rotating column-owner form: the layout of k_gj_cols, but after every W pivot steps each
+// thread rotates its column slots by one, so that the pivot column of a step is always in
+// register slot 0 of its owner warp (no runtime-indexed register access).  The pivot row
+// slot (p / 32) is warp-uniform: it is taken by branching, not by select chains.  The
+// multiply-adds and the pivot choice are those of k_gj_tile (bitwise the same inverse).
+template <int B, int W>
+__global__ void __launch_bounds__(32 * W) k_gj_rot(int E, float* __restrict__ blk) {
+    using G = GjCols<B, W>;
+    constexpr int RS = G::RS, CS = G::CS, LD = G::LD, T = 32 * W;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float* tile = reinterpret_cast<float*>(smraw);
+    __shared__ float colk[2][32 * RS];
+    __shared__ int s_p[2];
+    __shared__ int perm[B], invp[B];
+    const int e = blockIdx.x;
+    const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float* g = blk + (size_t)e * B * B;
+    for (int t = threadIdx.x; t < B * B; t += T) tile[(t / B) * LD + (t % B)] = g[t];
+    __syncthreads();
+    float a[RS][CS];
+#pragma unroll
+    for (int i = 0; i < RS; ++i)
+#pragma unroll
+        for (int j = 0; j < CS; ++j) {
+            const int r = tx + 32 * i, c = w + W * j;
+            a[i][j] = (r < B && c < B) ? tile[r * LD + c] : 0.0f;
+        }
+    unsigned used = 0u;
+#pragma unroll 1
+    for (int kb = 0; kb < CS; ++kb) {
+#pragma unroll 1
+        for (int wk = 0; wk < W; ++wk) {
+            const int k = kb * W + wk;
+            if (k >= B) break;   // uniform
+            const int buf = k & 1;
+            if (w == wk) {
+                // (1) column k is slot 0 of this warp; zero it (in-place scheme) and pivot
+                float v[RS];
+                float best = -1.0f;
+                int bi = B, lo = B;
+#pragma unroll
+                for (int i = 0; i < RS; ++i) {
+                    v[i] = a[i][0];
+                    a[i][0] = 0.0f;
+                    const int r = tx + 32 * i;
+                    if (r < B && !((used >> i) & 1u)) {
+                        const float m = fabsf(v[i]);
+                        if (m > best) {
+                            best = m;
+                            bi = r;
+                        }
+                        if (r < lo) lo = r;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    const int ol = __shfl_xor_sync(0xffffffffu, lo, o);
+                    if (ob > best || (ob == best && oi < bi)) {
+                        best = ob;
+                        bi = oi;
+                    }
+                    lo = ol < lo ? ol : lo;
+                }
+                const int p = bi < B ? bi : lo;   // lowest unused row if the column is not finite
+#pragma unroll
+                for (int i = 0; i < RS; ++i) colk[buf][tx + 32 * i] = v[i];
+                if (tx == 0) {
+                    s_p[buf] = p;
+                    perm[k] = p;
+                }
+            }
+            __syncthreads();
+            // (2) the scaled pivot row on this warp's columns, by shuffles from lane p mod 32
+            const int p = s_p[buf];
+            const float inv = 1.0f / colk[buf][p];
+            const int pl = p & 31, pi = p >> 5;
+            if (tx == pl) used |= 1u << pi;
+            float rk[CS];
+#pragma unroll
+            for (int c = 0; c < RS; ++c)
+                if (pi == c) {   // warp-uniform branch
+#pragma unroll
+                    for (int j = 0; j < CS; ++j) rk[j] = __shfl_sync(0xffffffffu, a[c][j], pl) * inv;
+                }
+            if (w == wk) rk[0] = inv;   // column k: 1 / a_pk
+            // (3) eliminate column k from every other row; row p becomes the scaled row
+            float f[RS];
+#pragma unroll
+            for (int i = 0; i < RS; ++i) f[i] = (tx + 32 * i == p) ? 0.0f : colk[buf][tx + 32 * i];
+#pragma unroll
+            for (int i = 0; i < RS; ++i)
+#pragma unroll
+                for (int j = 0; j < CS; ++j) a[i][j] -= f[i] * rk[j];
+            if (tx == pl) {
+#pragma unroll
+                for (int c = 0; c < RS; ++c)
+                    if (pi == c) {
+#pragma unroll
+                        for (int j = 0; j < CS; ++j) a[c][j] = rk[j];
+                    }
+            }
+        }
+        // rotate the column slots: the next group's pivot columns move to slot 0
+#pragma unroll
+        for (int i = 0; i < RS; ++i) {
+            const float t0 = a[i][0];
+#pragma unroll
+            for (int j = 0; j < CS - 1; ++j) a[i][j] = a[i][j + 1];
+            a[i][CS - 1] = t0;
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < B; t += T) invp[perm[t]] = t;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RS; ++i)
+#pragma unroll
+        for (int j = 0; j < CS; ++j) {
+            const int r = tx + 32 * i, c = w + W * j;
+            if (r < B && c < B) tile[perm[c] * LD + invp[r]] = a[i][j];
+        }
+    __syncthreads();
+    for (int t = threadIdx.x; t < B * B; t += T) g[t] = tile[(t / B) * LD + (t % B)];
+}
+
 // ---- variants of the FP32 Gauss-Jordan kernel and their tuning --------------------------------
 // Variant v unrolls the pivot loop kGjUnroll[v] times (0 = fully, only for B <= 100).  The
 // variants do the same arithmetic in the same order, so the choice never changes a result.
 // Variants 4..8 are the column-owner form with kGjWarps[v - 4] warps per element (valid
 // while a thread's share of the block stays at most 128 values).
+// Variants 9..13 the rotating column-owner form with kGjWarps[v - 9] warps.
 constexpr int kGjUnroll[] = {1, 4, 16, 0};
 constexpr int kGjWarps[] = {1, 2, 4, 8, 16};
-constexpr int kGjVariants = 9;
+constexpr int kGjVariants = 14;
 
 template <int B>
 static bool gj_variant_valid(int v) {
     if (v < 0 || v >= kGjVariants) return false;
     if (v < 4) return kGjUnroll[v] != 0 || B <= 100;
-    const int W = kGjWarps[v - 4];
-    return ((B + 31) / 32) * ((B + W - 1) / W) <= 128 && W <= (B + 31) / 32 * 8;
+    const int W = kGjWarps[(v - 4) % 5];
+    return ((B + 31) / 32) * ((B + W - 1) / W) <= 128;
 }
 
 static std::string gj_variant_name(int v) {
-    return v < 4 ? "tile unroll " + std::to_string(kGjUnroll[v]) : "cols " + std::to_string(kGjWarps[v - 4]) + " warps";
+    if (v < 4) return "tile unroll " + std::to_string(kGjUnroll[v]);
+    return std::string(v < 9 ? "cols " : "rotating cols ") + std::to_string(kGjWarps[(v - 4) % 5]) + " warps";
 }
 
 template <int B, int U>
@@ -525,9 +654,23 @@ static cudaError_t gj_cols_go(unsigned E, float* blk, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <int B, int W>
+static cudaError_t gj_rot_go(unsigned E, float* blk, cudaStream_t st) {
+    const size_t sm = GjCols<B, W>::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k_gj_rot<B, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_gj_rot<B, W><<<E, 32 * W, sm, st>>>((int)E, blk);
+    return cudaGetLastError();
+}
+
 template <int B>
 static cudaError_t gj_launch(int v, unsigned E, float* blk, cudaStream_t st) {
     switch (v) {
+        case 9: return gj_rot_go<B, 1>(E, blk, st);
+        case 10: return gj_rot_go<B, 2>(E, blk, st);
+        case 11: return gj_rot_go<B, 4>(E, blk, st);
+        case 12: return gj_rot_go<B, 8>(E, blk, st);
+        case 13: return gj_rot_go<B, 16>(E, blk, st);
         case 4: return gj_cols_go<B, 1>(E, blk, st);
         case 5: return gj_cols_go<B, 2>(E, blk, st);
         case 6: return gj_cols_go<B, 4>(E, blk, st);
