@@ -145,11 +145,56 @@ struct DiagCfg {
     static constexpr int THREADS = ((25 * Lv<D, P>::N + 31) / 32) * 32;
 };
 
+// Resident blocks asked of the register allocator: about 56 registers per thread for the
+// FP32 blocks, 80 for FP64 (its 2N-register accumulator row).
+template <int D, int P, class T>
+struct DiagMinB {
+    static constexpr int R = sizeof(T) == 4 ? 56 : 80;
+    static constexpr int T_ = DiagCfg<D, P>::THREADS;
+    static constexpr int V = (65536 / (T_ * R)) < 1 ? 1 : 65536 / (T_ * R);
+};
+
+// 16-byte vector of T (float4 or double2) for the broadcast reads of the staged basis rows.
+template <class T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using V = float4;
+    static constexpr int L = 4;
+    __device__ static void get(const float* p, float o[4]) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w;
+    }
+};
+template <>
+struct Vec16<double> {
+    using V = double2;
+    static constexpr int L = 2;
+    __device__ static void get(const double* p, double o[2]) {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        o[0] = v.x, o[1] = v.y;
+    }
+};
+
+// acc[j] += s * row[j], j < N, with the row read 16 bytes at a time (row padded to NP).
+template <int N, int NP, class T>
+__device__ __forceinline__ void axpy_row(T (&acc)[N], T s, const T* row) {
+    constexpr int VL = Vec16<T>::L;
+#pragma unroll
+    for (int j0 = 0; j0 < NP; j0 += VL) {
+        T v[VL];
+        Vec16<T>::get(row + j0, v);
+#pragma unroll
+        for (int c = 0; c < VL; ++c)
+            if (j0 + c < N) acc[j0 + c] += s * v[c];
+    }
+}
+
 // One CTA per element; thread (a, b, i) accumulates row (a,i), columns (b, 0..N-1).
 // T is the block precision: double (FP64 form) or float (FP32 block form, with float
 // copies of the basis tables; state and face Jacobians are rounded to float on load).
 template <int D, int P, class T>
-__global__ void __launch_bounds__(DiagCfg<D, P>::THREADS) k_diag_blocks(
+__global__ void __launch_bounds__(DiagCfg<D, P>::THREADS, (DiagMinB<D, P, T>::V)) k_diag_blocks(
     int E, int nmax, const double* __restrict__ u, const T* __restrict__ vpsi, const T* __restrict__ vgw,
     const int* __restrict__ elem_face, const T* __restrict__ fpsiL, const T* __restrict__ fpsiR,
     const T* __restrict__ fjl, const T* __restrict__ fjr, const double* __restrict__ psic,
@@ -158,14 +203,18 @@ __global__ void __launch_bounds__(DiagCfg<D, P>::THREADS) k_diag_blocks(
     using L = Lv<D, P>;
     constexpr int N = L::N, Q = L::Q, QF = L::QF, B = L::B, NF = L::NF;
     constexpr int QC = DiagCfg<D, P>::QC;
+    constexpr int VL = Vec16<T>::L, NP = ((N + VL - 1) / VL) * VL;   // padded basis rows
+    // the finished block goes out through shared memory (coalesced) when it fits
+    constexpr bool STAGE = (size_t)B * B * sizeof(T) <= 24576;
     __shared__ double ud[B];
     __shared__ T us[B];
     __shared__ T As[QC][D][25];
-    __shared__ T ps[QC][N];
+    __shared__ __align__(16) T ps[QC][NP];
     __shared__ T gs[QC][D][N];
     __shared__ T Us[QC][5];
-    __shared__ T fps[QF][N];
+    __shared__ __align__(16) T fps[QF][NP];
     __shared__ T fjs[QF][25];
+    __shared__ __align__(16) T ob[STAGE ? B * B : 1];
     __shared__ double s_dtau;
     const int e = blockIdx.x;
     const int tid = threadIdx.x;
@@ -201,7 +250,10 @@ __global__ void __launch_bounds__(DiagCfg<D, P>::THREADS) k_diag_blocks(
             __syncthreads();
             // stage the chunk's psi and W grad psi, and build U at its points (all threads)
             const T* pg = vpsi + ((size_t)e * Q + q0) * N;
-            for (int t = tid; t < nq * N; t += blockDim.x) ps[t / N][t % N] = pg[t];
+            for (int t = tid; t < nq * NP; t += blockDim.x) {
+                const int q = t / NP, j = t % NP;
+                ps[q][j] = j < N ? pg[q * N + j] : (T)0;
+            }
             for (int t = tid; t < D * nq * N; t += blockDim.x) {
                 const int k = t / (nq * N), r = t % (nq * N);
                 gs[r / N][k][r % N] = vgw[(((size_t)e * D + k) * Q + q0) * N + r];
@@ -221,8 +273,7 @@ __global__ void __launch_bounds__(DiagCfg<D, P>::THREADS) k_diag_blocks(
                     T s = (T)0;
 #pragma unroll
                     for (int k = 0; k < D; ++k) s += gs[t][k][i] * As[t][k][ab];
-#pragma unroll
-                    for (int j = 0; j < N; ++j) acc[j] += s * ps[t][j];
+                    axpy_row<N, NP, T>(acc, s, ps[t]);
                 }
             }
         }
@@ -235,20 +286,22 @@ __global__ void __launch_bounds__(DiagCfg<D, P>::THREADS) k_diag_blocks(
         const T* pt = ((code & 1) ? fpsiR : fpsiL) + ((size_t)(code >> 1) * QF) * N;
         const T* fj = ((code & 1) ? fjr : fjl) + ((size_t)(code >> 1) * QF) * 25;
         __syncthreads();
-        for (int t = tid; t < QF * N; t += blockDim.x) fps[t / N][t % N] = pt[t];
+        for (int t = tid; t < QF * NP; t += blockDim.x) {
+            const int q = t / NP, j = t % NP;
+            fps[q][j] = j < N ? pt[q * N + j] : (T)0;
+        }
         for (int t = tid; t < QF * 25; t += blockDim.x) fjs[t / 25][t % 25] = (code & 1) ? fj[t] : -fj[t];
         __syncthreads();
         if (active) {
             for (int t = 0; t < QF; ++t) {
                 const T s = fps[t][i] * fjs[t][ab];
-#pragma unroll
-                for (int j = 0; j < N; ++j) acc[j] += s * fps[t][j];
+                axpy_row<N, NP, T>(acc, s, fps[t]);
             }
         }
     }
     __syncthreads();
     if (active) {
-        T* row = out + (size_t)e * B * B + (size_t)(a * N + i) * B + b * N;
+        T* row = STAGE ? ob + (size_t)(a * N + i) * B + b * N : out + (size_t)e * B * B + (size_t)(a * N + i) * B + b * N;
         if (shifted) {
             const T idt = (T)(1.0 / s_dtau);
 #pragma unroll
@@ -257,6 +310,11 @@ __global__ void __launch_bounds__(DiagCfg<D, P>::THREADS) k_diag_blocks(
 #pragma unroll
             for (int j = 0; j < N; ++j) row[j] = acc[j];
         }
+    }
+    if (STAGE) {
+        __syncthreads();
+        T* g = out + (size_t)e * B * B;
+        for (int t = tid; t < B * B; t += blockDim.x) g[t] = ob[t];
     }
 }
 
