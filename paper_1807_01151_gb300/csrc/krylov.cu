@@ -18,30 +18,29 @@
 namespace emg {
 
 // ---- persistent Arnoldi: one cooperative launch for the whole Krylov loop ------------------
-// Grid barrier on a counter/generation pair in global memory.  Waits are bounded: after
-// `budget` clock cycles the block records a timeout in sc->timeout and the kernel returns
-// (the host maps it to EMG_ERR_TIMEOUT); nothing spins forever.
+// Grid barrier on a monotonic arrival counter in global memory (zeroed before the launch):
+// at its e-th barrier a block adds one and waits until the counter reaches e * nblocks, so
+// the last arrival releases everyone without a reset.  Waits are bounded: after `budget`
+// clock cycles the block records a timeout in sc->timeout and the kernel returns (the host
+// maps it to EMG_ERR_TIMEOUT); nothing spins forever.
 struct GridBar {
     unsigned int count;
-    unsigned int gen;
+    unsigned int unused;
 };
 
-__device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned nblocks, long long budget, DevScalars* sc,
-                                          int* s_ok) {
+__device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned nblocks, unsigned* epoch, long long budget,
+                                          DevScalars* sc, int* s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int* vgen = &bar->gen;
-        const unsigned int g = *vgen;
+        const unsigned target = (*epoch + 1u) * nblocks;
+        *epoch += 1u;
         __threadfence();
-        const unsigned int arrived = atomicAdd(&bar->count, 1u) + 1u;
+        const unsigned arrived = atomicAdd(&bar->count, 1u) + 1u;
         int ok = 1;
-        if (arrived == nblocks) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
-        } else {
+        if (arrived < target) {
+            volatile unsigned int* vc = &bar->count;
             const long long t0 = clock64();
-            while (*vgen == g) {
+            while (*vc < target) {
                 if (clock64() - t0 > budget) {
                     atomicExch(&sc->timeout, 1);
                     ok = 0;
@@ -236,6 +235,7 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
     __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
     __shared__ double h1[ARN_MAXCOL], h2[ARN_MAXCOL], red[8];
     __shared__ int s_ok;
+    unsigned epoch = 0;   // barriers passed (thread 0's copy is the one used)
     const unsigned nb = gridDim.x;
     const int64_t chunk = (K0 + nb - 1) / nb;
     const int64_t k0 = (int64_t)blockIdx.x * chunk;
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
         }
         block_reduce_store(v, 1, partA + (size_t)blockIdx.x * stride, sh);
     }
-    if (!grid_sync(bar, nb, budget, sc, &s_ok)) return;
+    if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
     reduce_cols(partA, nb, stride, 1, red, sh);
     const double beta = sqrt(red[0]);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
     for (int j = 0; j < m; ++j) {
         // CGS pass 1: h1 = V^T w and w.w
         slice_dots(V, w, K0, k0, k1, j + 1, 1, partA + (size_t)blockIdx.x * stride, sh);
-        if (!grid_sync(bar, nb, budget, sc, &s_ok)) return;
+        if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
         reduce_cols(partA, nb, stride, j + 2, h1, sh);
         for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
             double s = w[k];
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
         __syncthreads();
         // CGS pass 2 (re-orthogonalisation)
         slice_dots(V, w, K0, k0, k1, j + 1, 0, partB + (size_t)blockIdx.x * stride, sh);
-        if (!grid_sync(bar, nb, budget, sc, &s_ok)) return;
+        if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
         reduce_cols(partB, nb, stride, j + 1, h2, sh);
         {
             double v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
             }
             block_reduce_store(v, 1, partC + (size_t)blockIdx.x * stride, sh);
         }
-        if (!grid_sync(bar, nb, budget, sc, &s_ok)) return;
+        if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
         reduce_cols(partC, nb, stride, 1, red, sh);
         const double hn = sqrt(red[0]);
         const double w0 = sqrt(h1[j + 1]);
@@ -318,7 +318,8 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
 // the arrival it waits for never comes and the wait must give up by itself.
 __global__ void k_barrier_selftest(GridBar* bar, long long budget, DevScalars* sc) {
     __shared__ int s_ok;
-    grid_sync(bar, 2u, budget, sc, &s_ok);
+    unsigned epoch = 0;
+    grid_sync(bar, 2u, &epoch, budget, sc, &s_ok);
 }
 
 emg_status selftest_barrier_timeout(emg_ctx* c, int* timed_out) {
