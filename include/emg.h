@@ -100,6 +100,12 @@ typedef struct {
                               (FP32 Gauss-Jordan: pivot-loop unrolling) per block size on this
                               device and use the fastest (cached per process); 0: the first
                               variant.  Variants compute identically: results do not change. */
+    int32_t coop_krylov;   /* 1 (default): the Arnoldi process of the EXP1 step is one persistent
+                              cooperative kernel with bounded grid barriers; 0: the same process
+                              as 2 + 3m plain kernels with no grid barrier (bitwise the same
+                              result), for contexts that share the device with other work, where
+                              the blocks of a persistent kernel may not all be resident at once
+                              (the request loop uses 0). */
 } emg_params;
 
 typedef struct {

@@ -26,7 +26,7 @@ class ParamsC(C.Structure):
                 ("p_max", C.c_int32), ("rk_stages", C.c_int32), ("krylov_m", C.c_int32),
                 ("cfl_max", C.c_double), ("exp_dt_factor", C.c_double), ("pre_smooth", C.c_int32),
                 ("prec", C.c_int32), ("cuda_stream", C.c_void_p), ("lag_blocks", C.c_int32),
-                ("use_graph", C.c_int32), ("autotune", C.c_int32)]
+                ("use_graph", C.c_int32), ("autotune", C.c_int32), ("coop_krylov", C.c_int32)]
 
 
 class CycleInfoC(C.Structure):
@@ -148,7 +148,8 @@ def mesh_desc(mesh):
 
 
 def make_params(p_max=2, mach=0.3, alpha_deg=0.0, gamma=1.4, rk_stages=4, krylov_m=30, cfl_max=100.0,
-                exp_dt_factor=0.0, pre_smooth=2, prec=0, stream=None, lag_blocks=0, use_graph=1, autotune=1):
+                exp_dt_factor=0.0, pre_smooth=2, prec=0, stream=None, lag_blocks=0, use_graph=1, autotune=1,
+                coop_krylov=1):
     prm = ParamsC()
     load().emg_default_params(C.byref(prm))
     prm.gamma, prm.mach, prm.alpha_deg = gamma, mach, alpha_deg
@@ -158,6 +159,7 @@ def make_params(p_max=2, mach=0.3, alpha_deg=0.0, gamma=1.4, rk_stages=4, krylov
     prm.lag_blocks = int(lag_blocks)
     prm.use_graph = int(use_graph)
     prm.autotune = int(autotune)
+    prm.coop_krylov = int(coop_krylov)
     return prm
 
 
@@ -177,7 +179,7 @@ class Solver:
 
     def __init__(self, mesh, p_max=2, mach=0.3, alpha_deg=0.0, gamma=1.4, rk_stages=4, krylov_m=30,
                  cfl_max=100.0, exp_dt_factor=0.0, pre_smooth=2, prec=0, stream=None, lag_blocks=0,
-                 use_graph=1, autotune=1):
+                 use_graph=1, autotune=1, coop_krylov=1):
         self.lib = load()
         self.dim = int(mesh.dim)
         self.E = int(mesh.n_elems)
@@ -186,7 +188,7 @@ class Solver:
         prm = make_params(p_max=p_max, mach=mach, alpha_deg=alpha_deg, gamma=gamma, rk_stages=rk_stages,
                           krylov_m=krylov_m, cfl_max=cfl_max, exp_dt_factor=exp_dt_factor,
                           pre_smooth=pre_smooth, prec=prec, stream=stream, lag_blocks=lag_blocks,
-                          use_graph=use_graph, autotune=autotune)
+                          use_graph=use_graph, autotune=autotune, coop_krylov=coop_krylov)
         h = C.c_void_p()
         st = self.lib.emg_create_mesh(C.byref(d), C.byref(prm), C.byref(h))
         self.h = h

@@ -223,8 +223,12 @@ emg_status run_body(emg_ctx* c) {
     }
     EMG_CUDA_TRY(c, cudaGraphLaunch(c->body_exec, c->stream));
     cudaGraphExec_t kx = c->krylov_exec;
-    emg_status st = coop_ordered(c->device, c->stream, [kx, c]() { return cudaGraphLaunch(kx, c->stream); }, &c->err);
-    if (st != EMG_OK) return st;
+    if (c->prm.coop_krylov) {
+        emg_status st = coop_ordered(c->device, c->stream, [kx, c]() { return cudaGraphLaunch(kx, c->stream); }, &c->err);
+        if (st != EMG_OK) return st;
+    } else {
+        EMG_CUDA_TRY(c, cudaGraphLaunch(kx, c->stream));
+    }
     c->launches += c->body_kernels;
     return EMG_OK;
 }
@@ -297,6 +301,7 @@ void emg_default_params(emg_params* p) {
     p->cuda_stream = nullptr;
     p->use_graph = 1;
     p->autotune = 1;
+    p->coop_krylov = 1;
 }
 
 const char* emg_build_info(void) {

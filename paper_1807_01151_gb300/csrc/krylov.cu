@@ -247,10 +247,11 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
             const double x = dt[k / 5] * r[k];
             v[0] += x * x;
         }
-        block_reduce_store(v, 1, partA + (size_t)blockIdx.x * stride, sh);
+        // partC: partA is written again by the first dot sweep before any further barrier
+        block_reduce_store(v, 1, partC + (size_t)blockIdx.x * stride, sh);
     }
     if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
-    reduce_cols(partA, nb, stride, 1, red, sh);
+    reduce_cols(partC, nb, stride, 1, red, sh);
     const double beta = sqrt(red[0]);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         sc->beta = beta;
@@ -312,6 +313,148 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
         __syncthreads();
         w = wn;
     }
+}
+
+// ---- the same Arnoldi process without grid barriers ----------------------------------------
+// Kernel boundaries take the place of the persistent kernel's grid barriers: a start kernel
+// (norm partials of N), an init kernel (beta, v_1, A v_1, first dot sweep) and three kernels
+// per Krylov step (second sweep; norm; H column, v_{j+1}, next product and next first
+// sweep).  Each block does exactly the persistent kernel's work on the same slice, with the
+// same block count, so the Krylov basis and H are bitwise the same; no block ever waits for
+// another, so nothing depends on the blocks being co-resident (several contexts sharing the
+// device).  h1 travels between kernels through hcol[]; a kernel that finds the process
+// ended (breakdown or a zero start vector) returns at once.
+struct ArnArgs {
+    int64_t K0;
+    int NF, m, stride;
+    const double* bsr;
+    const int* nbr;
+    const double* dt;
+    const double* r;
+    double* V;
+    double* wbuf;
+    double* H;
+    double* hcol;
+    double* partA;
+    double* partB;
+    double* partC;
+    DevScalars* sc;
+};
+
+__device__ __forceinline__ void arn_slice(int64_t K0, int64_t* k0, int64_t* k1) {
+    const unsigned nb = gridDim.x;
+    const int64_t chunk = (K0 + nb - 1) / nb;
+    *k0 = (int64_t)blockIdx.x * chunk;
+    *k1 = (*k0 + chunk) < K0 ? (*k0 + chunk) : K0;
+}
+
+__global__ void __launch_bounds__(ARN_THREADS) k_arn_start(ArnArgs A) {
+    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
+    int64_t k0, k1;
+    arn_slice(A.K0, &k0, &k1);
+    double v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
+        const double x = A.dt[k / 5] * A.r[k];
+        v[0] += x * x;
+    }
+    block_reduce_store(v, 1, A.partC + (size_t)blockIdx.x * A.stride, sh);
+}
+
+__global__ void __launch_bounds__(ARN_THREADS) k_arn_init(ArnArgs A) {
+    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
+    __shared__ double red[8];
+    int64_t k0, k1;
+    arn_slice(A.K0, &k0, &k1);
+    const int nb = (int)gridDim.x;
+    reduce_cols(A.partC, nb, A.stride, 1, red, sh);
+    const double beta = sqrt(red[0]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.sc->beta = beta;
+        A.sc->m_used = 0;
+        A.sc->broken = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
+        if (!isfinite(beta)) A.sc->nonfinite = 1;
+    }
+    if (beta == 0.0 || !isfinite(beta)) return;
+    const double ib = 1.0 / beta;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) A.V[k] = A.dt[k / 5] * A.r[k] * ib;
+    spmv_rows(k0, k1, A.NF, A.bsr, A.nbr, A.dt, nullptr, A.r, ib, A.wbuf);
+    __syncthreads();
+    slice_dots(A.V, A.wbuf, A.K0, k0, k1, 1, 1, A.partA + (size_t)blockIdx.x * A.stride, sh);
+}
+
+// step j: h1 from the first sweep, w -= V h1, second sweep
+__global__ void __launch_bounds__(ARN_THREADS) k_arn_pass2(ArnArgs A, int j) {
+    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
+    __shared__ double h1[ARN_MAXCOL];
+    if (*((volatile int*)&A.sc->broken)) return;
+    int64_t k0, k1;
+    arn_slice(A.K0, &k0, &k1);
+    const int nb = (int)gridDim.x;
+    double* w = A.wbuf + (size_t)(j & 1) * A.K0;
+    reduce_cols(A.partA, nb, A.stride, j + 2, h1, sh);
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < j + 2; i += ARN_THREADS) A.hcol[i] = h1[i];
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
+        double s = w[k];
+        for (int i = 0; i <= j; ++i) s -= h1[i] * A.V[(size_t)i * A.K0 + k];
+        w[k] = s;
+    }
+    __syncthreads();
+    slice_dots(A.V, w, A.K0, k0, k1, j + 1, 0, A.partB + (size_t)blockIdx.x * A.stride, sh);
+}
+
+// step j: h2, w -= V h2, norm partials; column j of H above the subdiagonal
+__global__ void __launch_bounds__(ARN_THREADS) k_arn_pass3(ArnArgs A, int j) {
+    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
+    __shared__ double h2[ARN_MAXCOL];
+    if (*((volatile int*)&A.sc->broken)) return;
+    int64_t k0, k1;
+    arn_slice(A.K0, &k0, &k1);
+    const int nb = (int)gridDim.x;
+    double* w = A.wbuf + (size_t)(j & 1) * A.K0;
+    reduce_cols(A.partB, nb, A.stride, j + 1, h2, sh);
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int i = 0; i <= j; ++i) A.H[(size_t)i * A.m + j] = A.hcol[i] + h2[i];
+    double v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
+        double s = w[k];
+        for (int i = 0; i <= j; ++i) s -= h2[i] * A.V[(size_t)i * A.K0 + k];
+        w[k] = s;
+        v[0] += s * s;
+    }
+    block_reduce_store(v, 1, A.partC + (size_t)blockIdx.x * A.stride, sh);
+}
+
+// step j: h_{j+1,j}, breakdown test; unless the process ends, v_{j+1}, the next product and
+// the next step's first sweep
+__global__ void __launch_bounds__(ARN_THREADS) k_arn_pass4(ArnArgs A, int j) {
+    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
+    __shared__ double red[8];
+    if (*((volatile int*)&A.sc->broken)) return;
+    int64_t k0, k1;
+    arn_slice(A.K0, &k0, &k1);
+    const int nb = (int)gridDim.x;
+    reduce_cols(A.partC, nb, A.stride, 1, red, sh);
+    const double hn = sqrt(red[0]);
+    const double w0 = sqrt(A.hcol[j + 1]);
+    const bool brk = !(hn > 1e-12 * w0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        A.H[(size_t)(j + 1) * A.m + j] = hn;
+        A.sc->m_used = j + 1;
+        A.sc->hsub = hn;
+        A.sc->w0 = w0;
+        if (!isfinite(hn)) A.sc->nonfinite = 1;
+        if (brk) A.sc->broken = 1;
+    }
+    if (brk || j + 1 == A.m) return;
+    const double ih = 1.0 / hn;
+    const double* w = A.wbuf + (size_t)(j & 1) * A.K0;
+    double* vn = A.V + (size_t)(j + 1) * A.K0;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) vn[k] = w[k] * ih;
+    double* wn = A.wbuf + (size_t)((j + 1) & 1) * A.K0;
+    spmv_rows(k0, k1, A.NF, A.bsr, A.nbr, A.dt, w, nullptr, ih, wn);
+    __syncthreads();
+    slice_dots(A.V, wn, A.K0, k0, k1, j + 2, 1, A.partA + (size_t)blockIdx.x * A.stride, sh);
 }
 
 // Self-test of the bounded wait: one block waits at a barrier sized for two blocks, so
@@ -571,21 +714,35 @@ emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, do
     double* Vv = c->V;
     double* ww = c->w;
     double* HH = c->H;
-    long long budget = 4000000000LL;   // about two seconds of SM clock per barrier wait
-    DevScalars* scp = c->sc;
-    void* args[] = {&K0a, &Ea, &NFa, &ma, (void*)&bsr, (void*)&nbr, (void*)&dt, (void*)&rr, &Vv, &ww, &HH,
-                    &partA, &partB, &partC, &stra, &bar, &budget, &scp};
-    {
-        ProfScope _ps(c, PC_ARNOLDI);
-        auto launch = [&]() {
-            return cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3((unsigned)nb), dim3(ARN_THREADS), args, 0,
-                                               c->stream);
-        };
-        if (c->capturing) {
-            EMG_CUDA_TRY(c, launch());
-        } else {
-            emg_status so = coop_ordered(c->device, c->stream, launch, &c->err);
-            if (so != EMG_OK) return so;
+    if (!c->prm.coop_krylov) {
+        // barrier-free form (same blocks, same arithmetic): 2 + 3m plain launches
+        ArnArgs A{K0, 2 * c->dim, m, stride, bsr, nbr, dt, rr, Vv, ww, HH, c->hcol, partA, partB, partC, c->sc};
+        const unsigned g = (unsigned)nb;
+        { ProfScope _ps(c, PC_ARNOLDI); k_arn_start<<<g, ARN_THREADS, 0, c->stream>>>(A); }
+        { ProfScope _ps(c, PC_ARNOLDI); k_arn_init<<<g, ARN_THREADS, 0, c->stream>>>(A); }
+        for (int j = 0; j < m; ++j) {
+            { ProfScope _ps(c, PC_ARNOLDI); k_arn_pass2<<<g, ARN_THREADS, 0, c->stream>>>(A, j); }
+            { ProfScope _ps(c, PC_ARNOLDI); k_arn_pass3<<<g, ARN_THREADS, 0, c->stream>>>(A, j); }
+            { ProfScope _ps(c, PC_ARNOLDI); k_arn_pass4<<<g, ARN_THREADS, 0, c->stream>>>(A, j); }
+        }
+        EMG_CHECK_LAUNCH(c);
+    } else {
+        long long budget = 4000000000LL;   // about two seconds of SM clock per barrier wait
+        DevScalars* scp = c->sc;
+        void* args[] = {&K0a, &Ea, &NFa, &ma, (void*)&bsr, (void*)&nbr, (void*)&dt, (void*)&rr, &Vv, &ww, &HH,
+                        &partA, &partB, &partC, &stra, &bar, &budget, &scp};
+        {
+            ProfScope _ps(c, PC_ARNOLDI);
+            auto launch = [&]() {
+                return cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3((unsigned)nb), dim3(ARN_THREADS), args, 0,
+                                                   c->stream);
+            };
+            if (c->capturing) {
+                EMG_CUDA_TRY(c, launch());
+            } else {
+                emg_status so = coop_ordered(c->device, c->stream, launch, &c->err);
+                if (so != EMG_OK) return so;
+            }
         }
     }
     const int n = m + 1;

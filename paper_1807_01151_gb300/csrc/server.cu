@@ -126,6 +126,7 @@ struct emg_server {
         d.wall_normal = r->wn.empty() ? nullptr : r->wn.data();
         emg_params p = r->prm;
         p.cuda_stream = nullptr;  // every solve gets a stream of its own
+        p.coop_krylov = 0;        // solves share the device: no kernel may wait for co-resident blocks
         emg_status st = emg_create_mesh(&d, &p, &r->c);
         if (st == EMG_OK && !r->U0.empty()) st = emg_set_state(r->c, r->U0.data(), 0);
         if (st == EMG_OK && cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess) st = EMG_ERR_CUDA;

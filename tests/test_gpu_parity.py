@@ -354,3 +354,23 @@ def test_tuned_kernel_variants_give_bitwise_the_same_cycles():
         s.close()
     np.testing.assert_array_equal(out[0], out[1])
     assert notes[0] == "" and "gj B=75" in notes[1] and "gj B=15" in notes[1]
+
+
+@pytest.mark.gpu
+def test_barrier_free_arnoldi_is_bitwise_the_persistent_kernel():
+    """The Arnoldi process as plain kernels (no grid barrier) and as one cooperative
+    persistent kernel: same blocks, same arithmetic, bitwise the same cycles; also when
+    the process stops early at happy breakdown (4x1 O-grid at p = 0, K0 = 20 < m)."""
+    from paper_1807_01151_gb300 import Solver
+    from workloads import ogrid
+    for desc, p, prec in ((ogrid(16, 8), 3, 1), (ogrid(16, 8), 2, 0), (ogrid(4, 1), 0, 0)):
+        out = []
+        for coop in (1, 0):
+            s = Solver(desc, p_max=p, prec=prec, coop_krylov=coop)
+            infos = [s.vcycle() for _ in range(5)]
+            out.append((s.get_state(), [(i["krylov_dim"], i["cfl"], i["res_rho"]) for i in infos]))
+            s.close()
+        np.testing.assert_array_equal(out[0][0], out[1][0])
+        assert out[0][1] == out[1][1]
+        if p == 0:
+            assert out[0][1][0][0] <= 20         # breakdown: the space is exhausted
