@@ -254,7 +254,9 @@ emg_status emg_estimate_device_bytes(const emg_mesh_desc* mesh, const emg_params
  * admitted when one of max_active slots is free and its footprint
  * (emg_estimate_device_bytes) fits in what the memory budget has left.  An admitted solve
  * owns a context (its own stream; state, blocks and Krylov arrays resident on the device
- * until it ends) and keeps one V-cycle in flight; emg_server_step only polls events and
+ * until it ends; its Arnoldi process runs as plain kernels, coop_krylov = 0, since no
+ * kernel of a solve may wait for blocks that other solves' work keeps off the SMs) and
+ * keeps one V-cycle in flight; emg_server_step only polls events and
  * enqueues the next cycle of every solve whose residual check has arrived, so the cycles
  * of different solves overlap on the device.  A solve ends converged (EMG_OK), at
  * max_cycles (EMG_ERR_NOT_CONVERGED), or with its own failure status; the others carry
