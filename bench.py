@@ -57,6 +57,18 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, device="cuda"):
+    """The largest of every rank's x (the slowest rank sets a replica run's time); x itself
+    when no process group is running."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_info():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -195,10 +207,7 @@ def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks):
     prof = s.profile_read()
     s.profile(False)
     clk = clocks.stop() if clocks else None
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
     out = {"value": world * K * args.steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / args.steps,
            "gpu_launches": launches, "clocks": clk, "K": K, "E": E}
     # residual throughput (p_max residual, device buffers, back-to-back)
@@ -300,10 +309,7 @@ def run_serve(args, rank, world, local):
                                      stall_cycles=args.stall_cycles)
     clk = clocks.stop()
     span = summ["makespan_s"]
-    if world > 1:
-        t = torch.tensor([span], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        span = float(t.item())
+    span = max_over_ranks(span)
     if rank == 0:
         line = {
             "metric": "served steady solves to a 1e-10 drop: solves/s, p50/p99 time-to-converge",
