@@ -66,8 +66,10 @@ __global__ void __launch_bounds__(256) k_lu(int E, T* __restrict__ blk, int* __r
                 a[pr * LD + cc] = t0;
             }
         __syncthreads();
-        const T inv = (T)1 / a[k * LD + k];
-        for (int r = k + 1 + tid; r < B; r += nth) a[r * LD + k] *= inv;
+        if (k + 1 + tid < B) {   // only the threads that scale a row pay for the division
+            const T inv = (T)1 / a[k * LD + k];
+            for (int r = k + 1 + tid; r < B; r += nth) a[r * LD + k] *= inv;
+        }
         __syncthreads();
         // trailing update on a 32-wide column x 8-row thread grid (no index division)
         const int tx = tid & 31, ty = tid >> 5;
@@ -89,11 +91,18 @@ __global__ void __launch_bounds__(128) k_stage(int E, const T* __restrict__ lu, 
                                                const double* __restrict__ r, const double* __restrict__ un,
                                                double beta, double* __restrict__ out) {
     __shared__ T ys[4][B];
+    __shared__ T rd[4][B];   // reciprocals of U's diagonal
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int e = blockIdx.x * 4 + warp;
     if (e >= E) return;
     T* y = ys[warp];
-    for (int t = lane; t < B; t += 32) y[t] = (T)r[(size_t)e * B + t];
+    const T* M = lu + (size_t)e * B * B;
+    // the B divisions of the back substitution, done once and in parallel across the lanes
+    // (a division costs a warp-wide multi-instruction sequence on the FP64 pipe)
+    for (int t = lane; t < B; t += 32) {
+        y[t] = (T)r[(size_t)e * B + t];
+        rd[warp][t] = (T)1 / M[(size_t)t * B + t];
+    }
     __syncwarp();
     if (lane == 0) {
         const int* pv = piv + (size_t)e * B;
@@ -107,7 +116,6 @@ __global__ void __launch_bounds__(128) k_stage(int E, const T* __restrict__ lu, 
         }
     }
     __syncwarp();
-    const T* M = lu + (size_t)e * B * B;
     for (int j = 0; j < B; ++j) {
         const T yj = y[j];
         const T* col = M + (size_t)j * B;
@@ -116,7 +124,7 @@ __global__ void __launch_bounds__(128) k_stage(int E, const T* __restrict__ lu, 
     }
     for (int j = B - 1; j >= 0; --j) {
         const T* col = M + (size_t)j * B;
-        const T xj = y[j] / col[j];
+        const T xj = y[j] * rd[warp][j];
         __syncwarp();
         for (int rr = lane; rr < j; rr += 32) y[rr] -= col[rr] * xj;
         if (lane == 0) y[j] = xj;
