@@ -305,8 +305,10 @@ void emg_default_params(emg_params* p) {
 }
 
 const char* emg_build_info(void) {
-    return "emg sm_103a fp64: residual(face Roe + element volume), AD face Jacobians, block assembly, "
-           "smem LU + warp substitution, CGS2 Arnoldi, Pade-13 phi_1";
+    return "emg sm_103a: FP64 residual (face Roe + element volume), AD face Jacobians, block assembly; "
+           "FP64 blocks: shared-memory LU + warp substitution; FP32 blocks: tuned Gauss-Jordan inverse + GEMV; "
+           "CGS2 Arnoldi (persistent cooperative or barrier-free), Pade-13 phi_1; graph-captured V-cycle; "
+           "continuous-batching request loop";
 }
 
 emg_status emg_create_mesh(const emg_mesh_desc* m, const emg_params* prm, emg_ctx** out) {
