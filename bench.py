@@ -69,6 +69,12 @@ def max_over_ranks(x, device="cuda"):
     return float(t.item())
 
 
+def clocks_dir():
+    """Where the raw nvidia-smi samples go (their summary is in the JSON line)."""
+    import tempfile
+    return os.environ.get("EMG_CLOCKS_DIR") or tempfile.gettempdir()
+
+
 def dist_info():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -190,7 +196,7 @@ def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    outdir = os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ROOT
+    outdir = clocks_dir()
     clocks = Clocks(local, os.path.join(outdir, f"clocks_rank{rank}_{PREC_NAMES[prec]}.csv")) if with_clocks else None
     s.profile(True)
     l0 = s.launch_count
@@ -303,7 +309,7 @@ def run_serve(args, rank, world, local):
         make_mesh(rq)
     if world > 1:
         torch.distributed.barrier()
-    outdir = os.path.join(ROOT, "gpurun_out") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ROOT
+    outdir = clocks_dir()
     clocks = Clocks(local, os.path.join(outdir, f"clocks_rank{rank}_serve.csv"))
     out, summ = serving.serve_stream(reqs, make_mesh, max_active=args.max_active, prec=1,
                                      stall_cycles=args.stall_cycles)
