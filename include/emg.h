@@ -40,7 +40,8 @@ typedef enum {
     EMG_ERR_NONFINITE = 4,     /* NaN/Inf in a state or residual                      */
     EMG_ERR_UNPHYSICAL = 5,    /* non-positive density or pressure at a cell centre  */
     EMG_ERR_NOT_CONVERGED = 6, /* emg_solve_steady reached max_cycles                 */
-    EMG_ERR_TIMEOUT = 7        /* a bounded device-side wait gave up                  */
+    EMG_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up                  */
+    EMG_CANCELLED = 8          /* a served request withdrawn by emg_server_cancel     */
 } emg_status;
 
 /* Boundary codes of emg_mesh_desc.face_bc. */
@@ -305,6 +306,11 @@ emg_status emg_server_submit(emg_server* srv, const emg_mesh_desc* mesh, const e
 emg_status emg_server_step(emg_server* srv, int32_t* n_active, int32_t* n_queued);
 /* Move up to capacity finished requests' results (in completion order) into out. */
 emg_status emg_server_results(emg_server* srv, emg_request_result* out, int32_t capacity, int32_t* n_out);
+/* Withdraw request id: a queued request is dropped; an active one ends before its next
+ * cycle is enqueued (the cycle in flight completes first), its context and memory are
+ * released.  Its result (status EMG_CANCELLED, the cycles done) is then reported by
+ * emg_server_results.  EMG_ERR_ARG if id is unknown or has already finished. */
+emg_status emg_server_cancel(emg_server* srv, int64_t id);
 /* Copy the kept converged state of request id ([n_elems][5][N_pmax], n doubles) to host
  * memory and release it.  EMG_ERR_ARG if none is kept or n does not match. */
 emg_status emg_server_take_state(emg_server* srv, int64_t id, double* U, int64_t n);

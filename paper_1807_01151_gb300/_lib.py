@@ -12,7 +12,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libemg.so")
 
 STATUS = {0: "EMG_OK", 1: "EMG_ERR_ARG", 2: "EMG_ERR_OOM", 3: "EMG_ERR_CUDA", 4: "EMG_ERR_NONFINITE",
-          5: "EMG_ERR_UNPHYSICAL", 6: "EMG_ERR_NOT_CONVERGED", 7: "EMG_ERR_TIMEOUT"}
+          5: "EMG_ERR_UNPHYSICAL", 6: "EMG_ERR_NOT_CONVERGED", 7: "EMG_ERR_TIMEOUT", 8: "EMG_CANCELLED"}
 
 
 class MeshDescC(C.Structure):
@@ -91,6 +91,7 @@ EXPORTS = {
     "emg_server_step": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "emg_server_results": (C.c_int, [C.c_void_p, C.POINTER(RequestResultC), C.c_int32, C.POINTER(C.c_int32)]),
     "emg_server_take_state": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]),
+    "emg_server_cancel": (C.c_int, [C.c_void_p, C.c_int64]),
     "emg_build_info": (C.c_char_p, []),
 }
 
@@ -407,6 +408,10 @@ class Server:
                                 t_admit=r.t_admit, t_done=r.t_done, device_bytes=r.device_bytes))
             if n.value < 64:
                 return out
+
+    def cancel(self, rid):
+        """Withdraw a queued or active request (its result reports EMG_CANCELLED)."""
+        self._check(self.lib.emg_server_cancel(self.h, int(rid)))
 
     def take_state(self, rid):
         U = np.empty(self._shape[rid])

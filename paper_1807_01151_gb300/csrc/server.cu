@@ -40,6 +40,7 @@ struct Request {
     int64_t cycles = 0, best_at = 0;
     int64_t held = 0;  // bytes charged to the budget
     emg_status status = EMG_OK;
+    bool cancel = false;  // withdrawn while active: end at the next residual check
 };
 
 int64_t modes(int dim, int p) { return dim == 2 ? (p + 1) * (p + 2) / 2 : (p + 1) * (p + 2) * (p + 3) / 6; }
@@ -143,6 +144,10 @@ struct emg_server {
     // Returns true when the solve ended.
     bool advance(std::unique_ptr<Request>& r) {
         emg_ctx* c = r->c;
+        if (r->cancel) {
+            finish(r, EMG_CANCELLED, "");
+            return true;
+        }
         emg_status st = check_flags(c);
         if (st != EMG_OK) {
             finish(r, st, c->err);
@@ -295,6 +300,26 @@ emg_status emg_server_results(emg_server* s, emg_request_result* out, int32_t ca
     }
     *n_out = n;
     return EMG_OK;
+}
+
+emg_status emg_server_cancel(emg_server* s, int64_t id) {
+    if (!s) return EMG_ERR_ARG;
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+        if ((*it)->id == id) {
+            (*it)->t_admit = s->now();
+            s->finish(*it, EMG_CANCELLED, "");
+            s->queue.erase(it);
+            return EMG_OK;
+        }
+    }
+    for (auto& r : s->active) {
+        if (r->id == id) {
+            r->cancel = true;   // the request ends at its next residual check (emg_server_step)
+            return EMG_OK;
+        }
+    }
+    s->err = "cancel: request " + std::to_string(id) + " is not queued or active";
+    return EMG_ERR_ARG;
 }
 
 emg_status emg_server_take_state(emg_server* s, int64_t id, double* U, int64_t n) {

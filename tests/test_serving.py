@@ -47,6 +47,23 @@ def test_server_rejects_a_request_larger_than_its_budget_without_a_gpu():
     srv.close()
 
 
+def test_cancel_of_a_queued_request_needs_no_gpu():
+    from paper_1807_01151_gb300 import EmgError, Server
+    srv = Server(max_active=1, mem_budget=1 << 40, max_cycles=10)
+    a = srv.submit(ogrid(8, 4), p_max=1)
+    b = srv.submit(ogrid(8, 4), p_max=2)
+    srv.cancel(b)
+    res = srv.results()
+    assert [(r["id"], r["status_name"], r["cycles"]) for r in res] == [(b, "EMG_CANCELLED", 0)]
+    with pytest.raises(EmgError):
+        srv.cancel(b)              # already finished
+    with pytest.raises(EmgError):
+        srv.cancel(12345)          # unknown
+    srv.cancel(a)
+    assert [r["status_name"] for r in srv.results()] == ["EMG_CANCELLED"]
+    srv.close()
+
+
 # ---------------------------------------------------------------- GPU
 
 MIX = [  # (grid, p, Ma, prec): subcritical cases that converge to 1e-10 in both forms
@@ -152,3 +169,25 @@ def test_stall_detection_ends_a_solve_that_stops_improving():
     r = res[0]
     assert r["id"] == rid and r["status_name"] == "EMG_ERR_NOT_CONVERGED"
     assert 20 < r["cycles"] < 2000 and r["res_final"] < 1e-9 * r["res0"]
+
+
+@pytest.mark.gpu
+def test_cancel_of_an_active_request_leaves_the_others_intact():
+    from paper_1807_01151_gb300 import Server
+    U_alone, cycles_alone = _alone(*MIX[0])
+    srv = Server(max_active=2, max_cycles=2000, keep_state=True)
+    keep = srv.submit(ogrid(*MIX[0][0]), p_max=MIX[0][1], mach=MIX[0][2], prec=MIX[0][3])
+    gone = srv.submit(ogrid(64, 32), p_max=3, mach=0.3, prec=1)
+    res = {}
+    cancelled = False
+    while len(res) < 2:
+        a, q = srv.step()
+        if not cancelled and a == 2:
+            srv.cancel(gone)
+            cancelled = True
+        for r in srv.results():
+            res[r["id"]] = r
+    assert res[gone]["status_name"] == "EMG_CANCELLED"
+    assert res[keep]["status"] == 0 and res[keep]["cycles"] == cycles_alone
+    np.testing.assert_array_equal(srv.take_state(keep), U_alone)
+    srv.close()
