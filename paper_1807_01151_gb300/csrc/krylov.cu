@@ -7,6 +7,8 @@
 // exp([[H_k, e_1], [0, 0]]), computed in one CTA by [13/13] Pade scaling-and-squaring
 // (Higham, SIAM J. Matrix Anal. Appl. 26 (2005) 1179).  The device decides happy
 // breakdown itself, so the loop needs no host round trip.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -14,6 +16,8 @@
 #include <mutex>
 
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace emg {
 
@@ -486,19 +490,33 @@ struct Pade13 {
     double b[14];
 };
 
-// C = A B on n x n shared matrices with leading dimension ld.
+constexpr int PHI_CLUSTER = 8;   // blocks (one per SM) sharing the dense products of k_phi
+
+// C = A B on n x n shared matrices with leading dimension ld, split over the cluster: block
+// r forms a contiguous range of the entries (each entry summed in k order by one thread,
+// as on a single block) and stores it into C of every block of the cluster.  The first
+// barrier keeps the stores from overwriting a C that a slower block still reads.
 __device__ __forceinline__ void smm(const double* A, const double* B, double* C, int n, int ld) {
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int nr = (int)cl.num_blocks(), rk = (int)cl.block_rank();
+    const int tot = n * n, per = (tot + nr - 1) / nr;
+    const int t0 = rk * per, t1 = (t0 + per) < tot ? (t0 + per) : tot;
+    cl.sync();
+    for (int t = t0 + (int)threadIdx.x; t < t1; t += (int)blockDim.x) {
         const int i = t / n, j = t % n;
         double s = 0.0;
         for (int k = 0; k < n; ++k) s += A[i * ld + k] * B[k * ld + j];
-        C[i * ld + j] = s;
+        for (int r = 0; r < nr; ++r) cl.map_shared_rank(C, r)[i * ld + j] = s;
     }
-    __syncthreads();
+    cl.sync();
 }
 
-// y = beta * [exp([[H, e1], [0, 0]])]_{0:k, k}
-__global__ void k_phi(int m, const double* __restrict__ H, double* __restrict__ y, Pade13 pc, DevScalars* sc) {
+// y = beta * [exp([[H, e1], [0, 0]])]_{0:k, k}.  A cluster of PHI_CLUSTER blocks: the dense
+// products (bound by one SM's FP64 rate on a single block) are shared out; the cheap
+// element-wise steps and the small pivoted solve are repeated in every block on its own
+// copies, so every block holds the same matrices and block 0 writes y.
+__global__ void __cluster_dims__(PHI_CLUSTER, 1, 1)
+    k_phi(int m, const double* __restrict__ H, double* __restrict__ y, Pade13 pc, DevScalars* sc) {
     extern __shared__ double sm[];
     const int k = sc->m_used;
     const double beta = sc->beta;
@@ -621,7 +639,8 @@ __global__ void k_phi(int m, const double* __restrict__ H, double* __restrict__ 
         X = Y;
         Y = t;
     }
-    for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = beta * X[i * ld + k];
+    if (cg::this_cluster().block_rank() == 0)
+        for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = beta * X[i * ld + k];
 }
 
 // out = u0 + V[0:k]^T y  (out = u0 when the start vector was zero)
@@ -750,7 +769,7 @@ emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, do
     EMG_CUDA_TRY(c, cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
         ProfScope _ps(c, PC_PHI);
-        k_phi<<<1, 256, smem, c->stream>>>(m, c->H, c->y, pade13(), c->sc);
+        k_phi<<<PHI_CLUSTER, 256, smem, c->stream>>>(m, c->H, c->y, pade13(), c->sc);
     }
     EMG_CHECK_LAUNCH(c);
     {
@@ -861,7 +880,7 @@ extern "C" emg_status emg_exp1_step_noalloc(int32_t dim, int64_t n_elems, const 
     const size_t smem = (size_t)8 * n * n * sizeof(double);
     if (cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return EMG_ERR_CUDA;
-    k_phi<<<1, 256, smem, st>>>(krylov_m, H, y, pade13(), sc);
+    k_phi<<<PHI_CLUSTER, 256, smem, st>>>(krylov_m, H, y, pade13(), sc);
     k_combine<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(296, (K0 + 255) / 256)), 256, 0, st>>>(
         K0, u0, V, y, sc, u_out);
     if (cudaGetLastError() != cudaSuccess) return EMG_ERR_CUDA;
