@@ -583,15 +583,26 @@ __global__ void __cluster_dims__(PHI_CLUSTER, 1, 1)
     }
     __syncthreads();
     for (int c = 0; c < n; ++c) {
-        if (threadIdx.x == 0) {
-            int pr = c;
-            double best = fabs(T1[c * ld + c]);
-            for (int r = c + 1; r < n; ++r)
-                if (fabs(T1[r * ld + c]) > best) {
-                    best = fabs(T1[r * ld + c]);
-                    pr = r;
+        if (threadIdx.x < 32) {
+            // pivot: the first row (lowest index) of largest |T1[r][c]|, r >= c, by one warp
+            double best = -1.0;
+            int bi = c;
+            for (int r = c + (int)threadIdx.x; r < n; r += 32) {
+                const double v = fabs(T1[r * ld + c]);
+                if (v > best) {
+                    best = v;
+                    bi = r;
                 }
-            s_piv = pr;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (threadIdx.x == 0) s_piv = bi;
         }
         __syncthreads();
         const int pr = s_piv;
