@@ -169,3 +169,39 @@ def test_manufactured_solution_order_p_plus_1():
         errs = [mms_error(n, p)[0] for n in sizes]
         rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
         assert rates[-1] > p + 1 - 0.35, (p, errs, rates)
+
+
+def test_residual_conservation_split_3d():
+    """The telescoping of interior fluxes in 3-D (cubed-sphere shell, wall and far field)."""
+    dg = DG(cubed_sphere_shell(2, 2), 1)
+    u = perturbed_state(dg, amp=0.05)
+    R = dg.residual(1, u)
+    total = np.einsum('e,ea->a', np.sqrt(dg.mesh.vol), R[:, :, 0])
+    L = dg.levels[1]
+    m = dg.mesh
+    UL = np.einsum('fai,fqi->fqa', u[m.bnd_L], L.bnd_psi)
+    code = np.broadcast_to(L.bnd_code[:, None], UL.shape[:2])
+    Gs = dg.ghost(UL, L.bnd_n, L.bnd_x, code, L.bnd_wn)
+    bflux = np.einsum('fq,fqa->a', L.bnd_amag, euler.roe(UL, Gs, L.bnd_n))
+    assert np.allclose(total, -bflux, rtol=1e-12, atol=1e-13 * np.abs(bflux).max())
+
+
+def test_jvp_and_blocks_against_finite_differences_3d():
+    dg = DG(cubed_sphere_shell(2, 1), 2)
+    u = perturbed_state(dg, amp=0.05)
+    rng = np.random.default_rng(1)
+    eps = 1e-6
+    for p in (2, 1):
+        up = np.ascontiguousarray(u[:, :, :dg.N(p)])
+        x = rng.standard_normal(up.shape)
+        fd = (dg.residual(p, up + eps * x) - dg.residual(p, up - eps * x)) / (2 * eps)
+        jv = dg.jvp(p, up, x)
+        assert np.abs(fd - jv).max() < 1e-7 * np.abs(jv).max()
+        D = dg.diag_blocks(p, up)
+        b = 5 * dg.N(p)
+        for (e, col) in [(0, 0), (5, b - 1), (17, b // 2)]:
+            a, j = divmod(col, dg.N(p))
+            du = np.zeros_like(up)
+            du[e, a, j] = 1.0
+            fdc = (dg.residual(p, up + eps * du) - dg.residual(p, up - eps * du))[e].ravel() / (2 * eps)
+            assert np.abs(fdc - D[e, :, col]).max() < 1e-7 * np.abs(D[e]).max()
