@@ -27,7 +27,9 @@ function; flux Jacobian against the closed form of the Appendix (Eq. dfdu);
 free-stream preservation; discrete conservation; order p+1 on a manufactured
 solution; Jacobian blocks against central finite differences and dense brute force;
 PRK amplification polynomial; Krylov phi_1 against dense expm, linear-ODE
-exactness and the dt limits; restriction/prolongation identities; h_2D = 4A/P and
+exactness and the dt limits; the EXP1 step on tiny p = 0 meshes (Krylov space
+exhausted) against the dense phi_1(DT J_0) DT R~_0 from its Taylor series and from
+A^-1 (e^A - I) N; restriction/prolongation identities; h_2D = 4A/P and
 Eq. x2d; CFL_n sequence; converged state symmetry and path independence.
 
 Parity unpinned: the paper's own iteration counts and CPU times (its figures are

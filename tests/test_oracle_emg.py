@@ -152,3 +152,49 @@ def test_emg_converges_to_the_newton_steady_state():
     u, cycles, ok = emg.solve_steady(dg, u0, drop=1e-11, max_cycles=300)
     assert ok, cycles
     assert np.abs(u - u_newton).max() < 1e-9 * np.abs(u_newton).max()
+
+
+def _phi1_taylor(A, N, terms=80):
+    """phi_1(A) N = sum_k A^k N / (k+1)! (the series definition; no matrix exponential)."""
+    out = np.zeros_like(N)
+    t = N.copy()
+    for k in range(terms):
+        out += t
+        t = A @ t / (k + 2)
+    return out
+
+
+@pytest.mark.parametrize("mk", [lambda: ogrid(4, 1), lambda: ogrid(3, 2),
+                                lambda: __import__("workloads").cubed_sphere_shell(1, 1)])
+def test_exp1_step_equals_dense_phi1_on_exhausted_krylov_space(mk):
+    """EXP1 on level 0 (Eq. EXP1 with local steps, du/dtau = DT R): on a tiny p = 0 mesh
+    (K0 = 5E <= m) the Krylov space is the whole space, so the oracle's step must equal the
+    dense u0 + phi_1(A) N with A = DT J_0 and N = DT (R_0(u0) + tau0), DT = diag(dt_e)
+    repeated over the five variables.  The local steps differ between elements, so A = J DT
+    or N = R (no DT) would fail; tau0 != 0 checks that the forcing enters N.  phi_1 is taken
+    from its Taylor series at a moderate step and from A^-1 (e^A - I) N at a large one."""
+    dg = DG(mk(), 0)
+    assert 5 * dg.E <= 30
+    u0 = perturbed_state(dg, amp=0.05)
+    tau0 = 1e-3 * np.random.default_rng(21).standard_normal(u0.shape)
+    J = dg.full_jacobian(0, u0)
+    R = (dg.residual(0, u0) + tau0).ravel()
+    base = emg.dtau(dg, 0, u0, 1.0)
+    assert base.max() > 1.05 * base.min()            # genuinely local steps
+    for scale, kind in ((0.5, "taylor"), (50.0, "dense")):
+        dt = scale * base
+        DT = np.repeat(dt, 5)
+        A = DT[:, None] * J
+        Nv = DT * R
+        if kind == "taylor":
+            assert np.linalg.norm(A, 2) < 4.0        # the series converges fast
+            ref = _phi1_taylor(A, Nv)
+        else:
+            ref = np.linalg.solve(A, (scipy.linalg.expm(A) - np.eye(len(Nv))) @ Nv)
+        u1, k = emg.exp1_step(dg, u0, tau0, dt, emg.Options(krylov_m=30))
+        assert k <= 5 * dg.E + 1
+        du = (u1 - u0).ravel()
+        assert np.abs(du - ref).max() <= 1e-10 * np.abs(ref).max(), (kind, np.abs(du - ref).max())
+        # the same step without the forcing differs: tau0 is really part of N
+        u1b, _ = emg.exp1_step(dg, u0, np.zeros_like(u0), dt, emg.Options(krylov_m=30))
+        assert np.abs((u1b - u1).ravel()).max() > 1e-6 * np.abs(ref).max()
