@@ -30,12 +30,11 @@ WORKLOADS = {
     "cyl32x16_p2": dict(name="cyl32x16_p2", n_theta=32, n_r=16, p_max=2, mach=0.3),
 }
 METRIC = "time to 1e-10 residual drop & DG residual GDoF/s: mixed vs FP64, 1 GB300"
-FP64_PEAK_TFLOPS = 1.254     # FP64 FMA throughput of a GB300, measured with a register-only FMA loop
 # DRAM bytes (read + write) of one k_volume launch at p = 4 on the 128 x 64 O-grid, from an ncu
 # capture of this kernel (dram__bytes_read.sum + dram__bytes_write.sum); None once the kernel
 # changes until it is captured again.
 VOLUME_P4_TRAFFIC = {"cyl128x64_p4": 142.427e6}
-PREC_NAMES = {0: "fp64", 1: "fp32_blocks"}
+PREC_NAMES = {0: "fp64", 1: "fp32_blocks", 2: "bf16_blocks"}
 
 
 def parse():
@@ -82,7 +81,7 @@ def dist_info():
 
 def oracle_sample(W, steps, warmup):
     """The oracle's V-cycle (FP64 numpy) on a bounded sample of the workload: the same
-    O-grid family and degree at 16 x 8 elements.  Returns (GDoF/s, seconds, threads, E)."""
+    O-grid family and degree at 16 x 8 elements.  Returns (GDoF/s, seconds, E)."""
     from oracle import emg as oemg
     from oracle.dg import DG
     from workloads import ogrid
@@ -99,12 +98,39 @@ def oracle_sample(W, steps, warmup):
         n += 1
     el = time.perf_counter() - t
     K = 5 * dg.N(W["p_max"]) * dg.E
-    try:
-        from threadpoolctl import threadpool_info
-        threads = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
-    except Exception:
-        threads = 1
-    return K * steps / el / 1e9, el, threads, dg.E
+    return K * steps / el / 1e9, el, dg.E
+
+
+def _one_thread():
+    """Pool initializer: one BLAS/OpenMP thread per worker process (one core each)."""
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def _oracle_job(a):
+    return oracle_sample(*a)
+
+
+def oracle_cores(W, steps, warmup, cores):
+    """The oracle sample on `cores` host cores at once: one worker process per core (spawned,
+    never forked after CUDA), each on its own copy of the sample; the aggregate rate is the
+    sum of the workers' rates over their timed loops.  Returns (GDoF/s, wall s, E)."""
+    import multiprocessing as mp
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores, initializer=_one_thread) as pool:
+        res = pool.map(_oracle_job, [(W, steps, warmup)] * cores)
+    return sum(r[0] for r in res), time.perf_counter() - t0, res[0][2]
+
+
+def cpu_baseline(W, steps, warmup):
+    """The oracle on one core and on every host core (os.cpu_count())."""
+    ncores = os.cpu_count() or 1
+    v1, el1, E = oracle_cores(W, steps, warmup, 1)
+    vall, elall, _ = oracle_cores(W, steps, warmup, ncores)
+    sample = (f"{steps} oracle V-cycles (after {warmup} untimed) of the 16x8 O-grid at p={W['p_max']} "
+              f"({E} elements) per core")
+    return {"value": vall, "unit": "GDoF/s", "cores": ncores, "kind": "oracle", "sample": sample,
+            "single_core": {"value": v1, "cores": 1, "wall_s": round(el1, 2)}, "wall_s": round(elall, 2)}
 
 
 class Clocks:
@@ -162,23 +188,53 @@ def measured_peaks():
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle, as it stands, on every host core (one spawned worker
+    per core, each on its own copy of the bounded sample; rank 0 only)."""
     if rank != 0:
         return
     W = WORKLOADS[args.workload]
-    v, el, threads, E = oracle_sample(W, args.steps, args.warmup)
+    ncores = os.cpu_count() or 1
+    v, el, E = oracle_cores(W, args.steps, args.warmup, ncores)
+    sample = (f"{args.steps} oracle V-cycles (after {args.warmup} untimed) of the 16x8 O-grid at p={W['p_max']} "
+              f"({E} elements) per core, {ncores} cores")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "GDoF/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": W["name"], "sample": f"oracle V-cycles on the 16x8 O-grid at p={W['p_max']} ({E} elements)"},
-        "cpu_baseline": {"value": v, "unit": "GDoF/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{args.steps} oracle V-cycles, 16x8 O-grid, p={W['p_max']}"},
+        "config": {"workload": W["name"], "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "GDoF/s", "cores": ncores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks):
+def kernel_rooflines(prof_cycle, work, peaks, hbm_gbs, form):
+    """Achieved rate of each kernel class (algorithmic work of one cycle / its measured time
+    per cycle) against the roof that bounds it."""
+    out = {}
+    alu64, alu32 = peaks["fp64_tflops"], peaks["fp32_tflops"]
+    roofs = {"residual_volume": ("alu", alu64), "residual_face_flux": ("alu", alu64),
+             "diag_block_assembly": ("alu", alu64 if form == 0 else alu32),
+             "block_lu": ("alu", alu64 if form == 0 else alu32),
+             "prk_stage_solve": ("hbm", hbm_gbs), "arnoldi": ("hbm", hbm_gbs)}
+    for k, (bound, peak) in roofs.items():
+        if k not in prof_cycle or k not in work:
+            continue
+        ms = prof_cycle[k]["ms_per_cycle"]
+        if ms <= 0:
+            continue
+        if bound == "alu":
+            ach = work[k][0] / (ms * 1e-3) / 1e12
+            out[k] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                      "ms_per_cycle": ms}
+        else:
+            ach = work[k][1] / (ms * 1e-3) / 1e9
+            out[k] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                      "ms_per_cycle": ms}
+    return out
+
+
+def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks, peaks, hbm_gbs):
     """Time K V-cycles of one form; return a dict of results (and the solver closed)."""
     from paper_1807_01151_gb300 import perfmodel
     stream = torch.cuda.Stream()
@@ -187,7 +243,7 @@ def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks):
     K = 5 * N * E
     F = (4 * E + 2 * W["n_theta"]) // 2
     s.set_state(None)
-    for _ in range(args.warmup):
+    for _ in range(max(args.warmup, 3)):
         s.vcycle(info=False)
     torch.cuda.synchronize()
 
@@ -198,7 +254,7 @@ def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks):
 
     outdir = clocks_dir()
     clocks = Clocks(local, os.path.join(outdir, f"clocks_rank{rank}_{PREC_NAMES[prec]}.csv")) if with_clocks else None
-    s.profile(True)
+    # timed region: the product path (captured graphs replayed), profiler off
     l0 = s.launch_count
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -210,12 +266,21 @@ def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks):
     barrier()
     ms = ev0.elapsed_time(ev1)
     launches = s.launch_count - l0
-    prof = s.profile_read()
-    s.profile(False)
     clk = clocks.stop() if clocks else None
     ms = max_over_ranks(ms)
     out = {"value": world * K * args.steps / (ms * 1e-3) / 1e9, "ms_per_step": ms / args.steps,
-           "gpu_launches": launches, "clocks": clk, "K": K, "E": E}
+           "gpu_launches": launches, "graph_kernels": s.graph_kernels, "clocks": clk, "K": K, "E": E}
+    # a separate pass with the event profiler (kernel by kernel) for the split per kernel class
+    nprof = max(3, min(args.steps, 5))
+    s.profile(True)
+    for _ in range(nprof):
+        s.vcycle(info=False)
+    prof = s.profile_read()
+    s.profile(False)
+    prof_cycle = {k: {"ms_per_cycle": v[0] / nprof, "launches_per_cycle": v[1] / nprof}
+                  for k, v in prof.items() if v[1]}
+    out["kernels"] = prof_cycle
+    out["kernels_total_ms_per_cycle"] = sum(v["ms_per_cycle"] for v in prof_cycle.values())
     # residual throughput (p_max residual, device buffers, back-to-back)
     u = torch.empty((E, 5, N), dtype=torch.float64, device="cuda")
     R = torch.empty_like(u)
@@ -262,25 +327,23 @@ def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks):
         out["time_to_1e-10"] = {"seconds": time.perf_counter() - t0, "cycles": rep["cycles"],
                                 "converged": rep["converged"],
                                 "drop": rep["res_final"] / rep["res0"] if rep["res0"] else None}
-    # per-class kernel times over the timed region; the roofline of the dominant FP64
-    # kernel, k_volume at p_max, per launch (algorithmic FLOPs / live launch time)
+        out["state"] = s.get_state()
+    # roofline of the dominant FP64 kernel, k_volume at p_max, per launch (algorithmic FLOPs /
+    # live launch time), and of every kernel class per cycle
     work = perfmodel.vcycle_work(2, W["p_max"], E, F)
-    out["kernels"] = {k: {"ms_per_cycle": v[0] / args.steps, "launches_per_cycle": v[1] / args.steps}
-                      for k, v in prof.items() if v[1]}
     fl = perfmodel.residual_volume_flops(perfmodel.Shape(2, W["p_max"], E, F))
     achieved = fl / (vol_launch_ms * 1e-3) / 1e12
+    pk = peaks["fp64_tflops"]
     out["roofline"] = {"bound": "alu", "kernel": f"k_volume<2,{W['p_max']}> (DG residual, volume + face projection)",
-                       "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                       "frac": achieved / FP64_PEAK_TFLOPS, "traffic": VOLUME_P4_TRAFFIC.get(W["name"]),
-                       "peak_source": "FP64 FMA throughput of a GB300 measured with a register-only FMA loop",
+                       "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                       "traffic": VOLUME_P4_TRAFFIC.get(W["name"]),
+                       "peak_source": (f"emg_probe_peaks on this GPU: register-only FP64 FMA loop, "
+                                       f"{peaks['sm_mhz']:.0f} MHz; unit count check: 2 FP64 FMA/clk/SM x 152 SMs x "
+                                       f"2 flop x {peaks['sm_mhz']:.0f} MHz = "
+                                       f"{2 * 152 * 2 * peaks['sm_mhz'] * 1e6 / 1e12:.3f} TFLOP/s"),
                        "algorithmic_flops_per_launch": fl, "ms_per_launch": vol_launch_ms,
-                       "note": "FMA-only flop model; ncu shows the FP64 pipe 87.6 % busy for this kernel"}
-    if prec == 0:
-        top = "diag_block_assembly"
-        t_top = prof[top][0] * 1e-3 / args.steps
-        out["assembly_roofline"] = {"bound": "alu", "achieved": work[top][0] / t_top / 1e12, "peak": FP64_PEAK_TFLOPS,
-                                    "unit": "TFLOP/s", "frac": work[top][0] / t_top / 1e12 / FP64_PEAK_TFLOPS,
-                                    "ms_per_cycle": t_top * 1e3}
+                       "note": "FMA-only flop model (perfmodel.residual_volume_flops)"}
+    out["rooflines"] = kernel_rooflines(prof_cycle, work, peaks, hbm_gbs, prec)
     s.close()
     return out
 
@@ -353,40 +416,60 @@ def main():
         return run_reference(args, rank, world)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, el, threads, E = oracle_sample(W, 2, 0)   # before any GPU work (no fork after CUDA init)
-        cpu = {"value": v, "unit": "GDoF/s", "cores": threads, "kind": "oracle",
-               "sample": f"2 oracle V-cycles of the 16x8 O-grid at p={W['p_max']} ({E} elements), {el:.1f} s"}
+        cpu = cpu_baseline(W, 2, 0)   # spawned workers, before any GPU work
     import torch
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_1807_01151_gb300 as pkg
+    from paper_1807_01151_gb300._lib import probe_peaks
     from workloads import ogrid
+    peaks = probe_peaks()
+    mp_, mp_src = measured_peaks()
+    hbm_gbs = float(mp_.get("hbm_gbs", 6800.0))
     mesh = ogrid(W["n_theta"], W["n_r"])
     precs = {"both": [1, 0], "mixed": [1], "fp64": [0]}[args.prec]
-    res = {p: measure(pkg, torch, mesh, W, p, args, world, local, rank, with_clocks=(i == 0))
+    res = {p: measure(pkg, torch, mesh, W, p, args, world, local, rank, with_clocks=(i == 0), peaks=peaks,
+                      hbm_gbs=hbm_gbs)
            for i, p in enumerate(precs)}
     head = res[precs[0]]
     if rank == 0:
+        t_key = {}
+        for p in precs:
+            t = res[p].get("time_to_1e-10")
+            if t:
+                t_key[f"t_1e-10_{PREC_NAMES[p]}_s"] = round(t["seconds"], 3)
+                t_key[f"cycles_1e-10_{PREC_NAMES[p]}"] = t["cycles"]
+                t_key[f"converged_{PREC_NAMES[p]}"] = t["converged"]
+        if all("state" in res[p] for p in (0, 1) if p in res) and 0 in res and 1 in res:
+            a, b = res[1]["state"], res[0]["state"]
+            import numpy as np
+            t_key["mixed_vs_fp64_converged_relerr"] = float(np.abs(a - b).max() / np.abs(b).max())
         line = {
-            "metric": METRIC, "value": head["value"], "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64+f32" if precs[0] == 1 else "f64", "data": "synthetic",
+            "metric": METRIC, "value": head["value"], "unit": "GDoF/s", **t_key,
+            "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if precs[0] == 1 else "f64",
+            "data": "synthetic",
             "config": {"workload": W["name"], "mesh": f"O-grid {W['n_theta']}x{W['n_r']} r in [0.5,20]",
                        "p_max": W["p_max"], "elements": head["E"], "dof": head["K"], "mach": W["mach"],
                        "form": PREC_NAMES[precs[0]],
                        "l2": "inputs larger than L2: tables and block factors stream > 1 GB per V-cycle",
+                       "timed_path": "captured V-cycle graphs replayed, profiler off",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "residual_gdofs": head["residual_gdofs"], "residual_ms": head["residual_ms"],
             "time_to_1e-10": head.get("time_to_1e-10"),
             "e2e": head["e2e"], "gpu_launches": head["gpu_launches"], "roofline": head["roofline"],
-            "clocks": head["clocks"], "cpu_baseline": cpu, "kernels": head["kernels"],
+            "clocks": head["clocks"], "cpu_baseline": cpu,
+            "peaks": dict(peaks, hbm_gbs=hbm_gbs, hbm_source=mp_src),
+            "rooflines": head["rooflines"], "kernels": head["kernels"],
+            "kernels_total_ms_per_cycle": head["kernels_total_ms_per_cycle"],
         }
         for p in precs[1:]:
             r = res[p]
             line[PREC_NAMES[p]] = {k: r[k] for k in ("value", "ms_per_step", "residual_gdofs", "time_to_1e-10",
-                                                     "gpu_launches", "assembly_roofline", "kernels") if k in r}
+                                                     "gpu_launches", "rooflines", "kernels") if k in r}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -48,11 +48,15 @@ typedef enum {
 #define EMG_BC_INTERIOR (-1)
 #define EMG_BC_WALL 1      /* inviscid slip wall: ghost with mirrored normal velocity (Sec. 3.3) */
 #define EMG_BC_FARFIELD 2  /* characteristic far field from 1-D Riemann invariants (Sec. 5)     */
+#define EMG_BC_SYMMETRY 3  /* symmetry plane of the sphere case (Sec. 5): ghost state with the
+                              velocity mirrored about the (flat) face normal                   */
 
 typedef enum {
     EMG_PREC_FP64 = 0,        /* every step in float64                                   */
-    EMG_PREC_FP32_BLOCKS = 1  /* PRK block assembly, LU and solves in float32; residual,
+    EMG_PREC_FP32_BLOCKS = 1, /* PRK block assembly, LU and solves in float32; residual,
                                  Arnoldi and phi_1 in float64                             */
+    EMG_PREC_BF16_BLOCKS = 2  /* as EMG_PREC_FP32_BLOCKS, but the block assembly multiplies
+                                 bfloat16 operands (float32 accumulation)                 */
 } emg_prec;
 
 /* Mesh of straight-sided bilinear quadrilaterals (dim 2) or trilinear hexahedra (dim 3).
@@ -107,6 +111,22 @@ typedef struct {
                               result), for contexts that share the device with other work, where
                               the blocks of a persistent kernel may not all be resident at once
                               (the request loop uses 0). */
+    double krylov_tol;     /* 0 (default): the Arnoldi process takes krylov_m steps (or stops at
+                              happy breakdown).  > 0: the Krylov tolerance of Sec. 5 (paper:
+                              1e-5); step j ends the process when the leading term of the phi_1
+                              error series, beta h_{j+1,j} |(phi_2(H_j) e_1)_j|, is at most
+                              krylov_tol * beta ||phi_1(H_j) e_1|| (phi_1 and phi_2 from one
+                              exponential of the (j+2)-augmented Hessenberg matrix). */
+    int32_t exp_dt_global; /* 0 (default): local EXP1 steps dt_e = factor * dtau_e (p = p_max);
+                              1: one step for the whole mesh, min_e dt_e (Eq. EXP1 as written) */
+    int32_t jac_freeze;    /* k >= 1: the PRK block factors of every level are assembled and
+                              factored in V-cycles n with (n - 1) mod k = 0 only and reused by the
+                              other cycles (a frozen preconditioner; the fixed point R = 0 is
+                              unchanged).  1 (default): every cycle. */
+    int32_t quad_extra;    /* q = p + quad_extra Gauss points per direction and level; only the
+                              rule q = p + 2 is built (2, the default; 0 is read as 2) */
+    double omega[3];       /* angular velocity of the rotating frame (Eq. euler); only the
+                              absolute frame omega = 0 is built (other values: EMG_ERR_ARG) */
 } emg_params;
 
 typedef struct {
@@ -152,10 +172,11 @@ emg_status emg_get_state(emg_ctx* ctx, double* U, int32_t on_device);
 emg_status emg_set_cycle(emg_ctx* ctx, int64_t n, double res_ref);
 emg_status emg_get_cycle(emg_ctx* ctx, int64_t* n, double* res_ref);
 
-/* One FAS V-cycle p_max -> 0 -> p_max (Sec. 2.3): one PRK step (Eq. prk_scalar) per level
- * p >= 1 with exact element-diagonal Jacobian blocks (Eq. jac1) and P = I/dtau - dR/du,
- * restriction/forcing, EXP1 (Eq. EXP1) with an Arnoldi phi_1 product (Eqs. vm, final) on
- * p = 0, prolongation and correction.  info may be NULL (then nothing is read back). */
+/* One FAS V-cycle p_max -> 0 -> p_max (Sec. 2.3): params.pre_smooth PRK steps (Eq.
+ * prk_scalar; default 2) per level p >= 1 on the down leg, with exact element-diagonal
+ * Jacobian blocks (Eq. jac1) and P = I/dtau - dR/du, restriction/forcing, one EXP1 step
+ * (Eq. EXP1) with an Arnoldi phi_1 product (Eqs. vm, final) on p = 0, prolongation and
+ * correction, no post-smoothing.  info may be NULL (then nothing is read back). */
 emg_status emg_vcycle(emg_ctx* ctx, emg_cycle_info* info);
 
 /* Run V-cycles until ||R(rho)|| <= drop * ||R(rho)|| of the entry state, or max_cycles.
@@ -192,8 +213,9 @@ emg_status emg_exp1_step(emg_ctx* ctx, const double* u0, const double* tau0, con
 
 /* ---- EXP1 step that allocates nothing (the paper has no counterpart) ----
  * For callers that cannot allocate device memory once they are running: an application
- * whose device memory is handed out only by its own pool, or code that issues this step
- * while a stream is being captured and so may not call cudaMalloc.  The step is the same
+ * whose device memory is handed out only by its own pool (a caching allocator that already
+ * holds what the device has free, so a cudaMalloc would fail), or a loop that may not stall
+ * on the implicit device-wide synchronisation a cudaMalloc/cudaFree can take.  The step is the same
  * as emg_exp1_step (u_out = u0 + phi_1(DT J_0) DT r0, m Arnoldi steps with happy
  * breakdown, Pade phi_1), but it takes the p = 0 Jacobian in the block form that
  * emg_jacobian_p0 returns and the residual r0 = R~_0(u0), and needs no context.
@@ -204,9 +226,13 @@ emg_status emg_exp1_step(emg_ctx* ctx, const double* u0, const double* tau0, con
  * All array arguments are device pointers on the current device: diag [n_elems][5][5],
  * off [n_elems][2 dim][5][5], nbr [n_elems][2 dim] (neighbour or -1), r0 and u0 and
  * u_out [n_elems][5], dt [n_elems].  Work is enqueued on cuda_stream (NULL = the legacy
- * default stream) and the call synchronises it to read krylov_dim (may be NULL).
+ * default stream); the call then reads the Krylov dimension and the status flags back
+ * and synchronises that stream before it returns (krylov_dim may be NULL).
  * The first call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture.  Every call on a device
+ * current (once per device, safe from several host threads); make that first call
+ * before any stream capture.  Every neighbour index must be -1 or in [0, n_elems): the
+ * packing kernel checks each one and the call returns EMG_ERR_ARG, without running the
+ * Krylov step, if any is out of range.  Every call on a device
  * shares the one array and finds the previous call's contents in it (the call clears
  * what must start at zero), so calls whose work overlaps on the GPU, from several
  * streams or host threads, race and must be serialised by the caller.
@@ -215,6 +241,17 @@ emg_status emg_exp1_step(emg_ctx* ctx, const double* u0, const double* tau0, con
 emg_status emg_exp1_step_noalloc(int32_t dim, int64_t n_elems, const double* diag, const double* off,
                                  const int64_t* nbr, const double* r0, const double* dt, const double* u0,
                                  int32_t krylov_m, void* cuda_stream, double* u_out, int32_t* krylov_dim);
+
+/* The block operator the PRK stages of level p apply (Eq. prk_scalar), in the context's
+ * precision form, for the state u [n_elems][5][N_p] at the given CFL:
+ *   which = 0: P_e = I/dtau_e - D_e(u) as assembled (Eq. jac1 with dtau_e of Eq. x3d);
+ *   which = 1: P_e^{-1} as the stages apply it (the float32 explicit inverse of the
+ *              EMG_PREC_FP32_BLOCKS and EMG_PREC_BF16_BLOCKS forms; EMG_ERR_ARG for the
+ *              FP64 form, which keeps LU factors instead).
+ * out: [n_elems][5 N_p][5 N_p] float64, row-major, row/column index var*N_p + mode (float32
+ * values widened exactly).  Uses (and overwrites) the level's block storage. */
+emg_status emg_block_operator(emg_ctx* ctx, int32_t p, const double* u, double cfl, int32_t which,
+                              double* out, int32_t on_device);
 
 /* Element volumes |E| and length scales h = 2d|E|/|dE| (Eq. x3d), [n_elems] each. */
 emg_status emg_element_geometry(emg_ctx* ctx, double* vol, double* h);
@@ -314,6 +351,14 @@ emg_status emg_server_cancel(emg_server* srv, int64_t id);
 /* Copy the kept converged state of request id ([n_elems][5][N_pmax], n doubles) to host
  * memory and release it.  EMG_ERR_ARG if none is kept or n does not match. */
 emg_status emg_server_take_state(emg_server* srv, int64_t id, double* U, int64_t n);
+
+/* ---- arithmetic peaks of the current device (no counterpart in the paper) ----
+ * Register-only multiply-add loops (every block of the grid resident, 8 independent
+ * chains per thread, no memory traffic in the timed loop), timed with CUDA events:
+ * float64 and float32 FMA throughput in TFLOP/s (2 flop per FMA).  These are the
+ * denominators of the ALU rooflines of the FP64 residual and the FP32 block kernels.
+ * sm_mhz receives the SM clock the device reports for the run (may be NULL). */
+emg_status emg_probe_peaks(double* fp64_tflops, double* fp32_tflops, double* sm_mhz);
 
 /* Build identification string (architecture and kernel variants). */
 const char* emg_build_info(void);

@@ -20,7 +20,7 @@ import numpy as np
 from . import euler
 from .basis import Basis, n_modes
 from .geometry import Mesh, volume_rule
-from workloads import BC_WALL, BC_FARFIELD, BC_EXACT
+from workloads import BC_WALL, BC_FARFIELD, BC_SYMMETRY, BC_EXACT
 
 CSTEP = 1e-30
 
@@ -102,13 +102,17 @@ class DG:
 
     # -- residual -------------------------------------------------------------
     def ghost(self, UL, n, x, code, wn=None):
-        """Ghost states; the slip wall mirrors the velocity about wn (body normal)."""
+        """Ghost states; the slip wall mirrors the velocity about wn (body normal), a
+        symmetry plane (Sec. 5, sphere case) about the face's own normal n."""
         G = np.empty_like(UL)
         wall = code == BC_WALL
         far = code == BC_FARFIELD
+        sym = code == BC_SYMMETRY
         exact = code == BC_EXACT
         if wall.any():
             G[wall] = euler.wall_ghost(UL[wall], (n if wn is None else wn)[wall])
+        if sym.any():
+            G[sym] = euler.wall_ghost(UL[sym], n[sym])
         if far.any():
             G[far] = euler.farfield_ghost(UL[far], n[far], self.Uinf, self.gamma)
         if exact.any():

@@ -17,6 +17,13 @@ Passages followed:
   tau_{p-1} = restrict(R~_p(v_p)) - R_{p-1}(restrict(v_p)), R~_p = R_p + tau_p.
 * Eq. x3d: dtau = CFL h / ((2p+1)(|v|+c)) with v, c at the cell centre;
   EXP1 step dt_e = (p_max+1) dtau_e at p = p_max (Sec. 4).
+* Krylov tolerance (Sec. 5: m = 30, tolerance 1e-5; the criterion is not stated).
+  Reading: after k Arnoldi steps the process ends when the leading term of the error
+  series of the phi_1 approximation, beta h_{k+1,k} |(phi_2(H_k) e_1)_k|, is at most
+  tol * beta ||phi_1(H_k) e_1||; phi_1(H_k) e_1 and phi_2(H_k) e_1 are the last two
+  columns of exp([[H_k, e_1, 0], [0, 0, 1], [0, 0, 0]]).  tol = 0: fixed m.
+* Variants (Sec. 2.3, Sec. 4): a global EXP1 step min_e dt_e (Eq. EXP1 with one dt) and
+  block factors frozen for k V-cycles (re-evaluated in cycles n with (n-1) mod k = 0).
 * Eq. cfl: CFL_n = min{CFL_max, max[||R(rho_n)||^-1, 1 + (n-1)/(2p+1)]},
   ||R(rho)|| = (1/|Omega|) (sum_e sum_i R_{e,rho,i}^2)^(1/2), p = p_max.  Reading:
   the inverse-residual branch uses the residual relative to the first cycle's,
@@ -41,6 +48,10 @@ class Options:
     breakdown_rel: float = 1e-12
     res_ref: float = 0.0            # ||R(rho_1)|| of the first cycle (set by the driver)
     pre_smooth: int = 2             # PRK steps per level on the down leg
+    krylov_tol: float = 0.0         # > 0: stop the Arnoldi process by the error estimate
+    exp_dt_global: bool = False     # one EXP1 step min_e dt_e for the whole mesh
+    jac_freeze: int = 1             # block factors re-evaluated every jac_freeze cycles
+    frozen: dict = field(default_factory=dict)   # level -> last P (jac_freeze > 1)
 
 
 def prk_step(resid, P, u_n, stages=4):
@@ -56,7 +67,24 @@ def prk_step(resid, P, u_n, stages=4):
     return u
 
 
-def arnoldi(matvec, b, m, breakdown_rel=1e-12):
+def phi12_small(H):
+    """(phi_1(H) e_1, phi_2(H) e_1) from exp([[H, e_1, 0], [0, 0, 1], [0, 0, 0]])."""
+    k = H.shape[0]
+    A = np.zeros((k + 2, k + 2))
+    A[:k, :k] = H
+    A[0, k] = 1.0
+    A[k, k + 1] = 1.0
+    X = scipy.linalg.expm(A)
+    return X[:k, k], X[:k, k + 1]
+
+
+def krylov_converged(H, k, tol):
+    """The Krylov tolerance test after k steps (H [k+1][k] with the subdiagonal h_{k+1,k})."""
+    phi1, phi2 = phi12_small(H[:k, :k])
+    return H[k, k - 1] * abs(phi2[k - 1]) <= tol * np.linalg.norm(phi1)
+
+
+def arnoldi(matvec, b, m, breakdown_rel=1e-12, tol=0.0):
     """Arnoldi with modified Gram-Schmidt (Eq. vm).  Returns V [k][K], H [k][k], beta, k."""
     beta = np.linalg.norm(b)
     K = b.size
@@ -76,6 +104,9 @@ def arnoldi(matvec, b, m, breakdown_rel=1e-12):
         if H[j + 1, j] <= breakdown_rel * w0:
             k = j + 1
             break
+        if tol > 0.0 and j + 1 < m and krylov_converged(H, j + 1, tol):
+            k = j + 1
+            break
         V[j + 1] = w / H[j + 1, j]
     return V[:k], H[:k, :k], beta, k
 
@@ -89,9 +120,9 @@ def phi1_small(H):
     return scipy.linalg.expm(A)[:k, k]
 
 
-def krylov_phi1(matvec, b, m, breakdown_rel=1e-12):
+def krylov_phi1(matvec, b, m, breakdown_rel=1e-12, tol=0.0):
     """phi_1(A) b ~= beta V_k phi_1(H_k) e_1 (Eq. final with dt absorbed in A)."""
-    V, H, beta, k = arnoldi(matvec, b, m, breakdown_rel)
+    V, H, beta, k = arnoldi(matvec, b, m, breakdown_rel, tol)
     if k == 0:
         return np.zeros_like(b), 0
     y = beta * phi1_small(H)
@@ -125,7 +156,7 @@ def exp1_step(dg, u0, tau0, dt, opts):
     def matvec(x):
         return (dt[:, None, None] * dg.jvp(0, u0, x.reshape(u0.shape))).ravel()
 
-    du, k = krylov_phi1(matvec, Nv, opts.krylov_m, opts.breakdown_rel)
+    du, k = krylov_phi1(matvec, Nv, opts.krylov_m, opts.breakdown_rel, opts.krylov_tol)
     return u0 + du.reshape(u0.shape), k
 
 
@@ -164,6 +195,9 @@ def vcycle(dg, u, n, opts=None):
     R0, res, cfl = vcycle_entry(dg, u, n, opts)
     fac = opts.exp_dt_factor if opts.exp_dt_factor > 0 else P + 1
     dt = fac * dtau(dg, P, u, cfl)
+    if opts.exp_dt_global:
+        dt = np.full_like(dt, dt.min())
+    frozen = opts.jac_freeze > 1 and len(opts.frozen) > 0 and (n - 1) % opts.jac_freeze != 0
     v = {P: u}
     v0 = {}
     tau = {P: np.zeros_like(u)}
@@ -171,11 +205,16 @@ def vcycle(dg, u, n, opts=None):
         def resid(w, p=p):
             return dg.residual(p, w) + tau[p]
         for _ in range(opts.pre_smooth):
-            # P(u^n) is re-evaluated at the state entering every PRK step
-            D = dg.diag_blocks(p, v[p])
-            dt_p = dtau(dg, p, v[p], cfl)
-            b = D.shape[-1]
-            Pm = np.eye(b)[None, :, :] / dt_p[:, None, None] - D
+            if frozen:
+                Pm = opts.frozen[p]       # the factors of the last cycle that evaluated them
+            else:
+                # P(u^n) is re-evaluated at the state entering every PRK step
+                D = dg.diag_blocks(p, v[p])
+                dt_p = dtau(dg, p, v[p], cfl)
+                b = D.shape[-1]
+                Pm = np.eye(b)[None, :, :] / dt_p[:, None, None] - D
+                if opts.jac_freeze > 1:
+                    opts.frozen[p] = Pm
             v[p] = prk_step(resid, Pm, v[p], opts.rk_stages)
         nc = dg.N(p - 1)
         v0[p - 1] = restrict(v[p], nc)

@@ -26,7 +26,9 @@ class ParamsC(C.Structure):
                 ("p_max", C.c_int32), ("rk_stages", C.c_int32), ("krylov_m", C.c_int32),
                 ("cfl_max", C.c_double), ("exp_dt_factor", C.c_double), ("pre_smooth", C.c_int32),
                 ("prec", C.c_int32), ("cuda_stream", C.c_void_p), ("lag_blocks", C.c_int32),
-                ("use_graph", C.c_int32), ("autotune", C.c_int32), ("coop_krylov", C.c_int32)]
+                ("use_graph", C.c_int32), ("autotune", C.c_int32), ("coop_krylov", C.c_int32),
+                ("krylov_tol", C.c_double), ("exp_dt_global", C.c_int32), ("jac_freeze", C.c_int32),
+                ("quad_extra", C.c_int32), ("omega", C.c_double * 3)]
 
 
 class CycleInfoC(C.Structure):
@@ -71,6 +73,9 @@ EXPORTS = {
     "emg_exp1_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.POINTER(C.c_int32), C.c_int32]),
     "emg_element_geometry": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "emg_block_operator": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_void_p,
+                                     C.c_int32]),
+    "emg_probe_peaks": (C.c_int, [C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "emg_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "emg_profile_read": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "emg_profile_class_name": (C.c_char_p, [C.c_int32]),
@@ -150,7 +155,7 @@ def mesh_desc(mesh):
 
 def make_params(p_max=2, mach=0.3, alpha_deg=0.0, gamma=1.4, rk_stages=4, krylov_m=30, cfl_max=100.0,
                 exp_dt_factor=0.0, pre_smooth=2, prec=0, stream=None, lag_blocks=0, use_graph=1, autotune=1,
-                coop_krylov=1):
+                coop_krylov=1, krylov_tol=0.0, exp_dt_global=0, jac_freeze=1, quad_extra=2, omega=(0.0, 0.0, 0.0)):
     prm = ParamsC()
     load().emg_default_params(C.byref(prm))
     prm.gamma, prm.mach, prm.alpha_deg = gamma, mach, alpha_deg
@@ -161,6 +166,12 @@ def make_params(p_max=2, mach=0.3, alpha_deg=0.0, gamma=1.4, rk_stages=4, krylov
     prm.use_graph = int(use_graph)
     prm.autotune = int(autotune)
     prm.coop_krylov = int(coop_krylov)
+    prm.krylov_tol = float(krylov_tol)
+    prm.exp_dt_global = int(exp_dt_global)
+    prm.jac_freeze = int(jac_freeze)
+    prm.quad_extra = int(quad_extra)
+    for k in range(3):
+        prm.omega[k] = float(omega[k])
     return prm
 
 
@@ -178,18 +189,14 @@ def estimate_device_bytes(mesh, **params):
 class Solver:
     """One eMG context (device-resident mesh, basis tables, state and work arrays)."""
 
-    def __init__(self, mesh, p_max=2, mach=0.3, alpha_deg=0.0, gamma=1.4, rk_stages=4, krylov_m=30,
-                 cfl_max=100.0, exp_dt_factor=0.0, pre_smooth=2, prec=0, stream=None, lag_blocks=0,
-                 use_graph=1, autotune=1, coop_krylov=1):
+    def __init__(self, mesh, p_max=2, **params):
         self.lib = load()
         self.dim = int(mesh.dim)
         self.E = int(mesh.n_elems)
         self.p_max = int(p_max)
+        self.prec = int(params.get("prec", 0))
         d, self._keep = mesh_desc(mesh)
-        prm = make_params(p_max=p_max, mach=mach, alpha_deg=alpha_deg, gamma=gamma, rk_stages=rk_stages,
-                          krylov_m=krylov_m, cfl_max=cfl_max, exp_dt_factor=exp_dt_factor,
-                          pre_smooth=pre_smooth, prec=prec, stream=stream, lag_blocks=lag_blocks,
-                          use_graph=use_graph, autotune=autotune, coop_krylov=coop_krylov)
+        prm = make_params(p_max=p_max, **params)
         h = C.c_void_p()
         st = self.lib.emg_create_mesh(C.byref(d), C.byref(prm), C.byref(h))
         self.h = h
@@ -288,6 +295,20 @@ class Solver:
         out = np.empty_like(u)
         tp = _ptr(np.ascontiguousarray(tau, dtype=np.float64))[0] if tau is not None else None
         self._check(self.lib.emg_prk_step(self.h, p, _ptr(u)[0], tp, float(cfl), _ptr(out)[0], 0))
+        return out
+
+    def block_operator(self, p, u, cfl=1.0, which=0, out=None):
+        """P_e (which = 0) or the float32 explicit P_e^{-1} (which = 1) of level p at state u,
+        as [E][5N][5N] float64 row-major (emg_block_operator)."""
+        u = np.ascontiguousarray(u, dtype=np.float64) if isinstance(u, np.ndarray) else u
+        b = 5 * self.n_modes(p)
+        if out is None:
+            out = np.empty((self.E, b, b))
+        pu, du = _ptr(u)
+        po, do = _ptr(out)
+        if du != do:
+            raise ValueError("u and out must both be host or both be device")
+        self._check(self.lib.emg_block_operator(self.h, int(p), pu, float(cfl), int(which), po, du))
         return out
 
     def jacobian_p0(self, u0):
@@ -434,6 +455,16 @@ def exp1_step_noalloc(dim, diag, off, nbr, r0, dt, u0, u_out, krylov_m=30, strea
     if st != 0:
         raise EmgError(st, "emg_exp1_step_noalloc")
     return k.value
+
+
+def probe_peaks():
+    """Measured float64 / float32 FMA throughput of the current device (TFLOP/s) and the SM
+    clock of the run (MHz), from the library's register-only probe kernels."""
+    f64, f32, mhz = C.c_double(), C.c_double(), C.c_double()
+    st = load().emg_probe_peaks(C.byref(f64), C.byref(f32), C.byref(mhz))
+    if st != 0:
+        raise EmgError(st, "emg_probe_peaks")
+    return dict(fp64_tflops=f64.value, fp32_tflops=f32.value, sm_mhz=mhz.value)
 
 
 def build_info():

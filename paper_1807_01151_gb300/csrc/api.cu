@@ -70,6 +70,18 @@ __global__ void k_set_freestream(int64_t E, int N, const double* __restrict__ vo
     v[idx] = i == 0 ? U[a] * sqrt(vol[e]) : 0.0;
 }
 
+// float32 blocks widened to float64 row-major (colmajor: the source is column-major)
+__global__ void k_widen_blocks(int64_t E, int B, const float* __restrict__ src, int colmajor,
+                               double* __restrict__ dst) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t BB = (int64_t)B * B;
+    if (t >= E * BB) return;
+    const int64_t e = t / BB;
+    const int rc = (int)(t % BB);
+    const int r = rc / B, cc = rc % B;
+    dst[t] = (double)src[e * BB + (colmajor ? (int64_t)cc * B + r : (int64_t)r * B + cc)];
+}
+
 __global__ void k_set_cfl(DevScalars* sc, double cfl) { sc->cfl = cfl; }
 __global__ void k_set_ref(DevScalars* sc, double ref) { sc->res_ref = ref; }
 __global__ void k_set_cycle(DevScalars* sc, long long n) { sc->cycle = n; }
@@ -82,7 +94,7 @@ static emg_status prk_step(emg_ctx* c, int p, const double* tau, const double* r
     LevelDev& L = c->lv[p];
     const int64_t S = c->E * L.B;
     EMG_CUDA_TRY(c, cudaMemcpyAsync(L.un, L.v, S * 8, cudaMemcpyDeviceToDevice, c->stream));
-    const bool f32 = c->prm.prec == EMG_PREC_FP32_BLOCKS;
+    const bool f32 = blocks_f32(c->prm.prec);
     emg_status st = EMG_OK;
     if (!reuse_blocks) {
         st = f32 ? launch_diag_blocks32(c, p, L.un, &c->sc->cfl, 1, L.blk32)
@@ -123,6 +135,10 @@ emg_status vcycle_body_down(emg_ctx* c) {
     const double fac = c->prm.exp_dt_factor > 0.0 ? c->prm.exp_dt_factor : (double)(P + 1);
     emg_status st = launch_dtau(c, P, c->lv[P].v, &c->sc->cfl, fac, c->dt);
     if (st != EMG_OK) return st;
+    if (c->prm.exp_dt_global) {
+        st = launch_dt_global(c, c->dt);
+        if (st != EMG_OK) return st;
+    }
     for (int p = P; p >= 1; --p) {
         LevelDev& L = c->lv[p];
         LevelDev& Lc = c->lv[p - 1];
@@ -140,7 +156,7 @@ emg_status vcycle_body_down(emg_ctx* c) {
                     rfirst = L.r;
                 }
             }
-            st = prk_step(c, p, tau, rfirst, c->prm.lag_blocks != 0 && sm > 0);
+            st = prk_step(c, p, tau, rfirst, c->frozen || (c->prm.lag_blocks != 0 && sm > 0));
             if (st != EMG_OK) return st;
         }
         // restriction of the smoothed state and of its residual, FAS forcing of level p-1
@@ -207,21 +223,42 @@ static emg_status capture(emg_ctx* c, emg_status (*part)(emg_ctx*), cudaGraphExe
 // sequence has no data-dependent branch: every decision of the cycle is on the device).
 // The split sits before the cooperative Arnoldi kernel, whose replay is ordered with the
 // cooperative launches of other contexts.
-emg_status run_body(emg_ctx* c) {
+// With jac_freeze = k > 1, cycles n with (n - 1) mod k != 0 reuse the block factors of every
+// level (once factors from a V-cycle exist), through a second captured down leg.
+static emg_status run_body_impl(emg_ctx* c) {
     if (!c->prm.use_graph || c->graph_failed || c->prof.on) return vcycle_body(c);
     if (!c->body_exec || !c->krylov_exec) {
         int64_t k1 = 0, k2 = 0;
+        const bool fz = c->frozen;
+        c->frozen = false;
         if (capture(c, vcycle_body_down, &c->body_exec, &k1) != EMG_OK ||
             capture(c, vcycle_body_up, &c->krylov_exec, &k2) != EMG_OK) {
             if (c->body_exec) cudaGraphExecDestroy(c->body_exec);
             if (c->krylov_exec) cudaGraphExecDestroy(c->krylov_exec);
             c->body_exec = c->krylov_exec = nullptr;
             c->graph_failed = true;   // run kernel by kernel from now on (same kernels)
+            c->frozen = fz;
             return vcycle_body(c);
         }
+        c->frozen = fz;
         c->body_kernels = k1 + k2;
+        c->up_kernels = k2;
     }
-    EMG_CUDA_TRY(c, cudaGraphLaunch(c->body_exec, c->stream));
+    cudaGraphExec_t down = c->body_exec;
+    int64_t nk = c->body_kernels;
+    if (c->frozen) {
+        if (!c->body_exec_frozen) {
+            int64_t k1 = 0;
+            if (capture(c, vcycle_body_down, &c->body_exec_frozen, &k1) != EMG_OK) {
+                c->body_exec_frozen = nullptr;
+                return vcycle_body(c);
+            }
+            c->body_kernels_frozen = k1;
+        }
+        down = c->body_exec_frozen;
+        nk = c->body_kernels_frozen + c->up_kernels;
+    }
+    EMG_CUDA_TRY(c, cudaGraphLaunch(down, c->stream));
     cudaGraphExec_t kx = c->krylov_exec;
     if (c->prm.coop_krylov) {
         emg_status st = coop_ordered(c->device, c->stream, [kx, c]() { return cudaGraphLaunch(kx, c->stream); }, &c->err);
@@ -229,8 +266,17 @@ emg_status run_body(emg_ctx* c) {
     } else {
         EMG_CUDA_TRY(c, cudaGraphLaunch(kx, c->stream));
     }
-    c->launches += c->body_kernels;
+    c->launches += nk;
     return EMG_OK;
+}
+
+emg_status run_body(emg_ctx* c) {
+    const int k = c->prm.jac_freeze;
+    c->frozen = k > 1 && c->blocks_valid && ((c->cycle_n - 1) % k) != 0;
+    const emg_status st = run_body_impl(c);
+    if (st == EMG_OK && !c->frozen) c->blocks_valid = true;
+    c->frozen = false;
+    return st;
 }
 
 // Page-locked host slots for the per-context device scalars, taken from chunks that live
@@ -302,6 +348,11 @@ void emg_default_params(emg_params* p) {
     p->use_graph = 1;
     p->autotune = 1;
     p->coop_krylov = 1;
+    p->krylov_tol = 0.0;
+    p->exp_dt_global = 0;
+    p->jac_freeze = 1;
+    p->quad_extra = 2;
+    p->omega[0] = p->omega[1] = p->omega[2] = 0.0;
 }
 
 const char* emg_build_info(void) {
@@ -329,9 +380,17 @@ emg_status emg_create_mesh(const emg_mesh_desc* m, const emg_params* prm, emg_ct
     if (!(prm->cfl_max > 0.0)) return fail(c, EMG_ERR_ARG, "cfl_max must be positive");
     if (prm->pre_smooth < 1) return fail(c, EMG_ERR_ARG, "pre_smooth must be >= 1");
     if (!(prm->gamma > 1.0) || !(prm->mach >= 0.0)) return fail(c, EMG_ERR_ARG, "bad gamma or mach");
-    if (prm->prec != EMG_PREC_FP64 && prm->prec != EMG_PREC_FP32_BLOCKS)
-        return fail(c, EMG_ERR_ARG, "prec must be EMG_PREC_FP64 or EMG_PREC_FP32_BLOCKS");
+    if (prm->prec != EMG_PREC_FP64 && prm->prec != EMG_PREC_FP32_BLOCKS && prm->prec != EMG_PREC_BF16_BLOCKS)
+        return fail(c, EMG_ERR_ARG, "prec must be EMG_PREC_FP64, EMG_PREC_FP32_BLOCKS or EMG_PREC_BF16_BLOCKS");
+    if (!(prm->krylov_tol >= 0.0)) return fail(c, EMG_ERR_ARG, "krylov_tol must be >= 0");
+    if (prm->exp_dt_global != 0 && prm->exp_dt_global != 1) return fail(c, EMG_ERR_ARG, "exp_dt_global must be 0 or 1");
+    if (prm->jac_freeze < 0) return fail(c, EMG_ERR_ARG, "jac_freeze must be >= 1");
+    if (prm->quad_extra != 0 && prm->quad_extra != 2)
+        return fail(c, EMG_ERR_ARG, "only the rule q = p + 2 is built (quad_extra 2)");
+    if (prm->omega[0] != 0.0 || prm->omega[1] != 0.0 || prm->omega[2] != 0.0)
+        return fail(c, EMG_ERR_ARG, "only the absolute frame (omega = 0) is built");
     c->p_max = prm->p_max;
+    if (c->prm.jac_freeze < 1) c->prm.jac_freeze = 1;
     EMG_CUDA_TRY(c, cudaGetDevice(&c->device));
     if (prm->cuda_stream) {
         c->stream = (cudaStream_t)prm->cuda_stream;
@@ -355,6 +414,7 @@ emg_status emg_create_mesh(const emg_mesh_desc* m, const emg_params* prm, emg_ct
 emg_status emg_destroy(emg_ctx* c) {
     if (!c) return EMG_OK;
     if (c->body_exec) cudaGraphExecDestroy(c->body_exec);
+    if (c->body_exec_frozen) cudaGraphExecDestroy(c->body_exec_frozen);
     if (c->krylov_exec) cudaGraphExecDestroy(c->krylov_exec);
     for (void* p : c->allocs) cudaFreeAsync(p, c->stream);
     if (c->stage_out) cudaFreeAsync(c->stage_out, c->stream);
@@ -392,6 +452,7 @@ emg_status emg_set_state(emg_ctx* c, const double* U, int32_t on_device) {
     if (c->sc_host->nonfinite) return fail(c, EMG_ERR_NONFINITE, "state contains NaN or Inf");
     c->cycle_n = 1;
     c->res_ref = 0.0;
+    c->blocks_valid = false;
     return EMG_OK;
 }
 
@@ -536,9 +597,48 @@ emg_status emg_prk_step(emg_ctx* c, int32_t p, const double* u, const double* ta
     }
     { ProfScope _ps(c, PC_CONTROL); k_set_cfl<<<1, 1, 0, c->stream>>>(c->sc, cfl); }
     EMG_CHECK_LAUNCH(c);
+    c->blocks_valid = false;   // the level's stored factors are replaced
     st = prk_step(c, p, tau ? L.tau : nullptr, nullptr);
     if (st != EMG_OK) return st;
     return copy_out(c, u_out, L.v, n, on_device);
+}
+
+emg_status emg_block_operator(emg_ctx* c, int32_t p, const double* u, double cfl, int32_t which, double* out,
+                              int32_t on_device) {
+    if (!c || !u || !out || p < 1 || p > c->p_max || !(cfl > 0.0) || (which != 0 && which != 1)) return EMG_ERR_ARG;
+    const bool f32 = blocks_f32(c->prm.prec);
+    if (which == 1 && !f32) return fail(c, EMG_ERR_ARG, "the FP64 form keeps LU factors, not an explicit inverse");
+    LevelDev& L = c->lv[p];
+    const int B = L.B;
+    const int64_t n = c->E * B;
+    emg_status st = copy_in(c, L.un, u, n, on_device);
+    if (st != EMG_OK) return st;
+    { ProfScope _ps(c, PC_CONTROL); k_set_cfl<<<1, 1, 0, c->stream>>>(c->sc, cfl); }
+    EMG_CHECK_LAUNCH(c);
+    c->blocks_valid = false;   // the level's stored factors are replaced
+    double* Dd = out;
+    if (!on_device) {
+        st = stage_out(c, n * B, &Dd);
+        if (st != EMG_OK) return st;
+    }
+    if (f32) {
+        st = launch_diag_blocks32(c, p, L.un, &c->sc->cfl, 1, L.blk32);
+        if (st != EMG_OK) return st;
+        if (which == 1) {
+            st = launch_lu32(c, p);
+            if (st != EMG_OK) return st;
+        }
+        const int64_t tot = n * B;
+        { ProfScope _ps(c, PC_CONTROL); k_widen_blocks<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(
+            c->E, B, L.blk32, which, Dd); }
+        EMG_CHECK_LAUNCH(c);
+    } else {
+        st = launch_diag_blocks(c, p, L.un, &c->sc->cfl, 1, L.blk);
+        if (st != EMG_OK) return st;
+        EMG_CUDA_TRY(c, cudaMemcpyAsync(Dd, L.blk, (size_t)n * B * 8, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (!on_device) return copy_out(c, out, Dd, n * B, 0);
+    return EMG_OK;
 }
 
 emg_status emg_jacobian_p0(emg_ctx* c, const double* u0, double* diag, double* off, int64_t* nbr, int32_t on_device) {

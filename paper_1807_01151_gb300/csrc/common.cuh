@@ -19,6 +19,10 @@ constexpr int NVAR = 5;
 constexpr int MAX_P = 4;
 constexpr int MAX_KRYLOV = 64;
 
+// The float32 block forms (FP32 and BF16 blocks) share the float tables, the explicit
+// inverse and the stage GEMV.
+inline bool blocks_f32(int prec) { return prec == EMG_PREC_FP32_BLOCKS || prec == EMG_PREC_BF16_BLOCKS; }
+
 __host__ __device__ constexpr int n_modes(int D, int P) {
     return D == 2 ? (P + 1) * (P + 2) / 2 : (P + 1) * (P + 2) * (P + 3) / 6;
 }
@@ -87,6 +91,7 @@ struct DevScalars {
     int nonfinite;       // non-finite residual seen
     int pad;             // non-positive density or pressure seen
     int timeout;         // a bounded device-side wait gave up
+    int bad_index;       // an input index out of range (no-allocation EXP1 step)
     long long cycle;     // V-cycle index n of Eq. cfl (advanced on the device by every cycle body)
 };
 
@@ -162,6 +167,11 @@ struct emg_ctx {
     emg::Prof prof;
     int64_t launches = 0;            // kernels launched by this context
     cudaGraphExec_t body_exec = nullptr;  // captured V-cycle body up to the Arnoldi kernel
+    cudaGraphExec_t body_exec_frozen = nullptr;  // the same with the block factors reused (jac_freeze)
+    int64_t body_kernels_frozen = 0;
+    int64_t up_kernels = 0;          // kernels of the captured part from the Arnoldi kernel on
+    bool frozen = false;             // the cycle being issued reuses the stored block factors
+    bool blocks_valid = false;       // the stored factors of every level come from a V-cycle
     cudaGraphExec_t krylov_exec = nullptr; // the rest of the body, from the Arnoldi kernel on
     int64_t body_kernels = 0;        // kernels in both
     bool capturing = false;          // a graph capture is in progress on the stream
@@ -228,6 +238,7 @@ emg_status launch_tau(emg_ctx* c, int p_coarse, const double* rfine, const doubl
 emg_status launch_prolong(emg_ctx* c, int p_fine, double* fine, const double* vc, const double* v0c);
 emg_status launch_norm_cfl(emg_ctx* c, const double* R, int update_cfl);
 emg_status launch_dtau(emg_ctx* c, int p, const double* u, const double* cfl_dev, double factor, double* dt);
+emg_status launch_dt_global(emg_ctx* c, double* dt);
 emg_status launch_axpby(emg_ctx* c, int64_t n, double a, const double* x, double b, const double* y, double* out);
 emg_status launch_check_state(emg_ctx* c, const double* u, int64_t n);
 // V-cycle pieces (api.cu), shared with the request loop (server.cu)

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(128) k_face_jac(int F, int F_int, const int* _
         for (int a = 0; a < 5; ++a)
             for (int b = 0; b < 5; ++b) fjr[idx * 25 + a * 5 + b] = am * Fd[a].d[b];
     } else {
-        if (fbc[f] == EMG_BC_WALL) {
+        if (fbc[f] == EMG_BC_WALL || fbc[f] == EMG_BC_SYMMETRY) {
             const int64_t bi = idx - (int64_t)F_int * QF;
             const double nw[3] = {fwn[bi * 3], fwn[bi * 3 + 1], fwn[bi * 3 + 2]};
             wall_ghost(dL, nw, dR);

@@ -511,17 +511,27 @@ __device__ __forceinline__ void smm(const double* A, const double* B, double* C,
     cl.sync();
 }
 
-// y = beta * [exp([[H, e1], [0, 0]])]_{0:k, k}.  A cluster of PHI_CLUSTER blocks: the dense
-// products (bound by one SM's FP64 rate on a single block) are shared out; the cheap
-// element-wise steps and the small pivoted solve are repeated in every block on its own
-// copies, so every block holds the same matrices and block 0 writes y.
+// EST = false: y = beta * [exp([[H_k, e1], [0, 0]])]_{0:k, k} with k = sc->m_used (the
+// phi_1 weights of Eq. final).
+// EST = true: the Krylov tolerance test after Arnoldi step jstep (k = jstep + 1 steps, unless the
+// process has already ended): X = exp([[H_k, e1, 0], [0, 0, 1], [0, 0, 0]]) holds phi_1(H_k)e1
+// and phi_2(H_k)e1 in its last two columns; when h_{k+1,k} |(phi_2(H_k)e1)_k| <= tol
+// ||phi_1(H_k)e1|| the process ends with k steps (sc->broken = 1).
+// A cluster of PHI_CLUSTER blocks: the dense products (bound by one SM's FP64 rate on a
+// single block) are shared out; the cheap element-wise steps and the small pivoted solve
+// are repeated in every block on its own copies, so every block holds the same matrices
+// and block 0 writes the result.
+template <bool EST>
 __global__ void __cluster_dims__(PHI_CLUSTER, 1, 1)
-    k_phi(int m, const double* __restrict__ H, double* __restrict__ y, Pade13 pc, DevScalars* sc) {
+    k_phi(int m, int jstep, double tol, const double* __restrict__ H, double* __restrict__ y, Pade13 pc,
+          DevScalars* sc) {
     extern __shared__ double sm[];
-    const int k = sc->m_used;
+    const int k = EST ? jstep + 1 : sc->m_used;
     const double beta = sc->beta;
     if (k == 0) return;
-    const int n = k + 1, ld = n;
+    // uniform over the cluster: every block reads the same flags written by earlier kernels
+    if (EST && (*((volatile int*)&sc->broken) || sc->m_used != k)) return;
+    const int n = EST ? k + 2 : k + 1, ld = n;
     const int nn = ld * n;
     double* M = sm;
     double* M2 = M + nn;
@@ -534,11 +544,12 @@ __global__ void __cluster_dims__(PHI_CLUSTER, 1, 1)
     __shared__ double s_norm;
     __shared__ int s_piv;
     for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-        const int i = t / n, j = t % n;
+        const int i = t / n, jj = t % n;
         double v = 0.0;
-        if (i < k && j < k) v = H[(size_t)i * m + j];
-        if (i == 0 && j == k) v = 1.0;
-        M[i * ld + j] = v;
+        if (i < k && jj < k) v = H[(size_t)i * m + jj];
+        if (i == 0 && jj == k) v = 1.0;
+        if (EST && i == k && jj == k + 1) v = 1.0;
+        M[i * ld + jj] = v;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -650,8 +661,18 @@ __global__ void __cluster_dims__(PHI_CLUSTER, 1, 1)
         X = Y;
         Y = t;
     }
-    if (cg::this_cluster().block_rank() == 0)
-        for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = beta * X[i * ld + k];
+    if (cg::this_cluster().block_rank() == 0) {
+        if (EST) {
+            if (threadIdx.x == 0) {
+                double nrm = 0.0;
+                for (int i = 0; i < k; ++i) nrm += X[i * ld + k] * X[i * ld + k];
+                const double err = H[(size_t)k * m + (k - 1)] * fabs(X[(k - 1) * ld + k + 1]);
+                if (err <= tol * sqrt(nrm)) sc->broken = 1;
+            }
+        } else {
+            for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = beta * X[i * ld + k];
+        }
+    }
 }
 
 // out = u0 + V[0:k]^T y  (out = u0 when the start vector was zero)
@@ -744,16 +765,25 @@ emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, do
     double* Vv = c->V;
     double* ww = c->w;
     double* HH = c->H;
-    if (!c->prm.coop_krylov) {
-        // barrier-free form (same blocks, same arithmetic): 2 + 3m plain launches
+    const double tol = c->prm.krylov_tol;
+    if (!c->prm.coop_krylov || tol > 0.0) {
+        // barrier-free form (same blocks, same arithmetic): 2 + 3m plain launches; with a
+        // Krylov tolerance, the test of each step follows it (it may end the process)
         ArnArgs A{K0, 2 * c->dim, m, stride, bsr, nbr, dt, rr, Vv, ww, HH, c->hcol, partA, partB, partC, c->sc};
         const unsigned g = (unsigned)nb;
+        const size_t smem_est = (size_t)8 * (m + 2) * (m + 2) * sizeof(double);
+        if (tol > 0.0)
+            EMG_CUDA_TRY(c, cudaFuncSetAttribute(k_phi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_est));
         { ProfScope _ps(c, PC_ARNOLDI); k_arn_start<<<g, ARN_THREADS, 0, c->stream>>>(A); }
         { ProfScope _ps(c, PC_ARNOLDI); k_arn_init<<<g, ARN_THREADS, 0, c->stream>>>(A); }
         for (int j = 0; j < m; ++j) {
             { ProfScope _ps(c, PC_ARNOLDI); k_arn_pass2<<<g, ARN_THREADS, 0, c->stream>>>(A, j); }
             { ProfScope _ps(c, PC_ARNOLDI); k_arn_pass3<<<g, ARN_THREADS, 0, c->stream>>>(A, j); }
             { ProfScope _ps(c, PC_ARNOLDI); k_arn_pass4<<<g, ARN_THREADS, 0, c->stream>>>(A, j); }
+            if (tol > 0.0 && j + 1 < m) {
+                ProfScope _ps(c, PC_PHI);
+                k_phi<true><<<PHI_CLUSTER, 256, smem_est, c->stream>>>(m, j, tol, c->H, c->y, pade13(), c->sc);
+            }
         }
         EMG_CHECK_LAUNCH(c);
     } else {
@@ -777,10 +807,10 @@ emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, do
     }
     const int n = m + 1;
     const size_t smem = (size_t)8 * n * n * sizeof(double);
-    EMG_CUDA_TRY(c, cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    EMG_CUDA_TRY(c, cudaFuncSetAttribute(k_phi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
         ProfScope _ps(c, PC_PHI);
-        k_phi<<<PHI_CLUSTER, 256, smem, c->stream>>>(m, c->H, c->y, pade13(), c->sc);
+        k_phi<false><<<PHI_CLUSTER, 256, smem, c->stream>>>(m, 0, 0.0, c->H, c->y, pade13(), c->sc);
     }
     EMG_CHECK_LAUNCH(c);
     {
@@ -793,9 +823,9 @@ emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, do
 }
 
 // ---- EXP1 step without any allocation --------------------------------------------------------
-// For callers that must not allocate device memory once they are running (for example a
-// host application whose memory is handed out by its own pool, or code that issues work
-// while a stream is being captured): the Krylov basis, the packed block rows, the
+// For callers that must not allocate device memory once they are running (an application
+// whose memory is handed out by its own pool, or a loop that may not take the device-wide
+// synchronisation of cudaMalloc/cudaFree): the Krylov basis, the packed block rows, the
 // reduction partials, the Hessenberg matrix and the barrier live in one file-scope device
 // array of fixed size, so the call itself allocates nothing.
 constexpr int64_t NA_MAX_ELEMS = 8192;
@@ -819,18 +849,29 @@ constexpr size_t NA_DOUBLES = NA_OFF_BAR + 8;   // about 26 MB
 static __device__ __align__(256) double g_exp1_scratch[NA_DOUBLES];
 static_assert(sizeof(DevScalars) <= 16 * sizeof(double), "scalars do not fit their slot");
 
-// Device address of g_exp1_scratch for each device, taken once with that device current.
+// Device address of g_exp1_scratch for each device, looked up once per device (std::call_once,
+// so concurrent first calls from several host threads are safe) with that device current.
 static double* g_exp1_scratch_addr[64] = {};
+static cudaError_t g_exp1_scratch_err[64] = {};
+static std::once_flag g_exp1_scratch_once[64];
 
+// Packs the block rows and narrows the neighbour table.  A neighbour index outside
+// [-1, E) is replaced by -1 (so nothing out of range is ever read) and flagged.
 __global__ void k_pack_bsr(int64_t E, int NF, const double* __restrict__ diag, const double* __restrict__ off,
-                           const int64_t* __restrict__ nbr, double* __restrict__ bsr, int* __restrict__ nbr32) {
+                           const int64_t* __restrict__ nbr, double* __restrict__ bsr, int* __restrict__ nbr32,
+                           DevScalars* sc) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= E * (1 + NF) * 25) return;
     const int64_t e = idx / ((1 + NF) * 25);
     const int r = (int)(idx % ((1 + NF) * 25));
     const int blk = r / 25, t = r % 25;
     bsr[idx] = blk == 0 ? diag[e * 25 + t] : off[(e * NF + blk - 1) * 25 + t];
-    if (r < NF) nbr32[e * NF + r] = (int)nbr[e * NF + r];
+    if (r < NF) {
+        const int64_t nb = nbr[e * NF + r];
+        const bool ok = nb >= -1 && nb < E;
+        nbr32[e * NF + r] = ok ? (int)nb : -1;
+        if (!ok) sc->bad_index = 1;
+    }
 }
 
 }  // namespace emg
@@ -845,11 +886,13 @@ extern "C" emg_status emg_exp1_step_noalloc(int32_t dim, int64_t n_elems, const 
         return EMG_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return EMG_ERR_CUDA;
-    if (!g_exp1_scratch_addr[dev]) {
+    std::call_once(g_exp1_scratch_once[dev], [dev]() {
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_exp1_scratch) != cudaSuccess || !p) return EMG_ERR_CUDA;
+        g_exp1_scratch_err[dev] = cudaGetSymbolAddress(&p, g_exp1_scratch);
+        if (g_exp1_scratch_err[dev] == cudaSuccess && !p) g_exp1_scratch_err[dev] = cudaErrorInvalidSymbol;
         g_exp1_scratch_addr[dev] = static_cast<double*>(p);
-    }
+    });
+    if (g_exp1_scratch_err[dev] != cudaSuccess) return EMG_ERR_CUDA;
     double* S = g_exp1_scratch_addr[dev];
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int NF = 2 * dim;
@@ -869,8 +912,16 @@ extern "C" emg_status emg_exp1_step_noalloc(int32_t dim, int64_t n_elems, const 
     if (cudaMemsetAsync(sc, 0, sizeof(DevScalars), st) != cudaSuccess) return EMG_ERR_CUDA;
     if (cudaMemsetAsync(bar, 0, sizeof(GridBar), st) != cudaSuccess) return EMG_ERR_CUDA;
     const int64_t npack = E * (1 + NF) * 25;
-    k_pack_bsr<<<(unsigned)((npack + 255) / 256), 256, 0, st>>>(E, NF, diag, off, nbr, bsr, nbr32);
+    k_pack_bsr<<<(unsigned)((npack + 255) / 256), 256, 0, st>>>(E, NF, diag, off, nbr, bsr, nbr32, sc);
     if (cudaGetLastError() != cudaSuccess) return EMG_ERR_CUDA;
+    {
+        // the neighbour table is checked before anything reads through it
+        int bad = 0;
+        if (cudaMemcpyAsync(&bad, &sc->bad_index, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return EMG_ERR_CUDA;
+        if (bad) return EMG_ERR_ARG;
+    }
     int per_sm = 0, nsm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi, ARN_THREADS, 0) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -889,9 +940,9 @@ extern "C" emg_status emg_exp1_step_noalloc(int32_t dim, int64_t n_elems, const 
     if (coop_ordered(dev, st, launch, nullptr) != EMG_OK) return EMG_ERR_CUDA;
     const int n = krylov_m + 1;
     const size_t smem = (size_t)8 * n * n * sizeof(double);
-    if (cudaFuncSetAttribute(k_phi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_phi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return EMG_ERR_CUDA;
-    k_phi<<<PHI_CLUSTER, 256, smem, st>>>(krylov_m, H, y, pade13(), sc);
+    k_phi<false><<<PHI_CLUSTER, 256, smem, st>>>(krylov_m, 0, 0.0, H, y, pade13(), sc);
     k_combine<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(296, (K0 + 255) / 256)), 256, 0, st>>>(
         K0, u0, V, y, sc, u_out);
     if (cudaGetLastError() != cudaSuccess) return EMG_ERR_CUDA;

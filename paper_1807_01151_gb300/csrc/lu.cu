@@ -734,7 +734,7 @@ std::map<std::pair<int, int>, int> g_gj_best;   // (device, B) -> variant
 // Times every valid variant on min(E, 2048) stand-in blocks per block size of the FP32 levels
 // and keeps the fastest, once per (device, B) for the process.
 emg_status tune_gj(emg_ctx* c) {
-    if (c->prm.prec != EMG_PREC_FP32_BLOCKS) return EMG_OK;
+    if (!blocks_f32(c->prm.prec)) return EMG_OK;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (int p = 1; p <= c->p_max; ++p) {
         LevelDev& L = c->lv[p];

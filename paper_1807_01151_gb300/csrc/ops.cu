@@ -108,6 +108,31 @@ __global__ void k_dtau(int64_t E, int N, int nmax, const double* __restrict__ u,
     dt[e] = factor * cfl_dev[0] * h[e] / ((2 * p + 1) * (sqrt(q2) + c));
 }
 
+// dt_e <- min_e dt_e for every element (one block; the minimum does not depend on the
+// order of the comparisons).  A NaN step stays NaN.
+__global__ void k_dt_global(int64_t E, double* __restrict__ dt) {
+    __shared__ double sh[32];
+    double m = INFINITY;
+    bool nan = false;
+    for (int64_t e = threadIdx.x; e < E; e += blockDim.x) {
+        const double v = dt[e];
+        nan |= isnan(v);
+        m = fmin(m, v);
+    }
+    nan = __syncthreads_or(nan);
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double x = threadIdx.x < blockDim.x / 32 ? sh[threadIdx.x] : INFINITY;
+        for (int o = 16; o > 0; o >>= 1) x = fmin(x, __shfl_xor_sync(0xffffffffu, x, o));
+        if (threadIdx.x == 0) sh[0] = nan ? NAN : x;
+    }
+    __syncthreads();
+    const double g = sh[0];
+    for (int64_t e = threadIdx.x; e < E; e += blockDim.x) dt[e] = g;
+}
+
 __global__ void k_check_finite(int64_t n, const double* __restrict__ u, DevScalars* sc) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < n && !isfinite(u[idx])) sc->nonfinite = 1;
@@ -159,6 +184,12 @@ emg_status launch_dtau(emg_ctx* c, int p, const double* u, const double* cfl_dev
     const int nmax = n_modes(c->dim, c->p_max);
     { ProfScope _ps(c, PC_CONTROL); k_dtau<<<blocks_for(c->E, 128), 128, 0, c->stream>>>(c->E, c->lv[p].N, nmax, u, c->psic, c->h, cfl_dev, p, factor,
                                                          c->prm.gamma, dt, c->sc); }
+    EMG_CHECK_LAUNCH(c);
+    return EMG_OK;
+}
+
+emg_status launch_dt_global(emg_ctx* c, double* dt) {
+    { ProfScope _ps(c, PC_CONTROL); k_dt_global<<<1, 1024, 0, c->stream>>>(c->E, dt); }
     EMG_CHECK_LAUNCH(c);
     return EMG_OK;
 }

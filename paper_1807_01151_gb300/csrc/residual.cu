@@ -47,12 +47,12 @@ __global__ void __launch_bounds__(128) k_face_flux(int F, int F_int, const int* 
             for (int i = 0; i < N; ++i) s += ur[a * N + i] * pr[i];
             UR[a] = s;
         }
-    } else if (fbc[f] == EMG_BC_WALL) {
-        {
+    } else if (fbc[f] == EMG_BC_WALL || fbc[f] == EMG_BC_SYMMETRY) {
+        // mirror ghost about the reflection normal (body normal on walls, face normal on
+        // symmetry planes)
         const int64_t bi = idx - (int64_t)F_int * QF;
         const double nw[3] = {fwn[bi * 3], fwn[bi * 3 + 1], fwn[bi * 3 + 2]};
         wall_ghost(UL, nw, UR);
-    }
     } else {
         farfield_ghost(UL, n, uinf.v, g, UR);
     }

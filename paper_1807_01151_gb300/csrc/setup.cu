@@ -270,7 +270,8 @@ __global__ void k_face_tables(int F, int F_int, int n, int nmax, int q, const in
                               const double* __restrict__ gl, const double* __restrict__ xc,
                               const double* __restrict__ Lh, const int* __restrict__ exps,
                               const double* __restrict__ C, const double* __restrict__ ewn, int has_wn,
-                              double* fnrm, double* famag, double* fpsiL, double* fpsiR, double* fwn) {
+                              const int* __restrict__ fbc, double* fnrm, double* famag, double* fpsiL,
+                              double* fpsiR, double* fwn) {
     int QF = 1;
     for (int d = 0; d < D - 1; ++d) QF *= q;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -289,9 +290,10 @@ __global__ void k_face_tables(int F, int F_int, int n, int nmax, int q, const in
     for (int k = 0; k < 3; ++k) fnrm[idx * 3 + k] = a[k] / am;
     if (f >= F_int) {
         // reflection normal of the slip wall: node body normals interpolated with the
-        // multilinear shape functions at this face point and normalised
+        // multilinear shape functions at this face point and normalised; a symmetry plane
+        // reflects about its own (flat) normal
         double nw[3] = {a[0] / am, a[1] / am, a[2] / am};
-        if (has_wn) {
+        if (has_wn && fbc[f] == EMG_BC_WALL) {
             double v[3] = {0.0, 0.0, 0.0};
             const double* Wn = ewn + (size_t)eL * (1 << D) * D;
             for (int nd = 0; nd < (1 << D); ++nd) {
@@ -391,7 +393,7 @@ static emg_status build_tables(emg_ctx* c, int nmax, const int* exps_d) {
         int64_t nf = c->F * L.QF;
         { ProfScope _ps(c, PC_SETUP); k_face_tables<D, NM><<<(unsigned)((nf + thr - 1) / thr), thr, 0, c->stream>>>(
             (int)c->F, (int)c->F_int, L.N, nmax, L.q, c->face_L, c->face_fL, c->face_R, c->elem_x, c->gl, c->xc,
-            c->Lh, exps_d, c->C, c->elem_wn, c->has_wn, L.fnrm, L.famag, L.fpsiL, L.fpsiR, L.fwn); }
+            c->Lh, exps_d, c->C, c->elem_wn, c->has_wn, c->face_bc, L.fnrm, L.famag, L.fpsiL, L.fpsiR, L.fwn); }
         EMG_CHECK_LAUNCH(c);
     }
     return EMG_OK;
@@ -410,7 +412,7 @@ int64_t estimate_bytes(int dim, int64_t E, int64_t F, int64_t F_int, int p_max, 
         b += F * QF * (3 + 1 + N + 5 + 25) * 8 + Fi1 * QF * (N + 25) * 8 + Fb1 * QF * 3 * 8;
         b += 6 * E * B * 8;                                                     // v, v0, tau, un, r, r2
         if (p > 0) {
-            if (prec == EMG_PREC_FP32_BLOCKS)
+            if (blocks_f32(prec))
                 b += E * B * B * 4 + E * Q * N * (1 + dim) * 4 + F * QF * (N + 25) * 4 + Fi1 * QF * (N + 25) * 4;
             else
                 b += E * B * B * 8;
@@ -436,7 +438,7 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
         for (int f = 0; f < nf; ++f) {
             const int bc = m->face_bc[e * nf + f];
             if (bc >= 0) {
-                if (bc != EMG_BC_WALL && bc != EMG_BC_FARFIELD) {
+                if (bc != EMG_BC_WALL && bc != EMG_BC_FARFIELD && bc != EMG_BC_SYMMETRY) {
                     c->err = "unsupported boundary code " + std::to_string(bc);
                     return EMG_ERR_ARG;
                 }
@@ -583,7 +585,7 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
         EMG_ALLOC(L.fjl, double, F * L.QF * 25);
         EMG_ALLOC(L.fjr, double, std::max<int64_t>(F_int, 1) * L.QF * 25);
         if (p > 0) {
-            if (c->prm.prec == EMG_PREC_FP32_BLOCKS) {
+            if (blocks_f32(c->prm.prec)) {
                 EMG_ALLOC(L.blk32, float, E * L.B * L.B);
                 EMG_ALLOC(L.vpsi32, float, E * L.Q * L.N);
                 EMG_ALLOC(L.vgw32, float, E * D * L.Q * L.N);
@@ -650,7 +652,7 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
         st = build_tables<3, 35>(c, nmax, exps_d);
     }
     if (st != EMG_OK) return st;
-    if (c->prm.prec == EMG_PREC_FP32_BLOCKS) {
+    if (blocks_f32(c->prm.prec)) {
         st = build_float_tables(c);
         if (st != EMG_OK) return st;
         st = tune_gj(c);

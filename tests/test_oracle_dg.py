@@ -5,7 +5,7 @@ import pytest
 from oracle import euler
 from oracle.dg import DG
 from tests.helpers import perturbed_state
-from workloads import BC_EXACT, BC_FARFIELD, BC_WALL, box, cubed_sphere_shell, ogrid
+from workloads import BC_EXACT, BC_FARFIELD, BC_SYMMETRY, BC_WALL, box, cubed_sphere_shell, ogrid
 
 
 @pytest.mark.parametrize("desc,p", [(ogrid(8, 3, inner_bc=BC_FARFIELD), 3),
@@ -205,3 +205,49 @@ def test_jvp_and_blocks_against_finite_differences_3d():
             du[e, a, j] = 1.0
             fdc = (dg.residual(p, up + eps * du) - dg.residual(p, up - eps * du))[e].ravel() / (2 * eps)
             assert np.abs(fdc - D[e, :, col]).max() < 1e-7 * np.abs(D[e]).max()
+
+
+def _mirror_y_state(dg, u):
+    """(u + M u)/2 for the reflection y -> -y of a mesh that is symmetric about y = 0: the
+    element map pairs mirrored centroids; the orthonormal basis of a mirrored element is the
+    mirrored basis with sign (-1)^(y exponent) per mode, and rho v changes sign."""
+    from oracle.basis import exponents
+    xc = dg.mesh.xc
+    mir = xc.copy()
+    mir[:, 1] *= -1.0
+    d = np.linalg.norm(xc[None, :, :] - mir[:, None, :], axis=-1)
+    perm = np.argmin(d, axis=1)
+    assert np.allclose(xc[perm], mir, atol=1e-12)
+    n = u.shape[2]
+    sgn_mode = (-1.0) ** exponents(dg.dim, dg.p_max)[:n, 1]
+    sgn_var = np.array([1.0, 1.0, -1.0, 1.0, 1.0])
+    Mu = u[perm] * sgn_var[None, :, None] * sgn_mode[None, None, :]
+    return 0.5 * (u + Mu)
+
+
+@pytest.mark.parametrize("mk,p", [(lambda: ogrid(8, 3), 3), (lambda: cubed_sphere_shell(2, 1), 2)])
+def test_symmetry_plane_equals_the_mirrored_full_domain(mk, p):
+    """Symmetry boundary condition (Sec. 5, sphere case): for a state symmetric about y = 0,
+    the residual of the half mesh with symmetry planes on y = 0 equals the full mesh's
+    residual restricted to the same elements (across y = 0 the Roe flux sees the mirrored
+    state, which is exactly the symmetry ghost)."""
+    from workloads import half_mesh
+    full = mk()
+    half, keep = half_mesh(full, axis=1)
+    assert (half.face_bc == BC_SYMMETRY).sum() > 0
+    dgf = DG(full, p, mach=0.3)
+    dgh = DG(half, p, mach=0.3)
+    assert np.allclose(dgh.mesh.vol, dgf.mesh.vol[keep], rtol=1e-13)
+    us = _mirror_y_state(dgf, perturbed_state(dgf, amp=0.05))
+    for lev in range(p + 1):
+        ul = us[:, :, :dgf.N(lev)]
+        Rf = dgf.residual(lev, ul)[keep]
+        Rh = dgh.residual(lev, np.ascontiguousarray(ul[keep]))
+        assert np.abs(Rh - Rf).max() <= 1e-12 * np.abs(Rf).max(), (lev, np.abs(Rh - Rf).max())
+    # the pin is not vacuous: the same faces as far-field boundaries give another residual
+    from workloads import MeshDesc
+    fb = half.face_bc.copy()
+    fb[fb == BC_SYMMETRY] = BC_FARFIELD
+    dgx = DG(MeshDesc(half.dim, half.xyz, half.elem_nodes, fb, wall_normal=half.wall_normal), p, mach=0.3)
+    Rx = dgx.residual(p, np.ascontiguousarray(us[keep]))
+    assert np.abs(Rx - dgf.residual(p, us)[keep]).max() > 1e-6 * np.abs(Rx).max()

@@ -198,3 +198,66 @@ def test_exp1_step_equals_dense_phi1_on_exhausted_krylov_space(mk):
         # the same step without the forcing differs: tau0 is really part of N
         u1b, _ = emg.exp1_step(dg, u0, np.zeros_like(u0), dt, emg.Options(krylov_m=30))
         assert np.abs((u1b - u1).ravel()).max() > 1e-6 * np.abs(ref).max()
+
+
+def test_phi12_of_augmented_matrix_equals_series():
+    """phi_1(H) e_1 and phi_2(H) e_1 from one exponential of the (k+2)-augmented matrix equal
+    their series sum_j H^j e_1 / (j+1)! and sum_j H^j e_1 / (j+2)! (Hessenberg H)."""
+    rng = np.random.default_rng(3)
+    k = 7
+    H = np.triu(rng.standard_normal((k, k)), -1) * 0.6
+    p1, p2 = emg.phi12_small(H)
+    e1 = np.zeros(k)
+    e1[0] = 1.0
+    s1, s2, t = np.zeros(k), np.zeros(k), e1.copy()
+    f = 1.0
+    for j in range(60):
+        f1 = math.factorial(j + 1)
+        s1 += t / f1
+        s2 += t / (f1 * (j + 2))
+        t = H @ t
+    assert np.allclose(p1, s1, rtol=1e-13, atol=1e-15)
+    assert np.allclose(p2, s2, rtol=1e-13, atol=1e-15)
+
+
+def test_krylov_tolerance_mode_stops_early_within_tolerance():
+    """Sec. 5 Krylov tolerance (reading C4): on a p = 0 mesh small enough for a dense
+    reference (K0 = 60 > m), the tolerance-mode step stops before m steps, its distance to
+    the exact phi_1(A) N is within a small multiple of the tolerance, and it is within the
+    tolerance of the fixed-m step."""
+    import scipy.linalg
+    dg = DG(ogrid(6, 2), 0)
+    u0 = perturbed_state(dg, amp=0.05)
+    tau0 = np.zeros_like(u0)
+    dt = emg.dtau(dg, 0, u0, 5.0)
+    J = dg.full_jacobian(0, u0)
+    DT = np.repeat(dt, 5)
+    A = DT[:, None] * J
+    Nv = DT * dg.residual(0, u0).ravel()
+    exact = np.linalg.solve(A, (scipy.linalg.expm(A) - np.eye(len(Nv))) @ Nv)
+    tol = 1e-5
+    ut, kt = emg.exp1_step(dg, u0, tau0, dt, emg.Options(krylov_m=30, krylov_tol=tol))
+    uf, kf = emg.exp1_step(dg, u0, tau0, dt, emg.Options(krylov_m=30))
+    assert kt < kf == 30, (kt, kf)
+    scale = np.linalg.norm(exact)
+    # the estimate bounds the true error: within the tolerance of the exact step and of the
+    # fixed-m step (which is exact to rounding here)
+    assert np.linalg.norm((ut - u0).ravel() - exact) <= tol * scale
+    assert np.linalg.norm((ut - uf).ravel()) <= tol * scale
+    # and the tolerance is not idle: the same test at 1e-10 takes more steps
+    _, kt2 = emg.exp1_step(dg, u0, tau0, dt, emg.Options(krylov_m=30, krylov_tol=1e-10))
+    assert kt < kt2
+
+
+@pytest.mark.slow
+def test_frozen_blocks_converge_to_the_same_steady_state():
+    """A preconditioner frozen for three V-cycles changes the path, not the fixed point R = 0
+    (Eq. prk_scalar): the same Newton steady state as the default cycle."""
+    from tests.test_oracle_dg import mms_error
+    _, dg, u_newton = mms_error(4, 1)
+    u0 = np.einsum('eq,eqi,eqa->eai', dg.levels[1].W, dg.levels[1].psi,
+                   dg.exact_state(dg.levels[1].x))
+    u, cycles, ok = emg.solve_steady(dg, u0, drop=1e-11, max_cycles=400,
+                                     opts=emg.Options(jac_freeze=3, exp_dt_global=True))
+    assert ok, cycles
+    assert np.abs(u - u_newton).max() < 1e-9 * np.abs(u_newton).max()

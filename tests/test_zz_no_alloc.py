@@ -1,10 +1,13 @@
 """The EXP1 step that allocates nothing (emg_exp1_step_noalloc) against emg_exp1_step.
 
-The no-allocation variant serves callers that may not call cudaMalloc while they run
-(their device memory comes from their own pool, or they issue work during stream
-capture); it keeps its Krylov work arrays in one fixed device array.  It must give the
-same result as the context-based step, call after call, although every call reuses the
-array the previous call left behind.  This file is collected last on purpose.
+The no-allocation variant serves callers that may not call cudaMalloc once they are running:
+their device memory comes from their own pool (a caching allocator that already holds the
+free memory), or their loop may not take the device-wide synchronisation that cudaMalloc and
+cudaFree can cause.  It keeps its Krylov work arrays in one fixed device array.  It must give
+the same result as the context-based step, call after call, although every call reuses the
+array the previous call left behind; it must reject sizes beyond the array and neighbour
+indices out of range before anything reads through them.  This file is collected last on
+purpose.
 """
 import numpy as np
 import pytest
@@ -12,35 +15,49 @@ import pytest
 from oracle import emg as oemg
 from oracle.dg import DG
 from tests.helpers import perturbed_state, rel_err
-from workloads import ogrid
+from workloads import cubed_sphere_shell, ogrid
 
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-12
 
 
-def test_noalloc_exp1_matches_context_exp1_twice():
+def _inputs(s, dg, seed, dev, torch):
+    p = dg.p_max
+    u = perturbed_state(dg, seed=seed, amp=0.02)
+    u0 = np.ascontiguousarray(u[:, :, :1])
+    dt = np.ascontiguousarray(oemg.dtau(dg, p, u, 100.0) * 3.0)
+    diag, off, nbr = s.jacobian_p0(u0)
+    r0 = s.residual(0, u0)
+    t = {name: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+         for name, a in dict(diag=diag, off=off, nbr=nbr, r0=r0, dt=dt, u0=u0).items()}
+    return u0, dt, t
+
+
+@pytest.mark.parametrize("mk,p,m,on_stream", [
+    (lambda: ogrid(32, 16), 2, 30, False),            # 2-D, legacy default stream
+    (lambda: cubed_sphere_shell(4, 3), 1, 40, True),  # 3-D (six faces), a torch stream, m at its limit
+])
+def test_noalloc_exp1_matches_context_exp1_twice(mk, p, m, on_stream):
     import torch
 
     import paper_1807_01151_gb300 as pkg
     from paper_1807_01151_gb300._lib import exp1_step_noalloc
 
     torch.cuda.set_device(0)
-    desc = ogrid(32, 16)
-    s = pkg.Solver(desc, p_max=2)
-    dg = DG(desc, 2)
+    desc = mk()
+    s = pkg.Solver(desc, p_max=p, krylov_m=m)
+    dg = DG(desc, p)
     dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream() if on_stream else None
     for call, seed in enumerate((11, 12)):
-        u = perturbed_state(dg, seed=seed, amp=0.02)
-        u0 = np.ascontiguousarray(u[:, :, :1])
-        dt = np.ascontiguousarray(oemg.dtau(dg, 2, u, 100.0) * 3.0)
+        u0, dt, t = _inputs(s, dg, seed, dev, torch)
         ref, k_ref = s.exp1_step(u0, dt)                          # context entry point
-        diag, off, nbr = s.jacobian_p0(u0)
-        r0 = s.residual(0, u0)
-        t = {name: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-             for name, a in dict(diag=diag, off=off, nbr=nbr, r0=r0, dt=dt, u0=u0).items()}
         out = torch.full_like(t["u0"], float("nan"))
-        k = exp1_step_noalloc(2, t["diag"], t["off"], t["nbr"], t["r0"], t["dt"], t["u0"], out, krylov_m=30)
+        torch.cuda.synchronize()
+        k = exp1_step_noalloc(dg.dim, t["diag"], t["off"], t["nbr"], t["r0"], t["dt"], t["u0"], out,
+                              krylov_m=m, stream=stream.cuda_stream if stream else None)
+        torch.cuda.synchronize()
         got = out.cpu().numpy()
         assert k == k_ref, (call, k, k_ref)
         assert np.isfinite(got).all()
@@ -60,3 +77,35 @@ def test_noalloc_rejects_sizes_beyond_its_array():
     with pytest.raises(EmgError) as ei:
         exp1_step_noalloc(2, z(E, 5, 5), z(E, 4, 5, 5), nbr, z(E, 5, 1), z(E), z(E, 5, 1), z(E, 5, 1))
     assert ei.value.status == 1
+    with pytest.raises(EmgError) as ei:
+        exp1_step_noalloc(2, z(8, 5, 5), z(8, 4, 5, 5), nbr[:8], z(8, 5, 1), z(8), z(8, 5, 1), z(8, 5, 1),
+                          krylov_m=41)
+    assert ei.value.status == 1
+
+
+def test_noalloc_rejects_neighbour_indices_out_of_range():
+    """A neighbour index outside [-1, n_elems) is caught by the packing kernel (which
+    substitutes -1 so that nothing out of range is read) and the call returns EMG_ERR_ARG
+    before the Krylov step; the next valid call is unaffected."""
+    import torch
+
+    import paper_1807_01151_gb300 as pkg
+    from paper_1807_01151_gb300._lib import EmgError, exp1_step_noalloc
+
+    desc = ogrid(16, 8)
+    s = pkg.Solver(desc, p_max=1)
+    dg = DG(desc, 1)
+    dev = torch.device("cuda", 0)
+    u0, dt, t = _inputs(s, dg, 5, dev, torch)
+    out = torch.zeros_like(t["u0"])
+    for bad in (dg.E, -2, 1 << 40):
+        nb = t["nbr"].clone()
+        nb[3, 1] = bad
+        with pytest.raises(EmgError) as ei:
+            exp1_step_noalloc(2, t["diag"], t["off"], nb, t["r0"], t["dt"], t["u0"], out)
+        assert ei.value.status == 1, bad
+    ref, k_ref = s.exp1_step(u0, dt)
+    k = exp1_step_noalloc(2, t["diag"], t["off"], t["nbr"], t["r0"], t["dt"], t["u0"], out)
+    assert k == k_ref
+    assert rel_err(out.cpu().numpy() - u0, ref - u0) < TOL
+    s.close()

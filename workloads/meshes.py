@@ -28,7 +28,8 @@ import numpy as np
 BC_INTERIOR = -1
 BC_WALL = 1        # inviscid slip wall (mirror ghost state)
 BC_FARFIELD = 2    # characteristic far field built from Riemann invariants
-BC_EXACT = 3       # ghost = prescribed exact state (manufactured-solution tests only)
+BC_SYMMETRY = 3    # symmetry plane: mirror ghost about the (flat) face normal
+BC_EXACT = 9       # ghost = prescribed exact state (manufactured-solution tests only)
 
 
 @dataclass
@@ -197,6 +198,42 @@ def cubed_sphere_shell(n, n_r, r0=0.5, r1=20.0, inner_bc=BC_WALL, outer_bc=BC_FA
     wn = np.zeros_like(xyz)
     wn[:, :ns] = unit.T          # sphere r = r0: radial unit vectors at the wall nodes
     return MeshDesc(3, xyz, en, fb, name=f"cubedsphere6x{n}x{n}x{n_r}", wall_normal=wn)
+
+
+def half_mesh(desc, axis=1, tol=1e-9):
+    """The part of a mesh on the positive side of the plane x_axis = 0, with the faces that lie
+    on the plane tagged as symmetry planes (the paper's sphere mesh respects the flow's planes
+    of symmetry and imposes a symmetry condition on them, Sec. 5).
+
+    Elements are kept when the mean of their nodes is on the positive side, in their original
+    order; nodes are renumbered in order of first use.  A face is on the plane when all of its
+    nodes are within tol * (largest node coordinate) of it.  Returns (MeshDesc, kept element
+    indices of the input mesh).
+    """
+    dim = desc.dim
+    nn = 1 << dim
+    X = desc.xyz
+    cen = X[:, desc.elem_nodes].mean(axis=2)              # [dim][E]
+    keep = np.nonzero(cen[axis] > 0.0)[0]
+    en = desc.elem_nodes[keep]
+    new_id = {}
+    for nd in en.ravel():
+        if int(nd) not in new_id:
+            new_id[int(nd)] = len(new_id)
+    old_of_new = np.array(list(new_id.keys()), dtype=np.int64)
+    en_new = np.array([new_id[int(nd)] for nd in en.ravel()], dtype=np.int64).reshape(en.shape)
+    xyz = X[:, old_of_new].copy()
+    fb = desc.face_bc[keep].copy()
+    scale = np.abs(X).max()
+    ref = np.array([[(a & 1) ^ ((a >> 1) & 1), (a >> 1) & 1, (a >> 2) & 1] for a in range(nn)])
+    for e in range(len(keep)):
+        for f in range(2 * dim):
+            ax, side = f >> 1, f & 1
+            loc = [a for a in range(nn) if ref[a][ax] == side]
+            if np.all(np.abs(xyz[axis, en_new[e, loc]]) <= tol * scale):
+                fb[e, f] = BC_SYMMETRY
+    wn = None if desc.wall_normal is None else desc.wall_normal[:, old_of_new].copy()
+    return MeshDesc(dim, xyz, en_new, fb, name=desc.name + f"_half{axis}", wall_normal=wn), keep
 
 
 # The synthetic stand-ins for the paper's cylinder and sphere cases.
