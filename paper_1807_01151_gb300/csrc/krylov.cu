@@ -546,7 +546,7 @@ __global__ void __cluster_dims__(PHI_CLUSTER, 1, 1)
     for (int t = threadIdx.x; t < nn; t += blockDim.x) {
         const int i = t / n, jj = t % n;
         double v = 0.0;
-        if (i < k && jj < k) v = H[(size_t)i * m + jj];
+        if (i < k && jj < k && i <= jj + 1) v = H[(size_t)i * m + jj];   // the Hessenberg band only
         if (i == 0 && jj == k) v = 1.0;
         if (EST && i == k && jj == k + 1) v = 1.0;
         M[i * ld + jj] = v;
@@ -908,9 +908,12 @@ extern "C" emg_status emg_exp1_step_noalloc(int32_t dim, int64_t n_elems, const 
     double* partC = partB + (size_t)NA_BLOCKS * NA_STRIDE;
     DevScalars* sc = reinterpret_cast<DevScalars*>(S + NA_OFF_SC);
     GridBar* bar = reinterpret_cast<GridBar*>(S + NA_OFF_BAR);
-    // the previous call's contents remain: clear the flags and the barrier
+    // the previous call's contents remain: clear the flags, the barrier and the Hessenberg
+    // matrix (whose row stride is this call's krylov_m)
     if (cudaMemsetAsync(sc, 0, sizeof(DevScalars), st) != cudaSuccess) return EMG_ERR_CUDA;
     if (cudaMemsetAsync(bar, 0, sizeof(GridBar), st) != cudaSuccess) return EMG_ERR_CUDA;
+    if (cudaMemsetAsync(H, 0, (size_t)(NA_MAX_M + 1) * NA_MAX_M * sizeof(double), st) != cudaSuccess)
+        return EMG_ERR_CUDA;
     const int64_t npack = E * (1 + NF) * 25;
     k_pack_bsr<<<(unsigned)((npack + 255) / 256), 256, 0, st>>>(E, NF, diag, off, nbr, bsr, nbr32, sc);
     if (cudaGetLastError() != cudaSuccess) return EMG_ERR_CUDA;

@@ -109,3 +109,27 @@ def test_noalloc_rejects_neighbour_indices_out_of_range():
     assert k == k_ref
     assert rel_err(out.cpu().numpy() - u0, ref - u0) < TOL
     s.close()
+
+
+def test_noalloc_alternating_krylov_dimensions():
+    """Calls with different m reuse the array with a different row stride of the Hessenberg
+    matrix; each must still equal the context step of the same m."""
+    import torch
+
+    import paper_1807_01151_gb300 as pkg
+    from paper_1807_01151_gb300._lib import exp1_step_noalloc
+
+    desc = ogrid(16, 8)
+    dg = DG(desc, 1)
+    dev = torch.device("cuda", 0)
+    solvers = {m: pkg.Solver(desc, p_max=1, krylov_m=m) for m in (40, 30, 12)}
+    for call, m in enumerate((40, 30, 12, 40)):
+        s = solvers[m]
+        u0, dt, t = _inputs(s, dg, 20 + call, dev, torch)
+        ref, k_ref = s.exp1_step(u0, dt)
+        out = torch.full_like(t["u0"], float("nan"))
+        k = exp1_step_noalloc(2, t["diag"], t["off"], t["nbr"], t["r0"], t["dt"], t["u0"], out, krylov_m=m)
+        assert k == k_ref, (m, k, k_ref)
+        assert rel_err(out.cpu().numpy() - u0, ref - u0) < TOL, (m, rel_err(out.cpu().numpy() - u0, ref - u0))
+    for s in solvers.values():
+        s.close()
