@@ -199,6 +199,8 @@ def test_probe_peaks_are_plausible():
     assert 20.0 < pk["fp32_tflops"] < 200.0, pk
     assert pk["fp32_tflops"] > 10 * pk["fp64_tflops"]
     assert 300.0 < pk["sm_mhz"] < 2500.0, pk
-    # the FP64 rate matches the unit count of 2 FP64 FMA per clock per SM (152 SMs) at the
-    # probe's own clock, within 15 %
-    assert abs(pk["fp64_tflops"] / (2 * 2 * 152 * pk["sm_mhz"] * 1e-6) - 1.0) < 0.15, pk
+    # the rates stay below the unit counts (2 FP64 and 128 FP32 FMA per clock per SM, 152 SMs)
+    # at the probe's own clock and reach most of them
+    r64 = pk["fp64_tflops"] / (2 * 2 * 152 * pk["sm_mhz"] * 1e-6)
+    r32 = pk["fp32_tflops"] / (128 * 2 * 152 * pk["sm_mhz"] * 1e-6)
+    assert 0.7 < r64 < 1.02 and 0.7 < r32 < 1.02, (r64, r32, pk)
