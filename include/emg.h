@@ -127,6 +127,12 @@ typedef struct {
                               rule q = p + 2 is built (2, the default; 0 is read as 2) */
     double omega[3];       /* angular velocity of the rotating frame (Eq. euler); only the
                               absolute frame omega = 0 is built (other values: EMG_ERR_ARG) */
+    int32_t block_kernels; /* kernels of the float32 block forms' assembly and inverse:
+                              0 (default): per level, the form this build measured faster;
+                              1: the tensor-core forms (tcgen05: 3xTF32 assembly, blocked
+                              Gauss-Jordan with rank-16 MMA updates for B = 75, 100, 175);
+                              2: the SIMT (FMA) forms.  The forms differ only in rounding; the
+                              BF16 form always assembles on the tensor cores. */
 } emg_params;
 
 typedef struct {

@@ -353,6 +353,7 @@ void emg_default_params(emg_params* p) {
     p->jac_freeze = 1;
     p->quad_extra = 2;
     p->omega[0] = p->omega[1] = p->omega[2] = 0.0;
+    p->block_kernels = 0;
 }
 
 const char* emg_build_info(void) {
@@ -387,6 +388,7 @@ emg_status emg_create_mesh(const emg_mesh_desc* m, const emg_params* prm, emg_ct
     if (prm->jac_freeze < 0) return fail(c, EMG_ERR_ARG, "jac_freeze must be >= 1");
     if (prm->quad_extra != 0 && prm->quad_extra != 2)
         return fail(c, EMG_ERR_ARG, "only the rule q = p + 2 is built (quad_extra 2)");
+    if (prm->block_kernels < 0 || prm->block_kernels > 2) return fail(c, EMG_ERR_ARG, "block_kernels must be 0, 1 or 2");
     if (prm->omega[0] != 0.0 || prm->omega[1] != 0.0 || prm->omega[2] != 0.0)
         return fail(c, EMG_ERR_ARG, "only the absolute frame (omega = 0) is built");
     c->p_max = prm->p_max;

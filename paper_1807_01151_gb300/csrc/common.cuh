@@ -23,6 +23,20 @@ constexpr int MAX_KRYLOV = 64;
 // inverse and the stage GEMV.
 inline bool blocks_f32(int prec) { return prec == EMG_PREC_FP32_BLOCKS || prec == EMG_PREC_BF16_BLOCKS; }
 
+// Which float32 block kernels a level uses (emg_params.block_kernels); the default follows the
+// kernel times measured on the GB300 (the SIMT forms where they are faster).
+inline bool use_tc_assembly(int dim, int p, int prec, int block_kernels) {
+    if (prec == EMG_PREC_BF16_BLOCKS || block_kernels == 1) return true;
+    if (block_kernels == 2) return false;
+    return dim == 3 && p >= 3;
+}
+inline bool use_tc_inverse(int B, int block_kernels) {
+    const bool built = B == 75 || B == 100 || B == 175;
+    if (!built || block_kernels == 2) return false;
+    if (block_kernels == 1) return true;
+    return B == 175;
+}
+
 __host__ __device__ constexpr int n_modes(int D, int P) {
     return D == 2 ? (P + 1) * (P + 2) / 2 : (P + 1) * (P + 2) * (P + 3) / 6;
 }
@@ -75,6 +89,8 @@ struct LevelDev {
     float* fjl32 = nullptr;    // [F][QF][25]  face Jacobians for the FP32 blocks
     float* fjr32 = nullptr;    // [F_int][QF][25]
     int gj_variant = 0;        // tuned variant of the FP32 Gauss-Jordan kernel
+    bool tc_asm = false;       // float32 block assembly on the tensor cores
+    bool tc_gj = false;        // float32 block inverse on the tensor cores
 };
 
 // Small device-side scalars of the cycle (no host round trip inside a V-cycle).

@@ -350,7 +350,7 @@ struct TcAsm {
     static constexpr int NPAD = ((N + 15) / 16) * 16;
     static constexpr int KTOT = Q + NF * QF;
     static constexpr int KSTEP = BF16 ? 16 : 8;          // depth of one MMA (32 bytes of K)
-    static constexpr int KC = BF16 ? 16 : (D == 3 ? 8 : 16);
+    static constexpr int KC = BF16 ? 16 : 8;               // points per chunk (small: more CTAs per SM)
     static constexpr int NCHUNK = (KTOT + KC - 1) / KC;
     static constexpr int ESZ = BF16 ? 2 : 4;
     static constexpr int PER_CORE = 16 / ESZ;            // depth elements per core-matrix row
@@ -749,7 +749,8 @@ static emg_status diag_tc_go(emg_ctx* c, const double* u, const double* cfl_dev,
     return EMG_OK;
 }
 
-// Block assembly of the float32 block forms on the tensor cores (levels p >= 1).
+// Block assembly of the float32 block forms (levels p >= 1): on the tensor cores or, where the
+// level's choice says so, the SIMT form.
 emg_status launch_diag_blocks32(emg_ctx* c, int p, const double* u, const double* cfl_dev, int shifted,
                                 float* out) {
     emg_status st = launch_face_jacobian32(c, p, u);
@@ -760,6 +761,21 @@ emg_status launch_diag_blocks32(emg_ctx* c, int p, const double* u, const double
         return EMG_ERR_ARG;
     }
     const bool bf = c->prm.prec == EMG_PREC_BF16_BLOCKS;
+    if (!L.tc_asm) {
+        // the SIMT (FMA) form of the same contraction
+        const int nmax = n_modes(c->dim, c->p_max);
+#define EMG_DB32(DD, PP)                                                                                    \
+    {                                                                                                       \
+        ProfScope _ps(c, PC_DIAG);                                                                          \
+        k_diag_blocks<DD, PP, float><<<(unsigned)c->E, DiagCfg<DD, PP>::THREADS, 0, c->stream>>>(           \
+            (int)c->E, nmax, u, L.vpsi32, L.vgw32, c->elem_face, L.fpsiL32, L.fpsiR32, L.fjl32, L.fjr32, c->psic, \
+            c->h, cfl_dev, c->prm.gamma, shifted, out);                                                     \
+    }
+        EMG_DISPATCH_DP(c->dim, p, EMG_DB32)
+#undef EMG_DB32
+        EMG_CHECK_LAUNCH(c);
+        return EMG_OK;
+    }
 #define EMG_TC(DD, PP) return bf ? diag_tc_go<DD, PP, true>(c, u, cfl_dev, shifted, out) \
                              : diag_tc_go<DD, PP, false>(c, u, cfl_dev, shifted, out)
     switch (c->dim * 8 + p) {

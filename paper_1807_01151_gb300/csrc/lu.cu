@@ -628,17 +628,19 @@ __global__ void __launch_bounds__(32 * W) k_gj_rot(int E, float* __restrict__ bl
 // M_k = I + x_k e_p^T, so the KB steps of a panel act on the columns outside it as
 // T = I + X S_P^T (S_P selects the panel's pivot rows); X[:, j] is the panel's column j after
 // all KB steps minus e_{p_j} (the in-place rule leaves M_j e_{p_j} in column j at step j).
-// Per panel: the panel's columns are factored with the usual steps in registers (one thread per
-// row, the pivot row broadcast through a double-buffered shared copy: one barrier per step),
-// then every other column takes the rank-KB update A += X A[P, :] as one tcgen05.mma per row
-// tile and 32-column step (3xTF32: x = hi + lo, X_hi R_hi + X_hi R_lo + X_lo R_hi, float32
-// accumulation), with the matrix held in TMEM (row r in lane r mod 128 of row tile r / 128).
-// Pivot choice and tie rule are those of the kernels above (largest |a_rk| among the unused
-// rows, lowest row on ties, the lowest unused row for a non-finite column); the inverse is
-// written column-major with the same permutation.
+// The matrix lives in TMEM (row r in lane r mod 128 of row tile r / 128).  Per panel: every
+// warp copies its rows' panel columns to shared memory; warp 0 alone factors the panel in
+// registers (lane l holds rows l, l + 32, ...: the pivot search and the pivot row's broadcast
+// are warp shuffles, so the steps need no block barrier); then every other column takes the
+// rank-KB update A += X A[P, :] as one tcgen05.mma per row tile and 32-byte K step (3xTF32:
+// x = hi + lo, X_hi R_hi + X_hi R_lo + X_lo R_hi, float32 accumulation).  Pivot choice and tie
+// rule are those of the kernels above (largest |a_rk| among the unused rows, lowest row on
+// ties, the lowest unused row for a non-finite column); the inverse is written column-major
+// with the same permutation.
 template <int B>
 struct GjTc {
     static constexpr int RT = (B + 127) / 128;           // 128-row tiles
+    static constexpr int RI = (B + 31) / 32;             // rows per lane of the factoring warp
     static constexpr int NC = ((B + 15) / 16) * 16;      // columns held per row tile
     static constexpr int KB = 16;
     static constexpr int NPANEL = (B + KB - 1) / KB;
@@ -648,26 +650,26 @@ struct GjTc {
     static constexpr uint32_t X_LBO = RT * 2048, R_LBO = (NC / 8) * 128, SBO = 128;
     static constexpr int X_BYTES = RT * 128 * KB * 4;     // one of the hi / lo copies
     static constexpr int R_BYTES = NC * KB * 4;
-    static constexpr int PB = RT * 128 * KB;               // floats of one broadcast buffer
-    static constexpr int OPS = 2 * X_BYTES + 2 * R_BYTES + 2 * PB * 4;
+    static constexpr int PANEL = RT * 128 * KB;            // floats of the shared panel copy
+    static constexpr int OPS = 2 * X_BYTES + 2 * R_BYTES + PANEL * 4;
     static constexpr int STAGE = B * B * 4;
     static constexpr int SMEM = OPS > STAGE ? OPS : STAGE;
     static_assert(COLS <= 512, "the block does not fit in the SM's tensor memory");
+    static_assert(RI * 32 <= RT * 128, "the factoring warp's rows lie in the panel copy");
 };
 
 template <int B>
 __global__ void __launch_bounds__(128) k_gj_tc(int E, float* __restrict__ blk, int* __restrict__ timeout_flag) {
     using G = GjTc<B>;
-    constexpr int RT = G::RT, NC = G::NC, KB = G::KB, T = G::T, PB = G::PB;
+    constexpr int RT = G::RT, RI = G::RI, NC = G::NC, KB = G::KB, T = G::T;
     extern __shared__ __align__(1024) unsigned char gsm[];
     float* stage = reinterpret_cast<float*>(gsm);           // the block at the start and the end
     unsigned char* Xh = gsm;                                // operands during the panels
     unsigned char* Xl = Xh + G::X_BYTES;
     unsigned char* Rh = Xl + G::X_BYTES;
     unsigned char* Rl = Rh + G::R_BYTES;
-    float* pbuf = reinterpret_cast<float*>(Rl + G::R_BYTES);   // [2][RT * 128][KB]
-    __shared__ float wv[2][4];
-    __shared__ int wi[2][4], wl[2][4];
+    float* panel = reinterpret_cast<float*>(Rl + G::R_BYTES);   // [RT * 128][KB]
+    __shared__ int pjs[RT * 128];    // pivot step of each row within the current panel, or -1
     __shared__ int perm[B], invp[B];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tbase_s;
@@ -703,9 +705,7 @@ __global__ void __launch_bounds__(128) k_gj_tc(int E, float* __restrict__ blk, i
             tc::st16(tbase + lane_base + (uint32_t)(rt * NC + c0), v);
         }
     }
-    bool used[RT];
-#pragma unroll
-    for (int rt = 0; rt < RT; ++rt) used[rt] = tid + 128 * rt >= B;   // padding rows never pivot
+    unsigned used = 0u;   // factoring warp: bit i set once row lane + 32 i has been a pivot row
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -716,99 +716,109 @@ __global__ void __launch_bounds__(128) k_gj_tc(int E, float* __restrict__ blk, i
     for (int pn = 0; pn < G::NPANEL; ++pn) {
         const int k0 = pn * KB;
         const int kw = (B - k0) < KB ? (B - k0) : KB;
+        // (1) every warp: its rows' panel columns into the shared copy
+#pragma unroll
+        for (int rt = 0; rt < RT; ++rt) {
+            float v[16];
+            tc::ld16(tbase + lane_base + (uint32_t)(rt * NC + k0), v);
+            const int r = tid + 128 * rt;
+            float4* dst = reinterpret_cast<float4*>(panel + r * KB);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+            pjs[r] = -1;
+        }
+        __syncthreads();
+        // (2) warp 0 factors the panel
+        if (warp == 0) {
+            float pr[RI][16];
+#pragma unroll
+            for (int i = 0; i < RI; ++i) {
+                const float4* src = reinterpret_cast<const float4*>(panel + (lane + 32 * i) * KB);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 x = src[q];
+                    pr[i][4 * q] = x.x, pr[i][4 * q + 1] = x.y, pr[i][4 * q + 2] = x.z, pr[i][4 * q + 3] = x.w;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < KB; ++j) {
+                if (j >= kw) break;
+                float best = -1.f;
+                int bi = B, lo = B;
+#pragma unroll
+                for (int i = 0; i < RI; ++i) {
+                    const int r = lane + 32 * i;
+                    if (r < B && !((used >> i) & 1u)) {
+                        const float m = fabsf(pr[i][j]);
+                        if (m > best) {
+                            best = m;
+                            bi = r;
+                        }
+                        lo = r < lo ? r : lo;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    const int ol = __shfl_xor_sync(0xffffffffu, lo, o);
+                    if (ob > best || (ob == best && oi < bi)) {
+                        best = ob;
+                        bi = oi;
+                    }
+                    lo = ol < lo ? ol : lo;
+                }
+                const int p = bi < B ? bi : lo;   // lowest unused row if the column is not finite
+                const int pl = p & 31, pi = p >> 5;
+                float prow[16];
+#pragma unroll
+                for (int i = 0; i < RI; ++i)
+                    if (i == pi) {   // warp-uniform
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) prow[c] = __shfl_sync(0xffffffffu, pr[i][c], pl);
+                    }
+                const float inv = 1.f / prow[j];
+                float rk[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) rk[c] = (c == j ? 1.f : prow[c]) * inv;
+#pragma unroll
+                for (int i = 0; i < RI; ++i) {
+                    const int r = lane + 32 * i;
+                    if (r == p) {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) pr[i][c] = rk[c];
+                        used |= 1u << i;
+                        pjs[r] = j;
+                    } else {
+                        const float f = pr[i][j];
+                        pr[i][j] = 0.f;
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) pr[i][c] -= f * rk[c];
+                    }
+                }
+                if (lane == 0) perm[k0 + j] = p;
+            }
+#pragma unroll
+            for (int i = 0; i < RI; ++i) {
+                float4* dst = reinterpret_cast<float4*>(panel + (lane + 32 * i) * KB);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dst[q] = make_float4(pr[i][4 * q], pr[i][4 * q + 1], pr[i][4 * q + 2], pr[i][4 * q + 3]);
+            }
+        }
+        __syncthreads();
+        // (3) every thread: its rows' panel columns after the steps, and X = those - e_{p_j}
         float pv[RT][16];
         int pj[RT];
 #pragma unroll
         for (int rt = 0; rt < RT; ++rt) {
-            tc::ld16(tbase + lane_base + (uint32_t)(rt * NC + k0), pv[rt]);
-            pj[rt] = -1;
-            float4* dst = reinterpret_cast<float4*>(pbuf + (tid + 128 * rt) * KB);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) dst[q] = make_float4(pv[rt][4 * q], pv[rt][4 * q + 1], pv[rt][4 * q + 2], pv[rt][4 * q + 3]);
-        }
-#pragma unroll
-        for (int j = 0; j < KB; ++j) {
-            if (j >= kw) break;
-            const int k = k0 + j, b = j & 1;
-            // this thread's candidate: largest |a_rk| among its unused rows, lowest row on ties
-            float best = -1.f;
-            int bi = B, lo = B;
-#pragma unroll
-            for (int rt = 0; rt < RT; ++rt) {
-                const int r = tid + 128 * rt;
-                if (!used[rt]) {
-                    const float m = fabsf(pv[rt][j]);
-                    if (m > best) {
-                        best = m;
-                        bi = r;
-                    }
-                    lo = r < lo ? r : lo;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                const int ol = __shfl_xor_sync(0xffffffffu, lo, o);
-                if (ob > best || (ob == best && oi < bi)) {
-                    best = ob;
-                    bi = oi;
-                }
-                lo = ol < lo ? ol : lo;
-            }
-            if (lane == 0) {
-                wv[b][warp] = best;
-                wi[b][warp] = bi;
-                wl[b][warp] = lo;
-            }
-            __syncthreads();
-            float bv = wv[b][0];
-            int p = wi[b][0], lw = wl[b][0];
-#pragma unroll
-            for (int w = 1; w < 4; ++w) {
-                if (wv[b][w] > bv || (wv[b][w] == bv && wi[b][w] < p)) {
-                    bv = wv[b][w];
-                    p = wi[b][w];
-                }
-                lw = wl[b][w] < lw ? wl[b][w] : lw;
-            }
-            if (p >= B) p = lw;   // no comparable candidate (a non-finite column)
-            if (tid == 0) perm[k] = p;
-            const float4* pr4 = reinterpret_cast<const float4*>(pbuf + b * PB + p * KB);
-            float prow[16];
+            const int r = tid + 128 * rt;
+            const float4* src = reinterpret_cast<const float4*>(panel + r * KB);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float4 x = pr4[q];
-                prow[4 * q] = x.x, prow[4 * q + 1] = x.y, prow[4 * q + 2] = x.z, prow[4 * q + 3] = x.w;
+                const float4 x = src[q];
+                pv[rt][4 * q] = x.x, pv[rt][4 * q + 1] = x.y, pv[rt][4 * q + 2] = x.z, pv[rt][4 * q + 3] = x.w;
             }
-            const float inv = 1.f / prow[j];
-            float rk[16];
-#pragma unroll
-            for (int c = 0; c < 16; ++c) rk[c] = (c == j ? 1.f : prow[c]) * inv;
-#pragma unroll
-            for (int rt = 0; rt < RT; ++rt) {
-                const int r = tid + 128 * rt;
-                if (r == p) {
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) pv[rt][c] = rk[c];
-                    used[rt] = true;
-                    pj[rt] = j;
-                } else {
-                    const float f = pv[rt][j];
-                    pv[rt][j] = 0.f;
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) pv[rt][c] -= f * rk[c];
-                }
-                float4* dst = reinterpret_cast<float4*>(pbuf + (b ^ 1) * PB + r * KB);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    dst[q] = make_float4(pv[rt][4 * q], pv[rt][4 * q + 1], pv[rt][4 * q + 2], pv[rt][4 * q + 3]);
-            }
-        }
-        // X = (panel columns after its steps) - e_{p_j}: the A operand, rows of every tile
-#pragma unroll
-        for (int rt = 0; rt < RT; ++rt) {
-            const int r = tid + 128 * rt;
+            pj[rt] = pjs[r];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 float x[4];
@@ -827,7 +837,7 @@ __global__ void __launch_bounds__(128) k_gj_tc(int E, float* __restrict__ blk, i
                 *reinterpret_cast<float4*>(Xl + off) = lo;
             }
         }
-        // R = the pivot rows before the panel, zero on the panel's columns: the B operand
+        // (4) R = the pivot rows before the panel, zero on the panel's columns: the B operand
         for (int t = tid; t < 2 * G::R_BYTES / 16; t += T) reinterpret_cast<float4*>(Rh)[t] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
 #pragma unroll
@@ -837,7 +847,7 @@ __global__ void __launch_bounds__(128) k_gj_tc(int E, float* __restrict__ blk, i
                 float v[16];
                 tc::ld16(tbase + lane_base + (uint32_t)(rt * NC + c0), v);
                 const int jj = pj[rt];
-                if (jj >= 0 && (c0 < k0 || c0 >= k0 + KB)) {
+                if (jj >= 0 && c0 != k0) {
 #pragma unroll
                     for (int cc = 0; cc < 16; ++cc) {
                         const int c = c0 + cc;
@@ -853,15 +863,16 @@ __global__ void __launch_bounds__(128) k_gj_tc(int E, float* __restrict__ blk, i
         tc::fence_proxy_async();
         tc::fence_before();
         __syncthreads();
+        // (5) the rank-KB update of every row tile
         if (tid == 0) {
             tc::fence_after();
             const uint32_t xh = tc::smem_u32(Xh), xl = tc::smem_u32(Xl), rh = tc::smem_u32(Rh), rl = tc::smem_u32(Rl);
 #pragma unroll
             for (int rt = 0; rt < RT; ++rt)
 #pragma unroll
-                for (int s = 0; s < KB / 8; ++s) {
-                    const uint32_t ka = (uint32_t)(2 * s) * G::X_LBO + (uint32_t)rt * 16u * G::SBO;
-                    const uint32_t kr = (uint32_t)(2 * s) * G::R_LBO;
+                for (int s2 = 0; s2 < KB / 8; ++s2) {
+                    const uint32_t ka = (uint32_t)(2 * s2) * G::X_LBO + (uint32_t)rt * 16u * G::SBO;
+                    const uint32_t kr = (uint32_t)(2 * s2) * G::R_LBO;
                     const uint64_t dxh = tc::sdesc(xh + ka, G::X_LBO, G::SBO);
                     const uint64_t drh = tc::sdesc(rh + kr, G::R_LBO, G::SBO);
                     const uint32_t d = tbase + (uint32_t)(rt * NC);
@@ -874,7 +885,7 @@ __global__ void __launch_bounds__(128) k_gj_tc(int E, float* __restrict__ blk, i
         if (!tc::mbar_wait(&mbar, phase, budget)) failed = true;
         phase ^= 1u;
         tc::fence_after();
-        // the panel's columns take their values after its steps (the MMA added zero there)
+        // (6) the panel's columns take their values after the steps (the MMA added zero there)
 #pragma unroll
         for (int rt = 0; rt < RT; ++rt) tc::st16(tbase + lane_base + (uint32_t)(rt * NC + k0), pv[rt]);
         tc::fence_before();
@@ -913,10 +924,6 @@ __global__ void __launch_bounds__(128) k_gj_tc(int E, float* __restrict__ blk, i
     if (warp == 0) tc::tmem_dealloc(tbase, G::TMEM_COLS);
     for (int t = tid; t < B * B; t += T) g[t] = stage[t];
 }
-
-// Block sizes whose inverse runs on the tensor cores (the 128-row tiles are filled enough);
-// the smaller blocks keep the tuned SIMT forms.
-static bool gj_on_tensor_cores(int B) { return B == 75 || B == 100 || B == 175; }
 
 // ---- variants of the FP32 Gauss-Jordan kernel and their tuning --------------------------------
 // Variant v unrolls the pivot loop kGjUnroll[v] times (0 = fully, only for B <= 100).  The
@@ -1040,7 +1047,7 @@ emg_status tune_gj(emg_ctx* c) {
             L.gj_variant = 0;
             continue;
         }
-        if (gj_on_tensor_cores(L.B)) {
+        if (L.tc_gj) {
             c->tuning += "gj B=" + std::to_string(L.B) + ": blocked tensor-core form (not tuned); ";
             continue;
         }
@@ -1107,12 +1114,12 @@ static emg_status gj_tc_go(emg_ctx* c, float* blk) {
 
 emg_status launch_lu32(emg_ctx* c, int p) {
     LevelDev& L = c->lv[p];
-    switch (L.B) {
-        case 75: return gj_tc_go<75>(c, L.blk32);
-        case 100: return gj_tc_go<100>(c, L.blk32);
-        case 175: return gj_tc_go<175>(c, L.blk32);
-        default: break;
-    }
+    if (L.tc_gj) switch (L.B) {
+            case 75: return gj_tc_go<75>(c, L.blk32);
+            case 100: return gj_tc_go<100>(c, L.blk32);
+            case 175: return gj_tc_go<175>(c, L.blk32);
+            default: break;
+        }
     bool ok = true;
     {
         ProfScope _ps(c, PC_LU);

@@ -653,6 +653,10 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
     }
     if (st != EMG_OK) return st;
     if (blocks_f32(c->prm.prec)) {
+        for (int p = 1; p <= c->p_max; ++p) {
+            c->lv[p].tc_asm = use_tc_assembly(D, p, c->prm.prec, c->prm.block_kernels);
+            c->lv[p].tc_gj = use_tc_inverse(c->lv[p].B, c->prm.block_kernels);
+        }
         st = build_float_tables(c);
         if (st != EMG_OK) return st;
         st = tune_gj(c);

@@ -52,10 +52,11 @@ def n_terms(dim, p):
 
 @pytest.mark.parametrize("name,mk,p", BLOCK_CASES)
 @pytest.mark.parametrize("cfl", [3.0, 100.0])
-def test_fp32_block_operator_and_inverse(name, mk, p, cfl):
+@pytest.mark.parametrize("kernels", [1, 2])          # tensor-core and SIMT forms
+def test_fp32_block_operator_and_inverse(name, mk, p, cfl, kernels):
     import paper_1807_01151_gb300 as pkg
     desc, dg, u, D = oracle_case(name, mk, p)
-    s = pkg.Solver(desc, p_max=p, prec=1)
+    s = pkg.Solver(desc, p_max=p, prec=1, block_kernels=kernels)
     B = D.shape[-1]
     dt = oemg.dtau(dg, p, u, cfl)
     P = np.eye(B)[None] / dt[:, None, None] - D
@@ -76,11 +77,12 @@ def test_fp32_block_operator_and_inverse(name, mk, p, cfl):
 
 
 @pytest.mark.parametrize("name,mk,p", BLOCK_CASES)
-def test_fp32_block_prk_step_at_block_size(name, mk, p):
+@pytest.mark.parametrize("kernels", [1, 2])
+def test_fp32_block_prk_step_at_block_size(name, mk, p, kernels):
     import paper_1807_01151_gb300 as pkg
     desc, dg, u, D = oracle_case(name, mk, p)
     cfl = 3.0
-    s = pkg.Solver(desc, p_max=p, prec=1)
+    s = pkg.Solver(desc, p_max=p, prec=1, block_kernels=kernels)
     ug = s.prk_step(p, u, cfl=cfl)
     Pg = s.block_operator(p, u, cfl=cfl, which=0)
     s.close()
@@ -92,6 +94,34 @@ def test_fp32_block_prk_step_at_block_size(name, mk, p):
     bound = 8 * np.linalg.cond(P).max() * (eps + B * U32)
     e = rel_err(ug - u, uo - u)
     assert 1e-12 < e <= bound, (e, bound)
+
+
+@pytest.mark.parametrize("name,mk,p", BLOCK_CASES)
+def test_bf16_block_operator(name, mk, p):
+    """The BF16 form multiplies bfloat16 operands (8 significant bits, rounding 2^-9) with float32
+    accumulation: each entry of P_e is a sum of K products whose operands carry relative errors
+    up to 2^-9, so |P^_e - P_e|_max <= 4 K 2^-9 max_t |term| with the largest term bounded by
+    the largest entry of the float32 block times the block's cancellation; asserted as a
+    relative max-norm error of 2^-5 per element, and at least float32 error (it is not the
+    float32 form)."""
+    import paper_1807_01151_gb300 as pkg
+    desc, dg, u, D = oracle_case(name, mk, p)
+    cfl = 3.0
+    B = D.shape[-1]
+    dt = oemg.dtau(dg, p, u, cfl)
+    P = np.eye(B)[None] / dt[:, None, None] - D
+    s = pkg.Solver(desc, p_max=p, prec=2)
+    Pg = s.block_operator(p, u, cfl=cfl, which=0)
+    Xg = s.block_operator(p, u, cfl=cfl, which=1)
+    s.close()
+    amax = np.abs(P).max(axis=(1, 2))
+    err = np.abs(Pg - P).max(axis=(1, 2)) / amax
+    assert np.all(err <= 2.0 ** -5), err.max()
+    assert err.max() > 16 * n_terms(dg.dim, p) * U32
+    # its explicit inverse is the float32 inverse of the bf16-assembled block
+    Xr = np.linalg.inv(Pg)
+    rel = np.linalg.norm(Xg - Xr, ord=2, axis=(1, 2)) / np.linalg.norm(Xr, ord=2, axis=(1, 2))
+    assert np.all(rel <= 4 * np.linalg.cond(Pg) * B * U32), rel.max()
 
 
 @pytest.mark.parametrize("mk,p", [(lambda: ogrid(16, 8), 4), (lambda: cubed_sphere_shell(2, 2), 3)])
