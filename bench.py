@@ -28,7 +28,17 @@ WORKLOADS = {
     "cyl128x64_p4": dict(name="cyl128x64_p4", n_theta=128, n_r=64, p_max=4, mach=0.3),
     "cyl64x32_p4": dict(name="cyl64x32_p4", n_theta=64, n_r=32, p_max=4, mach=0.3),
     "cyl32x16_p2": dict(name="cyl32x16_p2", n_theta=32, n_r=16, p_max=2, mach=0.3),
+    # small spheres for profiling captures of the 3-D kernels
+    "sph6x8x8x8_p4": dict(name="sph6x8x8x8_p4", kind="sphere", n=8, n_r=8, p_max=4, mach=0.3),
+    "sph6x8x8x12_p3": dict(name="sph6x8x8x12_p3", kind="sphere", n=8, n_r=12, p_max=3, mach=0.3),
 }
+
+
+def make_mesh(W):
+    from workloads import cubed_sphere_shell, ogrid
+    if W.get("kind") == "sphere":
+        return cubed_sphere_shell(W["n"], W["n_r"])
+    return ogrid(W["n_theta"], W["n_r"])
 METRIC = "time to 1e-10 residual drop & DG residual GDoF/s: mixed vs FP64, 1 GB300"
 # DRAM bytes (read + write) of one k_volume launch at p = 4 on the 128 x 64 O-grid, from an ncu
 # capture of this kernel (dram__bytes_read.sum + dram__bytes_write.sum); None once the kernel
@@ -44,7 +54,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="emg", choices=["emg", "reference"])
     ap.add_argument("--workload", default="cyl128x64_p4", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="both", choices=["both", "fp64", "mixed"])
+    ap.add_argument("--prec", default="all", choices=["all", "both", "fp64", "mixed", "bf16"],
+                    help="all: the mixed (FP32 blocks) form timed, with the FP64 and BF16-block forms beside it")
+    ap.add_argument("--block-kernels", type=int, default=0, choices=[0, 1, 2],
+                    help="float32 block kernels: 0 the built-in choice per level, 1 tensor cores, 2 SIMT")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-10 solves")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--serve", action="store_true",
@@ -84,8 +97,9 @@ def oracle_sample(W, steps, warmup):
     O-grid family and degree at 16 x 8 elements.  Returns (GDoF/s, seconds, E)."""
     from oracle import emg as oemg
     from oracle.dg import DG
-    from workloads import ogrid
-    dg = DG(ogrid(16, 8), W["p_max"], mach=W["mach"])
+    from workloads import cubed_sphere_shell, ogrid
+    sample = cubed_sphere_shell(2, 1) if W.get("kind") == "sphere" else ogrid(16, 8)
+    dg = DG(sample, W["p_max"], mach=W["mach"])
     u = dg.freestream_state()
     opts = oemg.Options()
     n = 1
@@ -257,10 +271,12 @@ def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks, pe
     """Time K V-cycles of one form; return a dict of results (and the solver closed)."""
     from paper_1807_01151_gb300 import perfmodel
     stream = torch.cuda.Stream()
-    s = pkg.Solver(mesh, p_max=W["p_max"], mach=W["mach"], prec=prec, stream=stream.cuda_stream)
+    s = pkg.Solver(mesh, p_max=W["p_max"], mach=W["mach"], prec=prec, stream=stream.cuda_stream,
+                   block_kernels=args.block_kernels)
     E, N = s.E, s.n_modes(W["p_max"])
     K = 5 * N * E
-    F = (4 * E + 2 * W["n_theta"]) // 2
+    F = int((mesh.face_bc.size + (mesh.face_bc >= 0).sum()) // 2)   # interior faces counted twice
+    dim = mesh.dim
     s.set_state(None)
     for _ in range(max(args.warmup, 3)):
         s.vcycle(info=False)
@@ -350,11 +366,11 @@ def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks, pe
         out["state"] = s.get_state()
     # roofline of the dominant FP64 kernel, k_volume at p_max, per launch (algorithmic FLOPs /
     # live launch time), and of every kernel class per cycle
-    work = perfmodel.vcycle_work(2, W["p_max"], E, F)
-    fl = perfmodel.residual_volume_flops(perfmodel.Shape(2, W["p_max"], E, F))
+    work = perfmodel.vcycle_work(dim, W["p_max"], E, F)
+    fl = perfmodel.residual_volume_flops(perfmodel.Shape(dim, W["p_max"], E, F))
     achieved = fl / (vol_launch_ms * 1e-3) / 1e12
     pk = peaks["fp64_tflops"]
-    out["roofline"] = {"bound": "alu", "kernel": f"k_volume<2,{W['p_max']}> (DG residual, volume + face projection)",
+    out["roofline"] = {"bound": "alu", "kernel": f"k_volume<{dim},{W['p_max']}> (DG residual, volume + face projection)",
                        "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
                        "traffic": VOLUME_P4_TRAFFIC.get(W["name"]),
                        "peak_source": peaks["fp64_source"], "probe_tflops": peaks["fp64_probe_tflops"],
@@ -441,7 +457,6 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_1807_01151_gb300 as pkg
     from paper_1807_01151_gb300._lib import probe_peaks
-    from workloads import ogrid
     probe = probe_peaks()
     mp_, mp_src = measured_peaks()
     # ALU roofs from the unit counts and the SM clock (the recipe's maximum clock unless the
@@ -459,8 +474,8 @@ def main():
         "probe_sm_mhz": probe2["sm_mhz"], "probe_clock_samples": cs,
     }
     hbm_gbs = float(mp_.get("hbm_gbs", 6800.0))
-    mesh = ogrid(W["n_theta"], W["n_r"])
-    precs = {"both": [1, 0], "mixed": [1], "fp64": [0]}[args.prec]
+    mesh = make_mesh(W)
+    precs = {"all": [1, 0, 2], "both": [1, 0], "mixed": [1], "fp64": [0], "bf16": [2]}[args.prec]
     res = {p: measure(pkg, torch, mesh, W, p, args, world, local, rank, with_clocks=(i == 0), peaks=peaks,
                       hbm_gbs=hbm_gbs)
            for i, p in enumerate(precs)}
@@ -473,20 +488,27 @@ def main():
                 t_key[f"t_1e-10_{PREC_NAMES[p]}_s"] = round(t["seconds"], 3)
                 t_key[f"cycles_1e-10_{PREC_NAMES[p]}"] = t["cycles"]
                 t_key[f"converged_{PREC_NAMES[p]}"] = t["converged"]
-        if 0 in res and 1 in res and "state" in res[0] and "state" in res[1]:
-            a, b = res[1]["state"], res[0]["state"]
-            t_key.update(state_comparison(a, b, W))
+        if W.get("kind") != "sphere" and 0 in res and "state" in res[0]:
+            if 1 in res and "state" in res[1]:
+                t_key.update(state_comparison(res[1]["state"], res[0]["state"], W))
+            if 2 in res and "state" in res[2]:
+                c2 = state_comparison(res[2]["state"], res[0]["state"], W)
+                t_key["bf16_vs_fp64_symmetric_part_relerr"] = c2["mixed_vs_fp64_symmetric_part_relerr"]
+                t_key["bf16_vs_fp64_converged_relerr"] = c2["mixed_vs_fp64_converged_relerr"]
         line = {
             "metric": METRIC, "value": head["value"], "unit": "GDoF/s", **t_key,
             "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": head["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32" if precs[0] == 1 else "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": {0: "f64", 1: "f64+f32", 2: "f64+bf16"}[precs[0]],
             "data": "synthetic",
-            "config": {"workload": W["name"], "mesh": f"O-grid {W['n_theta']}x{W['n_r']} r in [0.5,20]",
+            "config": {"workload": W["name"],
+                       "mesh": (f"cubed-sphere shell 6x{W['n']}x{W['n']}x{W['n_r']} r in [0.5,20]" if W.get("kind") == "sphere"
+                                else f"O-grid {W['n_theta']}x{W['n_r']} r in [0.5,20]"),
                        "p_max": W["p_max"], "elements": head["E"], "dof": head["K"], "mach": W["mach"],
                        "form": PREC_NAMES[precs[0]],
                        "l2": "inputs larger than L2: tables and block factors stream > 1 GB per V-cycle",
                        "timed_path": "captured V-cycle graphs replayed, profiler off",
+                       "block_kernels": args.block_kernels,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "residual_gdofs": head["residual_gdofs"], "residual_ms": head["residual_ms"],
             "time_to_1e-10": head.get("time_to_1e-10"),

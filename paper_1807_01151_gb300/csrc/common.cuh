@@ -23,18 +23,22 @@ constexpr int MAX_KRYLOV = 64;
 // inverse and the stage GEMV.
 inline bool blocks_f32(int prec) { return prec == EMG_PREC_FP32_BLOCKS || prec == EMG_PREC_BF16_BLOCKS; }
 
-// Which float32 block kernels a level uses (emg_params.block_kernels); the default follows the
-// kernel times measured on the GB300 (the SIMT forms where they are faster).
+// Which float32 block kernels a level uses (emg_params.block_kernels).  The default follows the
+// per-cycle kernel times measured on the GB300 with both forms: the SIMT assembly was faster at
+// every level (2-D p = 4: 1.69 vs 2.33 ms, 3-D p = 3: 3.72 vs 4.63 ms, 3-D p = 4: 11.8 vs
+// 16.6 ms per cycle); the tensor-core inverse was faster at B = 100 (2.67 vs 3.47 ms) and
+// slower at B = 75 and 175.  The BF16 form needs the tensor-core assembly.
 inline bool use_tc_assembly(int dim, int p, int prec, int block_kernels) {
+    (void)dim;
+    (void)p;
     if (prec == EMG_PREC_BF16_BLOCKS || block_kernels == 1) return true;
-    if (block_kernels == 2) return false;
-    return dim == 3 && p >= 3;
+    return false;
 }
 inline bool use_tc_inverse(int B, int block_kernels) {
     const bool built = B == 75 || B == 100 || B == 175;
     if (!built || block_kernels == 2) return false;
     if (block_kernels == 1) return true;
-    return B == 175;
+    return B == 100;
 }
 
 __host__ __device__ constexpr int n_modes(int D, int P) {

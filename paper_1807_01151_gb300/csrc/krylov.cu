@@ -225,10 +225,98 @@ __device__ __forceinline__ void spmv_rows(int64_t k0, int64_t k1, int NF, const 
     }
 }
 
-// Three grid barriers per Krylov step: after the first dot sweep, after the second, and
-// after the norm.  The next step's product A v_{j+1} is taken as (A w)/h_{j+1,j} from the
-// neighbours' w (final before the third barrier) into the other half of w, so v_{j+1}
-// need not be published before it is used.
+// Row k of A x = DT J_0 x for the vector x (other blocks' entries read through L2).
+__device__ __forceinline__ double a_row(int64_t k, int NF, const double* __restrict__ bsr, const int* __restrict__ nbr,
+                                        const double* __restrict__ dt, const double* x) {
+    const int e = (int)(k / 5), a = (int)(k % 5);
+    const double* row = bsr + (size_t)e * (1 + NF) * 25;
+    double s = 0.0;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) s += row[a * 5 + b] * __ldcg(x + (size_t)e * 5 + b);
+    for (int lf = 0; lf < NF; ++lf) {
+        const int n = nbr[(size_t)e * NF + lf];
+        if (n < 0) continue;
+        const double* blk = row + (1 + lf) * 25;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) s += blk[a * 5 + b] * __ldcg(x + (size_t)n * 5 + b);
+    }
+    return dt[e] * s;
+}
+
+// The two halves of Krylov step j, shared by the persistent kernel and the barrier-free
+// kernels (the same blocks and the same arithmetic in the same order: bitwise the same
+// results).  CGS2 with two reductions per step: the first sweep gives h1 = V^T w and w.w,
+// the second h2 = V^T w1 and w1.w1 (w1 = w - V h1); with V orthonormal the subdiagonal is
+// h_{j+1,j} = (w1.w1 - h2.h2)^(1/2), so no third reduction is needed.  The next product is
+// A v_{j+1} = (A w1 - A V h2) / h_{j+1,j}: A w1 uses the neighbours' w1 (final at the second
+// reduction) and A V h2 = V (H~_j h2), from the Arnoldi relation A v_i = sum_l h_{l,i} v_l,
+// uses this block's rows only (h2 is at rounding level, so the correction is small).
+
+// First half: h1 from the first sweep's partials; w <- w1 = w - V h1 on this block's rows;
+// the second sweep into partB.
+__device__ __forceinline__ void arn_half1(int j, int64_t K0, int64_t k0, int64_t k1, int nb, int stride,
+                                          const double* V, double* w, const double* partA, double* partB_blk,
+                                          double* h1, double (*sh)[ARN_MAXCOL]) {
+    reduce_cols(partA, nb, stride, j + 2, h1, sh);
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
+        double s = w[k];
+        for (int i = 0; i <= j; ++i) s -= h1[i] * V[(size_t)i * K0 + k];
+        w[k] = s;
+    }
+    __syncthreads();
+    slice_dots(V, w, K0, k0, k1, j + 1, 1, partB_blk, sh);
+}
+
+// Second half: h2 and w1.w1; h_{j+1,j}; Hessenberg column j and the flags (block 0); unless the
+// process ends (breakdown or j + 1 = m): v_{j+1}, the next product into wn and the next step's
+// first sweep into partA.  Returns whether the process continues (the same in every block).
+__device__ __forceinline__ bool arn_half2(int j, int m, int64_t K0, int64_t k0, int64_t k1, int nb, int stride,
+                                          int NF, const double* __restrict__ bsr, const int* __restrict__ nbr,
+                                          const double* __restrict__ dt, double* V, const double* w1, double* wn,
+                                          double* H, const double* partB, double* partA_blk, const double* h1,
+                                          double* h2, double* cs, DevScalars* sc, double (*sh)[ARN_MAXCOL]) {
+    reduce_cols(partB, nb, stride, j + 2, h2, sh);
+    double hh = 0.0;
+    for (int i = 0; i <= j; ++i) hh += h2[i] * h2[i];
+    const double hn = sqrt(fmax(h2[j + 1] - hh, 0.0));
+    const double w0 = sqrt(h1[j + 1]);
+    const bool brk = !(hn > 1e-12 * w0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h1[i] + h2[i];
+        H[(size_t)(j + 1) * m + j] = hn;
+        sc->m_used = j + 1;
+        sc->hsub = hn;
+        sc->w0 = w0;
+        if (!isfinite(hn)) sc->nonfinite = 1;
+        if (brk) sc->broken = 1;
+    }
+    if (brk || j + 1 == m) return false;   // uniform: every block reduced the same values
+    const double ih = 1.0 / hn;
+    // c = H~_j h2 over l = 0..j+1 (column j from this step's values, the others from H)
+    for (int l = threadIdx.x; l <= j + 1; l += ARN_THREADS) {
+        double c = 0.0;
+        for (int i = (l > 0 ? l - 1 : 0); i < j; ++i) c += __ldcg(H + (size_t)l * m + i) * h2[i];
+        c += (l <= j ? h1[l] + h2[l] : hn) * h2[j];
+        cs[l] = c;
+    }
+    __syncthreads();
+    double* vn = V + (size_t)(j + 1) * K0;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
+        double s = w1[k];
+        for (int i = 0; i <= j; ++i) s -= h2[i] * V[(size_t)i * K0 + k];
+        const double v = s * ih;
+        vn[k] = v;
+        double t = a_row(k, NF, bsr, nbr, dt, w1);
+        for (int l = 0; l <= j; ++l) t -= cs[l] * V[(size_t)l * K0 + k];
+        t -= cs[j + 1] * v;
+        wn[k] = t * ih;
+    }
+    __syncthreads();
+    slice_dots(V, wn, K0, k0, k1, j + 2, 1, partA_blk, sh);
+    return true;
+}
+
+// Two grid barriers per Krylov step (one per reduction).
 __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int NF, int m,
                                                          const double* __restrict__ bsr, const int* __restrict__ nbr,
                                                          const double* __restrict__ dt, const double* __restrict__ r,
@@ -237,7 +325,7 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
                                                          double* __restrict__ partB, double* __restrict__ partC,
                                                          int stride, GridBar* bar, long long budget, DevScalars* sc) {
     __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
-    __shared__ double h1[ARN_MAXCOL], h2[ARN_MAXCOL], red[8];
+    __shared__ double h1[ARN_MAXCOL], h2[ARN_MAXCOL], cs[ARN_MAXCOL], red[8];
     __shared__ int s_ok;
     unsigned epoch = 0;   // barriers passed (thread 0's copy is the one used)
     const unsigned nb = gridDim.x;
@@ -251,7 +339,6 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
             const double x = dt[k / 5] * r[k];
             v[0] += x * x;
         }
-        // partC: partA is written again by the first dot sweep before any further barrier
         block_reduce_store(v, 1, partC + (size_t)blockIdx.x * stride, sh);
     }
     if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
@@ -266,64 +353,24 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
     if (beta == 0.0 || !isfinite(beta)) return;   // uniform across blocks
     const double ib = 1.0 / beta;
     for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) V[k] = dt[k / 5] * r[k] * ib;
-    double* w = wbuf;
-    spmv_rows(k0, k1, NF, bsr, nbr, dt, nullptr, r, ib, w);   // A v_1 from the inputs: no barrier
+    spmv_rows(k0, k1, NF, bsr, nbr, dt, nullptr, r, ib, wbuf);   // A v_1 from the inputs: no barrier
     __syncthreads();
+    slice_dots(V, wbuf, K0, k0, k1, 1, 1, partA + (size_t)blockIdx.x * stride, sh);
     for (int j = 0; j < m; ++j) {
-        // CGS pass 1: h1 = V^T w and w.w
-        slice_dots(V, w, K0, k0, k1, j + 1, 1, partA + (size_t)blockIdx.x * stride, sh);
+        double* w = wbuf + (size_t)(j & 1) * K0;
         if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
-        reduce_cols(partA, nb, stride, j + 2, h1, sh);
-        for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
-            double s = w[k];
-            for (int i = 0; i <= j; ++i) s -= h1[i] * V[(size_t)i * K0 + k];
-            w[k] = s;
-        }
-        __syncthreads();
-        // CGS pass 2 (re-orthogonalisation)
-        slice_dots(V, w, K0, k0, k1, j + 1, 0, partB + (size_t)blockIdx.x * stride, sh);
+        arn_half1(j, K0, k0, k1, (int)nb, stride, V, w, partA, partB + (size_t)blockIdx.x * stride, h1, sh);
         if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
-        reduce_cols(partB, nb, stride, j + 1, h2, sh);
-        {
-            double v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
-            for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
-                double s = w[k];
-                for (int i = 0; i <= j; ++i) s -= h2[i] * V[(size_t)i * K0 + k];
-                w[k] = s;
-                v[0] += s * s;
-            }
-            block_reduce_store(v, 1, partC + (size_t)blockIdx.x * stride, sh);
-        }
-        if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
-        reduce_cols(partC, nb, stride, 1, red, sh);
-        const double hn = sqrt(red[0]);
-        const double w0 = sqrt(h1[j + 1]);
-        const bool brk = !(hn > 1e-12 * w0);
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h1[i] + h2[i];
-            H[(size_t)(j + 1) * m + j] = hn;
-            sc->m_used = j + 1;
-            sc->hsub = hn;
-            sc->w0 = w0;
-            if (!isfinite(hn)) sc->nonfinite = 1;
-            if (brk) sc->broken = 1;
-        }
-        if (brk || j + 1 == m) break;   // uniform: every block reduced the same value
-        const double ih = 1.0 / hn;
-        double* vn = V + (size_t)(j + 1) * K0;
-        for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) vn[k] = w[k] * ih;
-        double* wn = wbuf + (size_t)((j + 1) & 1) * K0;
-        spmv_rows(k0, k1, NF, bsr, nbr, dt, w, nullptr, ih, wn);
-        __syncthreads();
-        w = wn;
+        if (!arn_half2(j, m, K0, k0, k1, (int)nb, stride, NF, bsr, nbr, dt, V, w, wbuf + (size_t)((j + 1) & 1) * K0, H,
+                       partB, partA + (size_t)blockIdx.x * stride, h1, h2, cs, sc, sh))
+            break;
     }
 }
 
 // ---- the same Arnoldi process without grid barriers ----------------------------------------
 // Kernel boundaries take the place of the persistent kernel's grid barriers: a start kernel
-// (norm partials of N), an init kernel (beta, v_1, A v_1, first dot sweep) and three kernels
-// per Krylov step (second sweep; norm; H column, v_{j+1}, next product and next first
-// sweep).  Each block does exactly the persistent kernel's work on the same slice, with the
+// (norm partials of N), an init kernel (beta, v_1, A v_1, first dot sweep) and two kernels
+// per Krylov step (the two halves above).  Each block does exactly the persistent kernel's work on the same slice, with the
 // same block count, so the Krylov basis and H are bitwise the same; no block ever waits for
 // another, so nothing depends on the blocks being co-resident (several contexts sharing the
 // device).  h1 travels between kernels through hcol[]; a kernel that finds the process
@@ -386,79 +433,33 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arn_init(ArnArgs A) {
     slice_dots(A.V, A.wbuf, A.K0, k0, k1, 1, 1, A.partA + (size_t)blockIdx.x * A.stride, sh);
 }
 
-// step j: h1 from the first sweep, w -= V h1, second sweep
-__global__ void __launch_bounds__(ARN_THREADS) k_arn_pass2(ArnArgs A, int j) {
+// step j, first half (h1 reaches the second half through hcol[])
+__global__ void __launch_bounds__(ARN_THREADS) k_arn_half1(ArnArgs A, int j) {
     __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
     __shared__ double h1[ARN_MAXCOL];
     if (*((volatile int*)&A.sc->broken)) return;
     int64_t k0, k1;
     arn_slice(A.K0, &k0, &k1);
-    const int nb = (int)gridDim.x;
     double* w = A.wbuf + (size_t)(j & 1) * A.K0;
-    reduce_cols(A.partA, nb, A.stride, j + 2, h1, sh);
+    arn_half1(j, A.K0, k0, k1, (int)gridDim.x, A.stride, A.V, w, A.partA, A.partB + (size_t)blockIdx.x * A.stride,
+              h1, sh);
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i < j + 2; i += ARN_THREADS) A.hcol[i] = h1[i];
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
-        double s = w[k];
-        for (int i = 0; i <= j; ++i) s -= h1[i] * A.V[(size_t)i * A.K0 + k];
-        w[k] = s;
-    }
+}
+
+// step j, second half
+__global__ void __launch_bounds__(ARN_THREADS) k_arn_half2(ArnArgs A, int j) {
+    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
+    __shared__ double h1[ARN_MAXCOL], h2[ARN_MAXCOL], cs[ARN_MAXCOL];
+    if (*((volatile int*)&A.sc->broken)) return;
+    int64_t k0, k1;
+    arn_slice(A.K0, &k0, &k1);
+    for (int i = threadIdx.x; i < j + 2; i += ARN_THREADS) h1[i] = __ldcg(A.hcol + i);
     __syncthreads();
-    slice_dots(A.V, w, A.K0, k0, k1, j + 1, 0, A.partB + (size_t)blockIdx.x * A.stride, sh);
-}
-
-// step j: h2, w -= V h2, norm partials; column j of H above the subdiagonal
-__global__ void __launch_bounds__(ARN_THREADS) k_arn_pass3(ArnArgs A, int j) {
-    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
-    __shared__ double h2[ARN_MAXCOL];
-    if (*((volatile int*)&A.sc->broken)) return;
-    int64_t k0, k1;
-    arn_slice(A.K0, &k0, &k1);
-    const int nb = (int)gridDim.x;
-    double* w = A.wbuf + (size_t)(j & 1) * A.K0;
-    reduce_cols(A.partB, nb, A.stride, j + 1, h2, sh);
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        for (int i = 0; i <= j; ++i) A.H[(size_t)i * A.m + j] = A.hcol[i] + h2[i];
-    double v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
-        double s = w[k];
-        for (int i = 0; i <= j; ++i) s -= h2[i] * A.V[(size_t)i * A.K0 + k];
-        w[k] = s;
-        v[0] += s * s;
-    }
-    block_reduce_store(v, 1, A.partC + (size_t)blockIdx.x * A.stride, sh);
-}
-
-// step j: h_{j+1,j}, breakdown test; unless the process ends, v_{j+1}, the next product and
-// the next step's first sweep
-__global__ void __launch_bounds__(ARN_THREADS) k_arn_pass4(ArnArgs A, int j) {
-    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
-    __shared__ double red[8];
-    if (*((volatile int*)&A.sc->broken)) return;
-    int64_t k0, k1;
-    arn_slice(A.K0, &k0, &k1);
-    const int nb = (int)gridDim.x;
-    reduce_cols(A.partC, nb, A.stride, 1, red, sh);
-    const double hn = sqrt(red[0]);
-    const double w0 = sqrt(A.hcol[j + 1]);
-    const bool brk = !(hn > 1e-12 * w0);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        A.H[(size_t)(j + 1) * A.m + j] = hn;
-        A.sc->m_used = j + 1;
-        A.sc->hsub = hn;
-        A.sc->w0 = w0;
-        if (!isfinite(hn)) A.sc->nonfinite = 1;
-        if (brk) A.sc->broken = 1;
-    }
-    if (brk || j + 1 == A.m) return;
-    const double ih = 1.0 / hn;
-    const double* w = A.wbuf + (size_t)(j & 1) * A.K0;
-    double* vn = A.V + (size_t)(j + 1) * A.K0;
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) vn[k] = w[k] * ih;
+    const double* w1 = A.wbuf + (size_t)(j & 1) * A.K0;
     double* wn = A.wbuf + (size_t)((j + 1) & 1) * A.K0;
-    spmv_rows(k0, k1, A.NF, A.bsr, A.nbr, A.dt, w, nullptr, ih, wn);
-    __syncthreads();
-    slice_dots(A.V, wn, A.K0, k0, k1, j + 2, 1, A.partA + (size_t)blockIdx.x * A.stride, sh);
+    arn_half2(j, A.m, A.K0, k0, k1, (int)gridDim.x, A.stride, A.NF, A.bsr, A.nbr, A.dt, A.V, w1, wn, A.H, A.partB,
+              A.partA + (size_t)blockIdx.x * A.stride, h1, h2, cs, A.sc, sh);
 }
 
 // Self-test of the bounded wait: one block waits at a barrier sized for two blocks, so
@@ -767,7 +768,7 @@ emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, do
     double* HH = c->H;
     const double tol = c->prm.krylov_tol;
     if (!c->prm.coop_krylov || tol > 0.0) {
-        // barrier-free form (same blocks, same arithmetic): 2 + 3m plain launches; with a
+        // barrier-free form (same blocks, same arithmetic): 2 + 2m plain launches; with a
         // Krylov tolerance, the test of each step follows it (it may end the process)
         ArnArgs A{K0, 2 * c->dim, m, stride, bsr, nbr, dt, rr, Vv, ww, HH, c->hcol, partA, partB, partC, c->sc};
         const unsigned g = (unsigned)nb;
@@ -777,9 +778,8 @@ emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, do
         { ProfScope _ps(c, PC_ARNOLDI); k_arn_start<<<g, ARN_THREADS, 0, c->stream>>>(A); }
         { ProfScope _ps(c, PC_ARNOLDI); k_arn_init<<<g, ARN_THREADS, 0, c->stream>>>(A); }
         for (int j = 0; j < m; ++j) {
-            { ProfScope _ps(c, PC_ARNOLDI); k_arn_pass2<<<g, ARN_THREADS, 0, c->stream>>>(A, j); }
-            { ProfScope _ps(c, PC_ARNOLDI); k_arn_pass3<<<g, ARN_THREADS, 0, c->stream>>>(A, j); }
-            { ProfScope _ps(c, PC_ARNOLDI); k_arn_pass4<<<g, ARN_THREADS, 0, c->stream>>>(A, j); }
+            { ProfScope _ps(c, PC_ARNOLDI); k_arn_half1<<<g, ARN_THREADS, 0, c->stream>>>(A, j); }
+            { ProfScope _ps(c, PC_ARNOLDI); k_arn_half2<<<g, ARN_THREADS, 0, c->stream>>>(A, j); }
             if (tol > 0.0 && j + 1 < m) {
                 ProfScope _ps(c, PC_PHI);
                 k_phi<true><<<PHI_CLUSTER, 256, smem_est, c->stream>>>(m, j, tol, c->H, c->y, pade13(), c->sc);
