@@ -366,7 +366,7 @@ def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks, pe
         out["state"] = s.get_state()
     # roofline of the dominant FP64 kernel, k_volume at p_max, per launch (algorithmic FLOPs /
     # live launch time), and of every kernel class per cycle
-    work = perfmodel.vcycle_work(dim, W["p_max"], E, F)
+    work = perfmodel.vcycle_work(dim, W["p_max"], E, F, form=prec)
     fl = perfmodel.residual_volume_flops(perfmodel.Shape(dim, W["p_max"], E, F))
     achieved = fl / (vol_launch_ms * 1e-3) / 1e12
     pk = peaks["fp64_tflops"]

@@ -131,7 +131,8 @@ __device__ __forceinline__ void block_reduce_store(double v[ARN_CHUNK], int n, d
 }
 
 // out_sh[c] = sum over blocks b of part[b * stride + c], c < ncol, identical in every block:
-// ARN_SUB threads per column sum a fixed stride of blocks, then a fixed shuffle tree.
+// ARN_SUB threads per column sum a fixed stride of blocks (eight loads issued together, then
+// added in order), then a fixed shuffle tree.
 __device__ __forceinline__ void reduce_cols(const double* part, int nb, int stride, int ncol, double* out_sh,
                                             double (*sh)[ARN_MAXCOL]) {
     const int sub = threadIdx.x % ARN_SUB;
@@ -139,17 +140,16 @@ __device__ __forceinline__ void reduce_cols(const double* part, int nb, int stri
         const int c = c0 + threadIdx.x / ARN_SUB;
         double v = 0.0;
         if (c < ncol) {
-            // four independent chains (loads in flight together), combined in a fixed order
-            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-            int b = sub;
-            for (; b + 3 * ARN_SUB < nb; b += 4 * ARN_SUB) {
-                v0 += __ldcg(part + (size_t)b * stride + c);   // other blocks' data: L2
-                v1 += __ldcg(part + (size_t)(b + ARN_SUB) * stride + c);
-                v2 += __ldcg(part + (size_t)(b + 2 * ARN_SUB) * stride + c);
-                v3 += __ldcg(part + (size_t)(b + 3 * ARN_SUB) * stride + c);
+            for (int b0 = sub; b0 < nb; b0 += 8 * ARN_SUB) {
+                double x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int b = b0 + u * ARN_SUB;
+                    x[u] = b < nb ? __ldcg(part + (size_t)b * stride + c) : 0.0;   // other blocks' data: L2
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v += x[u];
             }
-            for (; b < nb; b += ARN_SUB) v0 += __ldcg(part + (size_t)b * stride + c);
-            v = (v0 + v1) + (v2 + v3);
         }
         for (int o = ARN_SUB / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, ARN_SUB);
         if (sub == 0 && c < ncol) out_sh[c] = v;
@@ -267,14 +267,18 @@ __device__ __forceinline__ void arn_half1(int j, int64_t K0, int64_t k0, int64_t
     slice_dots(V, w, K0, k0, k1, j + 1, 1, partB_blk, sh);
 }
 
-// Second half: h2 and w1.w1; h_{j+1,j}; Hessenberg column j and the flags (block 0); unless the
-// process ends (breakdown or j + 1 = m): v_{j+1}, the next product into wn and the next step's
-// first sweep into partA.  Returns whether the process continues (the same in every block).
+// Second half: h2 and w1.w1; h_{j+1,j}; Hessenberg column j (into this block's copy Hs, and by
+// block 0 into H with the flags); unless the process ends (breakdown or j + 1 = m): v_{j+1},
+// the next product into wn and the next step's first sweep into partA.  Returns whether the
+// process continues (the same in every block).  Hs is the block's shared copy of H (row
+// stride ARN_HLD), complete up to column j - 1 on entry.
+constexpr int ARN_HLD = 41;   // row stride of the shared Hessenberg copy (m <= 40)
 __device__ __forceinline__ bool arn_half2(int j, int m, int64_t K0, int64_t k0, int64_t k1, int nb, int stride,
                                           int NF, const double* __restrict__ bsr, const int* __restrict__ nbr,
                                           const double* __restrict__ dt, double* V, const double* w1, double* wn,
-                                          double* H, const double* partB, double* partA_blk, const double* h1,
-                                          double* h2, double* cs, DevScalars* sc, double (*sh)[ARN_MAXCOL]) {
+                                          double* H, double* Hs, const double* partB, double* partA_blk,
+                                          const double* h1, double* h2, double* cs, DevScalars* sc,
+                                          double (*sh)[ARN_MAXCOL]) {
     reduce_cols(partB, nb, stride, j + 2, h2, sh);
     double hh = 0.0;
     for (int i = 0; i <= j; ++i) hh += h2[i] * h2[i];
@@ -291,23 +295,27 @@ __device__ __forceinline__ bool arn_half2(int j, int m, int64_t K0, int64_t k0, 
         if (brk) sc->broken = 1;
     }
     if (brk || j + 1 == m) return false;   // uniform: every block reduced the same values
+    for (int i = threadIdx.x; i <= j + 1; i += ARN_THREADS) Hs[i * ARN_HLD + j] = i <= j ? h1[i] + h2[i] : hn;
+    __syncthreads();
     const double ih = 1.0 / hn;
-    // c = H~_j h2 over l = 0..j+1 (column j from this step's values, the others from H)
+    // c = H~_j h2 over l = 0..j+1
     for (int l = threadIdx.x; l <= j + 1; l += ARN_THREADS) {
         double c = 0.0;
-        for (int i = (l > 0 ? l - 1 : 0); i < j; ++i) c += __ldcg(H + (size_t)l * m + i) * h2[i];
-        c += (l <= j ? h1[l] + h2[l] : hn) * h2[j];
+        for (int i = (l > 0 ? l - 1 : 0); i <= j; ++i) c += Hs[l * ARN_HLD + i] * h2[i];
         cs[l] = c;
     }
     __syncthreads();
     double* vn = V + (size_t)(j + 1) * K0;
     for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
         double s = w1[k];
-        for (int i = 0; i <= j; ++i) s -= h2[i] * V[(size_t)i * K0 + k];
+        double t = a_row(k, NF, bsr, nbr, dt, w1);
+        for (int i = 0; i <= j; ++i) {
+            const double vi = V[(size_t)i * K0 + k];
+            s -= h2[i] * vi;
+            t -= cs[i] * vi;
+        }
         const double v = s * ih;
         vn[k] = v;
-        double t = a_row(k, NF, bsr, nbr, dt, w1);
-        for (int l = 0; l <= j; ++l) t -= cs[l] * V[(size_t)l * K0 + k];
         t -= cs[j + 1] * v;
         wn[k] = t * ih;
     }
@@ -326,6 +334,7 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
                                                          int stride, GridBar* bar, long long budget, DevScalars* sc) {
     __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
     __shared__ double h1[ARN_MAXCOL], h2[ARN_MAXCOL], cs[ARN_MAXCOL], red[8];
+    __shared__ double Hs[(ARN_HLD + 1) * ARN_HLD];
     __shared__ int s_ok;
     unsigned epoch = 0;   // barriers passed (thread 0's copy is the one used)
     const unsigned nb = gridDim.x;
@@ -362,7 +371,7 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
         arn_half1(j, K0, k0, k1, (int)nb, stride, V, w, partA, partB + (size_t)blockIdx.x * stride, h1, sh);
         if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
         if (!arn_half2(j, m, K0, k0, k1, (int)nb, stride, NF, bsr, nbr, dt, V, w, wbuf + (size_t)((j + 1) & 1) * K0, H,
-                       partB, partA + (size_t)blockIdx.x * stride, h1, h2, cs, sc, sh))
+                       Hs, partB, partA + (size_t)blockIdx.x * stride, h1, h2, cs, sc, sh))
             break;
     }
 }
@@ -451,15 +460,21 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arn_half1(ArnArgs A, int j) {
 __global__ void __launch_bounds__(ARN_THREADS) k_arn_half2(ArnArgs A, int j) {
     __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
     __shared__ double h1[ARN_MAXCOL], h2[ARN_MAXCOL], cs[ARN_MAXCOL];
+    __shared__ double Hs[(ARN_HLD + 1) * ARN_HLD];
     if (*((volatile int*)&A.sc->broken)) return;
     int64_t k0, k1;
     arn_slice(A.K0, &k0, &k1);
     for (int i = threadIdx.x; i < j + 2; i += ARN_THREADS) h1[i] = __ldcg(A.hcol + i);
+    // columns 0..j-1 of H (written by earlier kernels)
+    for (int t = threadIdx.x; t < (j + 1) * j; t += ARN_THREADS) {
+        const int r = t / (j > 0 ? j : 1), cc = t % (j > 0 ? j : 1);
+        Hs[r * ARN_HLD + cc] = __ldcg(A.H + (size_t)r * A.m + cc);
+    }
     __syncthreads();
     const double* w1 = A.wbuf + (size_t)(j & 1) * A.K0;
     double* wn = A.wbuf + (size_t)((j + 1) & 1) * A.K0;
-    arn_half2(j, A.m, A.K0, k0, k1, (int)gridDim.x, A.stride, A.NF, A.bsr, A.nbr, A.dt, A.V, w1, wn, A.H, A.partB,
-              A.partA + (size_t)blockIdx.x * A.stride, h1, h2, cs, A.sc, sh);
+    arn_half2(j, A.m, A.K0, k0, k1, (int)gridDim.x, A.stride, A.NF, A.bsr, A.nbr, A.dt, A.V, w1, wn, A.H, Hs,
+              A.partB, A.partA + (size_t)blockIdx.x * A.stride, h1, h2, cs, A.sc, sh);
 }
 
 // Self-test of the bounded wait: one block waits at a barrier sized for two blocks, so

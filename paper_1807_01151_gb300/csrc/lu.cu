@@ -87,6 +87,72 @@ __global__ void __launch_bounds__(256) k_lu(int E, T* __restrict__ blk, int* __r
     }
 }
 
+// The same factorisation for blocks that do not fit in shared memory (B = 175 in float64):
+// the block is factored in place in global memory (it stays in L2 while its CTA works on it),
+// row-major during the elimination, then transposed in place to the column-major layout the
+// substitutions read.  Pivot choice and tie rule as in k_lu.
+template <int B, class T>
+__global__ void __launch_bounds__(256) k_lu_gmem(int E, T* __restrict__ blk, int* __restrict__ piv) {
+    __shared__ int s_piv;
+    const int e = blockIdx.x;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    T* a = blk + (size_t)e * B * B;
+    for (int k = 0; k < B; ++k) {
+        if (tid < 32) {
+            T best = (T)-1;
+            int bi = k;
+            for (int r = k + tid; r < B; r += 32) {
+                const T v = fabs(a[(size_t)r * B + k]);
+                if (v > best) {
+                    best = v;
+                    bi = r;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (tid == 0) {
+                s_piv = bi;
+                piv[(size_t)e * B + k] = bi;
+            }
+        }
+        __syncthreads();
+        const int pr = s_piv;
+        if (pr != k)
+            for (int cc = tid; cc < B; cc += nth) {
+                const T t0 = a[(size_t)k * B + cc];
+                a[(size_t)k * B + cc] = a[(size_t)pr * B + cc];
+                a[(size_t)pr * B + cc] = t0;
+            }
+        __syncthreads();
+        if (k + 1 + tid < B) {
+            const T inv = (T)1 / a[(size_t)k * B + k];
+            for (int r = k + 1 + tid; r < B; r += nth) a[(size_t)r * B + k] *= inv;
+        }
+        __syncthreads();
+        const int tx = tid & 31, ty = tid >> 5;
+        for (int r = k + 1 + ty; r < B; r += 8) {
+            const T l = a[(size_t)r * B + k];
+            for (int cc = k + 1 + tx; cc < B; cc += 32) a[(size_t)r * B + cc] -= l * a[(size_t)k * B + cc];
+        }
+        __syncthreads();
+    }
+    // row-major -> column-major, in place
+    for (int t = tid; t < B * B; t += nth) {
+        const int r = t / B, cc = t % B;
+        if (r < cc) {
+            const T t0 = a[(size_t)r * B + cc];
+            a[(size_t)r * B + cc] = a[(size_t)cc * B + r];
+            a[(size_t)cc * B + r] = t0;
+        }
+    }
+}
+
 template <int B, class T>
 __global__ void __launch_bounds__(128) k_stage(int E, const T* __restrict__ lu, const int* __restrict__ piv,
                                                const double* __restrict__ r, const double* __restrict__ un,
@@ -326,8 +392,10 @@ static emg_status lu_dispatch(emg_ctx* c, int B, T* blk, int* piv) {
     case BB: {                                                                                               \
         const size_t sm = LuCfg<BB, T>::SMEM;                                                                \
         if (sm > 227 * 1024) {                                                                               \
-            c->err = "block of size " #BB " does not fit in shared memory in this precision";                \
-            return EMG_ERR_ARG;                                                                              \
+            ProfScope _ps(c, PC_LU);                                                                         \
+            k_lu_gmem<BB, T><<<E, 256, 0, c->stream>>>((int)E, blk, piv);                                   \
+            EMG_CHECK_LAUNCH(c);                                                                             \
+            return EMG_OK;                                                                                   \
         }                                                                                                    \
         EMG_CUDA_TRY(c, cudaFuncSetAttribute(k_lu<BB, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
         {                                                                                                    \

@@ -90,7 +90,12 @@ def stage_bytes(s):
     return s.E * (s.B * s.B * 8 + 3 * s.B * 8 + s.B * 4)
 
 
-def vcycle_work(dim, p_max, E, F, rk_stages=4, pre_smooth=2, krylov_m=30):
+def inverse_flops(s):
+    """Explicit inverse by Gauss-Jordan (the float32 block forms): 2 B^3 per block."""
+    return s.E * 2.0 * s.B ** 3
+
+
+def vcycle_work(dim, p_max, E, F, rk_stages=4, pre_smooth=2, krylov_m=30, form=0):
     """Per-V-cycle algorithmic FLOPs and compulsory bytes of each kernel class."""
     w = {k: [0.0, 0.0] for k in ("residual_face_flux", "residual_volume", "diag_block_assembly", "block_lu",
                                  "prk_stage_solve", "arnoldi")}
@@ -109,7 +114,7 @@ def vcycle_work(dim, p_max, E, F, rk_stages=4, pre_smooth=2, krylov_m=30):
         if p > 0:
             w["diag_block_assembly"][0] += pre_smooth * diag_flops(s)
             w["diag_block_assembly"][1] += pre_smooth * diag_bytes(s)
-            w["block_lu"][0] += pre_smooth * lu_flops(s)
+            w["block_lu"][0] += pre_smooth * (lu_flops(s) if form == 0 else inverse_flops(s))
             w["block_lu"][1] += pre_smooth * 2 * diag_bytes(s)
             w["prk_stage_solve"][0] += pre_smooth * rk_stages * stage_flops(s)
             w["prk_stage_solve"][1] += pre_smooth * rk_stages * stage_bytes(s)

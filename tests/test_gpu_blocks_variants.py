@@ -234,3 +234,23 @@ def test_probe_peaks_are_plausible():
     r64 = pk["fp64_tflops"] / (2 * 2 * 152 * pk["sm_mhz"] * 1e-6)
     r32 = pk["fp32_tflops"] / (128 * 2 * 152 * pk["sm_mhz"] * 1e-6)
     assert 0.7 < r64 < 1.02 and 0.7 < r32 < 1.02, (r64, r32, pk)
+
+
+def test_fp64_form_at_3d_p4():
+    """The plain FP64 form at 3-D p = 4 (175 x 175 float64 blocks, larger than shared memory:
+    factored in global memory): the PRK step and one V-cycle against the oracle."""
+    import paper_1807_01151_gb300 as pkg
+    name, mk, p = BLOCK_CASES[2]
+    desc, dg, u, D = oracle_case(name, mk, p)
+    s = pkg.Solver(desc, p_max=p)
+    for cfl in (3.0, 100.0):
+        ug = s.prk_step(p, u, cfl=cfl)
+        dt = oemg.dtau(dg, p, u, cfl)
+        P = np.eye(D.shape[-1])[None] / dt[:, None, None] - D
+        uo = oemg.prk_step(lambda w: dg.residual(p, w), P, u)
+        assert rel_err(ug - u, uo - u) < TOL_CYCLE, (cfl, rel_err(ug - u, uo - u))
+    s.set_state(np.ascontiguousarray(u))
+    s.vcycle()
+    uo, _ = oemg.vcycle(dg, u, 1)
+    assert rel_err(s.get_state(), uo) < TOL_CYCLE
+    s.close()
