@@ -579,8 +579,10 @@ __global__ void __cluster_dims__(PHI_CLUSTER, 1, 1)
     }
     __syncthreads();
     const double theta13 = 5.371920351148152;
+    // squarings: a non-finite norm (the Krylov data are not finite) takes none, and the count
+    // is capped (2^-1100 underflows every double)
     int s = 0;
-    if (s_norm > theta13) s = (int)ceil(log2(s_norm / theta13));
+    if (isfinite(s_norm) && s_norm > theta13) s = (int)fmin(ceil(log2(s_norm / theta13)), 1100.0);
     const double sc2 = ldexp(1.0, -s);
     for (int t = threadIdx.x; t < nn; t += blockDim.x) M[t] *= sc2;
     __syncthreads();

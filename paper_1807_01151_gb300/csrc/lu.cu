@@ -17,6 +17,20 @@
 
 namespace emg {
 
+// Pivot magnitude as an ordered integer key: the IEEE bits of |x| order like its value for
+// every finite or infinite x; a NaN gets -1, so it never wins against a number.  Comparing
+// keys as integers keeps the pivot search deterministic and independent of how the compiler
+// treats float comparisons with NaN (where every thread of a warp computes the pivot on its
+// own, a disagreement would break the permutation).
+__device__ __forceinline__ int piv_key(float x) {
+    const unsigned b = __float_as_uint(x) & 0x7fffffffu;
+    return b <= 0x7f800000u ? (int)b : -1;
+}
+__device__ __forceinline__ long long piv_key(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    return b <= 0x7ff0000000000000ull ? (long long)b : -1ll;
+}
+
 template <int B, class T>
 struct LuCfg {
     static constexpr int LD = B + 1;                 // padded row stride in shared memory
@@ -36,17 +50,17 @@ __global__ void __launch_bounds__(256) k_lu(int E, T* __restrict__ blk, int* __r
     __syncthreads();
     for (int k = 0; k < B; ++k) {
         if (tid < 32) {
-            T best = (T)-1;
+            auto best = piv_key((T)0) - 1;   // every key is >= -1: a NaN row is taken only if no row is a number
             int bi = k;
             for (int r = k + tid; r < B; r += 32) {
-                const T v = fabs(a[r * LD + k]);
+                const auto v = piv_key(a[r * LD + k]);
                 if (v > best) {
                     best = v;
                     bi = r;
                 }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const auto ob = __shfl_xor_sync(0xffffffffu, best, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ob > best || (ob == best && oi < bi)) {
                     best = ob;
@@ -99,17 +113,17 @@ __global__ void __launch_bounds__(256) k_lu_gmem(int E, T* __restrict__ blk, int
     T* a = blk + (size_t)e * B * B;
     for (int k = 0; k < B; ++k) {
         if (tid < 32) {
-            T best = (T)-1;
+            auto best = piv_key((T)0) - 1;
             int bi = k;
             for (int r = k + tid; r < B; r += 32) {
-                const T v = fabs(a[(size_t)r * B + k]);
+                const auto v = piv_key(a[(size_t)r * B + k]);
                 if (v > best) {
                     best = v;
                     bi = r;
                 }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const auto ob = __shfl_xor_sync(0xffffffffu, best, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 if (ob > best || (ob == best && oi < bi)) {
                     best = ob;
@@ -264,13 +278,13 @@ __global__ void __launch_bounds__(256) k_gj_tile(int E, float* __restrict__ blk)
         }
         __syncthreads();
         // (2) every warp: the pivot row p among the unused rows
-        float best = -1.0f;
+        int best = -1;
         int bi = B;
 #pragma unroll
         for (int m = 0; m < MW; ++m) {
             const int r = tx + 32 * m;
             if (r < B && !((used[m] >> tx) & 1u)) {
-                const float v = fabsf(ck[r]);
+                const int v = piv_key(ck[r]);
                 if (v > best) {
                     best = v;
                     bi = r;
@@ -279,7 +293,7 @@ __global__ void __launch_bounds__(256) k_gj_tile(int E, float* __restrict__ blk)
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int ob = __shfl_xor_sync(0xffffffffu, best, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ob > best || (ob == best && oi < bi)) {
                 best = ob;
@@ -479,7 +493,7 @@ __global__ void __launch_bounds__(32 * W) k_gj_cols(int E, float* __restrict__ b
         if (w == wk) {
             // (1) column k (then zeroed: in-place scheme), pivot among the unused rows
             float v[RS];
-            float best = -1.0f;
+            int best = -1;
             int bi = B, lo = B;
 #pragma unroll
             for (int i = 0; i < RS; ++i) {
@@ -493,7 +507,7 @@ __global__ void __launch_bounds__(32 * W) k_gj_cols(int E, float* __restrict__ b
                 v[i] = x;
                 const int r = tx + 32 * i;
                 if (r < B && !((used >> i) & 1u)) {
-                    const float m = fabsf(x);
+                    const int m = piv_key(x);
                     if (m > best) {
                         best = m;
                         bi = r;
@@ -503,7 +517,7 @@ __global__ void __launch_bounds__(32 * W) k_gj_cols(int E, float* __restrict__ b
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int ob = __shfl_xor_sync(0xffffffffu, best, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                 const int ol = __shfl_xor_sync(0xffffffffu, lo, o);
                 if (ob > best || (ob == best && oi < bi)) {
@@ -601,7 +615,7 @@ __global__ void __launch_bounds__(32 * W) k_gj_rot(int E, float* __restrict__ bl
             if (w == wk) {
                 // (1) column k is slot 0 of this warp; zero it (in-place scheme) and pivot
                 float v[RS];
-                float best = -1.0f;
+                int best = -1;
                 int bi = B, lo = B;
 #pragma unroll
                 for (int i = 0; i < RS; ++i) {
@@ -609,7 +623,7 @@ __global__ void __launch_bounds__(32 * W) k_gj_rot(int E, float* __restrict__ bl
                     a[i][0] = 0.0f;
                     const int r = tx + 32 * i;
                     if (r < B && !((used >> i) & 1u)) {
-                        const float m = fabsf(v[i]);
+                        const int m = piv_key(v[i]);
                         if (m > best) {
                             best = m;
                             bi = r;
@@ -619,7 +633,7 @@ __global__ void __launch_bounds__(32 * W) k_gj_rot(int E, float* __restrict__ bl
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int ob = __shfl_xor_sync(0xffffffffu, best, o);
                     const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                     const int ol = __shfl_xor_sync(0xffffffffu, lo, o);
                     if (ob > best || (ob == best && oi < bi)) {
@@ -811,13 +825,13 @@ __global__ void __launch_bounds__(128) k_gj_tc(int E, float* __restrict__ blk, i
 #pragma unroll
             for (int j = 0; j < KB; ++j) {
                 if (j >= kw) break;
-                float best = -1.f;
+                int best = -1;
                 int bi = B, lo = B;
 #pragma unroll
                 for (int i = 0; i < RI; ++i) {
                     const int r = lane + 32 * i;
                     if (r < B && !((used >> i) & 1u)) {
-                        const float m = fabsf(pr[i][j]);
+                        const int m = piv_key(pr[i][j]);
                         if (m > best) {
                             best = m;
                             bi = r;
@@ -827,7 +841,7 @@ __global__ void __launch_bounds__(128) k_gj_tc(int E, float* __restrict__ blk, i
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+                    const int ob = __shfl_xor_sync(0xffffffffu, best, o);
                     const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
                     const int ol = __shfl_xor_sync(0xffffffffu, lo, o);
                     if (ob > best || (ob == best && oi < bi)) {
@@ -836,7 +850,8 @@ __global__ void __launch_bounds__(128) k_gj_tc(int E, float* __restrict__ blk, i
                     }
                     lo = ol < lo ? ol : lo;
                 }
-                const int p = bi < B ? bi : lo;   // lowest unused row if the column is not finite
+                // lowest unused row if the column is not finite; lane 0's choice for the whole warp
+                const int p = __shfl_sync(0xffffffffu, bi < B ? bi : lo, 0);
                 const int pl = p & 31, pi = p >> 5;
                 float prow[16];
 #pragma unroll
@@ -957,7 +972,8 @@ __global__ void __launch_bounds__(128) k_gj_tc(int E, float* __restrict__ blk, i
 #pragma unroll
         for (int rt = 0; rt < RT; ++rt) tc::st16(tbase + lane_base + (uint32_t)(rt * NC + k0), pv[rt]);
         tc::fence_before();
-        if (__syncthreads_or(failed)) break;
+        failed = __syncthreads_or(failed) != 0;   // the same decision in every thread
+        if (failed) break;
         tc::fence_after();
     }
     if (failed) {

@@ -254,3 +254,22 @@ def test_fp64_form_at_3d_p4():
     uo, _ = oemg.vcycle(dg, u, 1)
     assert rel_err(s.get_state(), uo) < TOL_CYCLE
     s.close()
+
+
+@pytest.mark.parametrize("name,mk,p", BLOCK_CASES)
+@pytest.mark.parametrize("kernels", [1, 2])
+def test_inverse_of_non_finite_blocks_completes(name, mk, p, kernels):
+    """A state with NaN entries (a diverging solve) gives blocks with NaN entries: the
+    Gauss-Jordan forms must still pick one pivot row per step (the lowest unused row when a
+    column has no number), so the permutation stays whole, the call completes and the
+    context stays usable; the result is simply not finite."""
+    import paper_1807_01151_gb300 as pkg
+    desc, dg, u, D = oracle_case(name, mk, p)
+    s = pkg.Solver(desc, p_max=p, prec=1, block_kernels=kernels)
+    bad = u.copy()
+    bad[::3, :, :] = np.nan
+    X = s.block_operator(p, bad, cfl=3.0, which=1)
+    assert not np.isfinite(X[::3]).any()
+    Xg = s.block_operator(p, u, cfl=3.0, which=1)       # the context still works
+    assert np.isfinite(Xg).all()
+    s.close()
