@@ -102,7 +102,7 @@ typedef struct {
                               give bitwise the same result.  The event profiler, when on, uses
                               the kernel-by-kernel path. */
     int32_t autotune;      /* 1 (default): at creation, time the variants of the tuned kernels
-                              (FP32 Gauss-Jordan: pivot-loop unrolling) per block size on this
+                              (FP32 Gauss-Jordan: warps per block) per block size on this
                               device and use the fastest (cached per process); 0: the first
                               variant.  Variants compute identically: results do not change. */
     int32_t coop_krylov;   /* 1 (default): the Arnoldi process of the EXP1 step is one persistent
@@ -131,8 +131,11 @@ typedef struct {
                               0 (default): per level, the form this build measured faster;
                               1: the tensor-core forms (tcgen05: 3xTF32 assembly, blocked
                               Gauss-Jordan with rank-16 MMA updates for B = 75, 100, 175);
-                              2: the SIMT (FMA) forms.  The forms differ only in rounding; the
-                              BF16 form always assembles on the tensor cores. */
+                              2: the SIMT (FMA) forms (blocked Gauss-Jordan with rank-8
+                              updates where a thread's share fits 64 registers, else the
+                              unblocked column-owner form); 3: the SIMT forms with the
+                              unblocked Gauss-Jordan everywhere.  The forms differ only in
+                              rounding; the BF16 form always assembles on the tensor cores. */
 } emg_params;
 
 typedef struct {

@@ -388,7 +388,8 @@ emg_status emg_create_mesh(const emg_mesh_desc* m, const emg_params* prm, emg_ct
     if (prm->jac_freeze < 0) return fail(c, EMG_ERR_ARG, "jac_freeze must be >= 1");
     if (prm->quad_extra != 0 && prm->quad_extra != 2)
         return fail(c, EMG_ERR_ARG, "only the rule q = p + 2 is built (quad_extra 2)");
-    if (prm->block_kernels < 0 || prm->block_kernels > 2) return fail(c, EMG_ERR_ARG, "block_kernels must be 0, 1 or 2");
+    if (prm->block_kernels < 0 || prm->block_kernels > 3)
+        return fail(c, EMG_ERR_ARG, "block_kernels must be 0, 1, 2 or 3");
     if (prm->omega[0] != 0.0 || prm->omega[1] != 0.0 || prm->omega[2] != 0.0)
         return fail(c, EMG_ERR_ARG, "only the absolute frame (omega = 0) is built");
     c->p_max = prm->p_max;

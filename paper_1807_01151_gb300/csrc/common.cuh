@@ -36,7 +36,7 @@ inline bool use_tc_assembly(int dim, int p, int prec, int block_kernels) {
 }
 inline bool use_tc_inverse(int B, int block_kernels) {
     const bool built = B == 75 || B == 100 || B == 175;
-    if (!built || block_kernels == 2) return false;
+    if (!built || block_kernels >= 2) return false;
     if (block_kernels == 1) return true;
     return B == 100;
 }

@@ -1,0 +1,450 @@
+// Explicit inverses P_e^{-1} of the float32 block forms by Gauss-Jordan elimination with
+// partial pivoting (SIMT forms), their variants and the per-device tuner.  The tensor-core
+// form is in gj_tc.cu.
+#include <algorithm>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "blocks.cuh"
+#include "common.cuh"
+#include "gj.cuh"
+
+namespace emg {
+
+emg_status launch_gj_tc(emg_ctx* c, int B, float* blk, bool* built);
+
+// Blocked form of the same Gauss-Jordan inversion (right-looking, panels of NB = 8 pivot
+// columns), SIMT.  Layout of k_gj_cols: lane tx owns rows tx + 32 i, warp w owns columns
+// w + W j; after every panel each thread rotates its column slots by NB / W, so the next
+// panel's columns always sit in slots 0 .. NB/W - 1 (no runtime-indexed register access).
+// The NB steps of a panel act on every column c outside it as A[:, c] <- T A[:, c],
+// T = T_{k0+NB-1} ... T_{k0} (T_k: the elementary Gauss-Jordan transform of step k, identity
+// but for column p_k).  T differs from I only in the pivot-row columns P, and the in-place
+// rule leaves exactly F = T[:, P] in the panel's columns once the panel is factored, so
+//   rows r outside P:  A[r, c] <- A[r, c] + sum_s F[r, s] A[p_s, c]
+//   rows r = p_t in P: A[r, c] <-           sum_s F[r, s] A[p_s, c]
+// (writing the second case without "A[r, c] +" avoids forming T[p_t, p_t] - 1 in float).
+// Per panel: (A) the panel's owners copy its columns to shared memory; (B) warp 0 alone
+// factors the panel in registers (the in-place steps of k_gj_rot on B x NB values: pivot
+// search by warp reductions, the pivot row by shuffles: no block barrier inside) and
+// publishes F and the pivot rows; (C) every warp gathers the pivot rows' entries of its own
+// columns in a warp-private buffer (no block barrier) and applies the rank-NB update,
+// s = 0 .. NB-1 in order, one FMA per term.  Pivot choice and tie rule are those of the
+// kernels above (largest |a_rk| among the unused rows, lowest row on ties, the lowest unused
+// row if no candidate is a number).  The summation order differs from the unblocked forms
+// (results agree to float rounding, not bitwise); the variants with different W compute
+// identically.  The inverse is written column-major, as by the other forms.
+template <int B, int W>
+struct GjBlk {
+    static constexpr int NB = 8;                        // panel width
+    static constexpr int SPW = NB / W;                  // panel columns per warp and panel
+    static constexpr int RS = (B + 31) / 32;            // row slots per lane
+    static constexpr int R32 = 32 * RS;
+    static constexpr int NP = (B + NB - 1) / NB;        // panels
+    static constexpr int CS = NP * SPW;                 // column slots per thread
+    static constexpr int PLD = NB + 1;                  // row stride of the panel buffers
+    static constexpr int YN = CS - SPW;                 // non-panel slots per thread
+    static constexpr int YL = YN > 0 ? ((YN + 3) / 4) * 4 : 4;
+    static constexpr int LD = (B % 2) ? B + 2 : B + 1;  // row stride of the staging tile
+    static constexpr size_t TILE = (size_t)B * LD * sizeof(float);
+    static constexpr size_t WORK = (size_t)(2 * R32 * PLD + W * NB * YL) * sizeof(float);
+    static constexpr size_t SMEM = ((TILE > WORK ? TILE : WORK) + 15) / 16 * 16;
+    static constexpr bool VALID = (NB % W == 0) && RS * CS <= 64;
+};
+
+template <int B, int W>
+__global__ void __launch_bounds__(32 * W) k_gj_blk(int E, float* __restrict__ blk) {
+    using G = GjBlk<B, W>;
+    constexpr int NB = G::NB, SPW = G::SPW, RS = G::RS, R32 = G::R32, NP = G::NP, CS = G::CS;
+    constexpr int PLD = G::PLD, YL = G::YL, LD = G::LD, T = 32 * W;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float* tile = reinterpret_cast<float*>(smraw);      // staging (load and store only)
+    float* Pn = tile;                                   // panel columns [R32][PLD]
+    float* Fs = tile + R32 * PLD;                       // factored panel F [R32][PLD]
+    float* Yw = tile + 2 * R32 * PLD;                   // pivot rows, per warp [W][NB][YL]
+    __shared__ int perm[B], invp[B];
+    __shared__ int s_piv[NB];
+    const int e = blockIdx.x;
+    const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float* g = blk + (size_t)e * B * B;
+    for (int t = threadIdx.x; t < B * B; t += T) tile[(t / B) * LD + (t % B)] = g[t];
+    __syncthreads();
+    float a[RS][CS];
+#pragma unroll
+    for (int i = 0; i < RS; ++i)
+#pragma unroll
+        for (int j = 0; j < CS; ++j) {
+            const int r = tx + 32 * i, c = w + W * j;
+            a[i][j] = (r < B && c < B) ? tile[r * LD + c] : 0.0f;
+        }
+    unsigned used = 0u;   // warp 0: bit i set once row tx + 32 i has been a pivot row
+    float* yw = Yw + (size_t)w * NB * YL;
+#pragma unroll 1
+    for (int t = 0; t < NP; ++t) {
+        const int k0 = t * NB;
+        const int nb = (B - k0) < NB ? (B - k0) : NB;
+        __syncthreads();   // the previous panel's F and the staging tile are no longer read
+        // (A) the panel's columns k0 + w + W s (slots s < SPW) to the panel buffer
+#pragma unroll
+        for (int s = 0; s < SPW; ++s)
+#pragma unroll
+            for (int i = 0; i < RS; ++i) Pn[(tx + 32 * i) * PLD + w + W * s] = a[i][s];
+        __syncthreads();
+        // (B) warp 0 factors the panel
+        if (w == 0) {
+            float x[RS][NB];
+#pragma unroll
+            for (int i = 0; i < RS; ++i)
+#pragma unroll
+                for (int c = 0; c < NB; ++c) x[i][c] = Pn[(tx + 32 * i) * PLD + c];
+#pragma unroll
+            for (int s = 0; s < NB; ++s) {
+                if (s >= nb) break;   // uniform
+                // pivot: the largest key among the unused rows (key + 1, so a NaN row is 0)
+                unsigned km = 0u;
+#pragma unroll
+                for (int i = 0; i < RS; ++i) {
+                    const int r = tx + 32 * i;
+                    const unsigned kk = (r < B && !((used >> i) & 1u)) ? (unsigned)(piv_key(x[i][s]) + 1) : 0u;
+                    km = kk > km ? kk : km;
+                }
+                km = __reduce_max_sync(0xffffffffu, km);
+                int rl = B;
+#pragma unroll
+                for (int i = 0; i < RS; ++i) {
+                    const int r = tx + 32 * i;
+                    const bool cand = r < B && !((used >> i) & 1u) &&
+                                      (unsigned)(piv_key(x[i][s]) + 1) == km;
+                    if (cand && r < rl) rl = r;
+                }
+                // lowest row holding the largest key; with km = 0 (no row is a number) every
+                // unused row qualifies: the lowest unused row
+                const int p = (int)__reduce_min_sync(0xffffffffu, (unsigned)rl);
+                const int pl = p & 31, pi = p >> 5;
+                float rk[NB];
+#pragma unroll
+                for (int ii = 0; ii < RS; ++ii)
+                    if (pi == ii) {   // warp-uniform branch
+#pragma unroll
+                        for (int c = 0; c < NB; ++c) rk[c] = __shfl_sync(0xffffffffu, x[ii][c], pl);
+                    }
+                const float inv = 1.0f / rk[s];
+#pragma unroll
+                for (int c = 0; c < NB; ++c) rk[c] = (c == s) ? inv : rk[c] * inv;
+                float f[RS];
+#pragma unroll
+                for (int i = 0; i < RS; ++i) {
+                    f[i] = (tx + 32 * i == p) ? 0.0f : x[i][s];
+                    x[i][s] = 0.0f;
+                }
+#pragma unroll
+                for (int i = 0; i < RS; ++i)
+#pragma unroll
+                    for (int c = 0; c < NB; ++c) x[i][c] -= f[i] * rk[c];
+                if (tx == pl) {
+                    used |= 1u << pi;
+#pragma unroll
+                    for (int ii = 0; ii < RS; ++ii)
+                        if (pi == ii) {
+#pragma unroll
+                            for (int c = 0; c < NB; ++c) x[ii][c] = rk[c];
+                        }
+                }
+                if (tx == 0) {
+                    perm[k0 + s] = p;
+                    s_piv[s] = p;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < RS; ++i)
+#pragma unroll
+                for (int c = 0; c < NB; ++c) Fs[(tx + 32 * i) * PLD + c] = x[i][c];
+        }
+        __syncthreads();
+        // (C) pivot rows of this warp's non-panel columns into the warp's buffer; the pivot
+        // rows' own entries are then cleared (they are rebuilt from F alone)
+        __syncwarp();
+        for (int s = 0; s < nb; ++s) {
+            const int p = s_piv[s];
+            const int pl = p & 31, pi = p >> 5;
+            if (tx == pl) {
+#pragma unroll
+                for (int ii = 0; ii < RS; ++ii)
+                    if (pi == ii) {
+#pragma unroll
+                        for (int j = SPW; j < CS; ++j) {
+                            yw[s * YL + (j - SPW)] = a[ii][j];
+                            a[ii][j] = 0.0f;
+                        }
+                    }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int s = 0; s < NB; ++s) {
+            if (s >= nb) break;   // uniform
+            float f[RS];
+#pragma unroll
+            for (int i = 0; i < RS; ++i) f[i] = Fs[(tx + 32 * i) * PLD + s];
+            const float* yr = yw + s * YL;
+#pragma unroll
+            for (int j0 = 0; j0 < CS - SPW; j0 += 4) {
+                const float4 y4 = *reinterpret_cast<const float4*>(yr + j0);
+                const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (j0 + q < CS - SPW) {
+#pragma unroll
+                        for (int i = 0; i < RS; ++i) a[i][SPW + j0 + q] = fmaf(f[i], yv[q], a[i][SPW + j0 + q]);
+                    }
+            }
+        }
+        // the panel's own columns become F
+#pragma unroll
+        for (int s = 0; s < SPW; ++s)
+#pragma unroll
+            for (int i = 0; i < RS; ++i) a[i][s] = Fs[(tx + 32 * i) * PLD + w + W * s];
+        // rotate the column slots by SPW: the next panel's columns move to slots 0 .. SPW-1
+#pragma unroll
+        for (int i = 0; i < RS; ++i) {
+            float t0[SPW];
+#pragma unroll
+            for (int s = 0; s < SPW; ++s) t0[s] = a[i][s];
+#pragma unroll
+            for (int j = 0; j < CS - SPW; ++j) a[i][j] = a[i][j + SPW];
+#pragma unroll
+            for (int s = 0; s < SPW; ++s) a[i][CS - SPW + s] = t0[s];
+        }
+    }
+    // NP rotations by SPW = CS slots: every column is back in its own slot
+    __syncthreads();
+    for (int t = threadIdx.x; t < B; t += T) invp[perm[t]] = t;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RS; ++i)
+#pragma unroll
+        for (int j = 0; j < CS; ++j) {
+            const int r = tx + 32 * i, c = w + W * j;
+            if (r < B && c < B) tile[perm[c] * LD + invp[r]] = a[i][j];
+        }
+    __syncthreads();
+    for (int t = threadIdx.x; t < B * B; t += T) g[t] = tile[(t / B) * LD + (t % B)];
+}
+
+// ---- variants of the FP32 Gauss-Jordan kernel and their tuning --------------------------------
+// Two families.  Unblocked (variants 0..13): variant v < 4 unrolls the pivot loop kGjUnroll[v]
+// times (0 = fully, only for B <= 100); 4..8 are the column-owner form with kGjWarps[v - 4]
+// warps per element (valid while a thread's share of the block stays at most 128 values);
+// 9..13 the rotating column-owner form with kGjWarps[v - 9] warps.  Blocked (14..17):
+// k_gj_blk with kGjBlkWarps[v - 14] warps (valid while a thread holds at most 64 values).
+// Within a family the variants do the same arithmetic in the same order, so the tuner's choice
+// never changes a result; the tuner times one family only (the blocked one where it is valid,
+// unless emg_params.block_kernels asks for the unblocked forms).
+constexpr int kGjUnroll[] = {1, 4, 16, 0};
+constexpr int kGjWarps[] = {1, 2, 4, 8, 16};
+constexpr int kGjBlkWarps[] = {1, 2, 4, 8};
+constexpr int kGjBlkFirst = 14;
+constexpr int kGjVariants = 18;
+
+template <int B, int W>
+constexpr bool gj_blk_valid() {
+    return GjBlk<B, W>::VALID;
+}
+
+template <int B>
+static bool gj_variant_valid(int v) {
+    if (v < 0 || v >= kGjVariants) return false;
+    if (v < 4) return kGjUnroll[v] != 0 || B <= 100;
+    if (v >= kGjBlkFirst) {
+        switch (kGjBlkWarps[v - kGjBlkFirst]) {
+            case 1: return gj_blk_valid<B, 1>();
+            case 2: return gj_blk_valid<B, 2>();
+            case 4: return gj_blk_valid<B, 4>();
+            default: return gj_blk_valid<B, 8>();
+        }
+    }
+    const int W = kGjWarps[(v - 4) % 5];
+    return ((B + 31) / 32) * ((B + W - 1) / W) <= 128;
+}
+
+static std::string gj_variant_name(int v) {
+    if (v < 4) return "tile unroll " + std::to_string(kGjUnroll[v]);
+    if (v >= kGjBlkFirst) return "blocked " + std::to_string(kGjBlkWarps[v - kGjBlkFirst]) + " warps";
+    return std::string(v < 9 ? "cols " : "rotating cols ") + std::to_string(kGjWarps[(v - 4) % 5]) + " warps";
+}
+
+template <int B, int W>
+static cudaError_t gj_blk_go(unsigned E, float* blk, cudaStream_t st) {
+    if constexpr (GjBlk<B, W>::VALID) {
+        const size_t sm = GjBlk<B, W>::SMEM;
+        cudaError_t e = cudaFuncSetAttribute(k_gj_blk<B, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_gj_blk<B, W><<<E, 32 * W, sm, st>>>((int)E, blk);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;   // not reached: gj_dispatch checks the variant first
+    }
+}
+
+template <int B>
+static cudaError_t gj_launch(int v, unsigned E, float* blk, cudaStream_t st) {
+    switch (v) {
+        case 14: return gj_blk_go<B, 1>(E, blk, st);
+        case 15: return gj_blk_go<B, 2>(E, blk, st);
+        case 16: return gj_blk_go<B, 4>(E, blk, st);
+        case 17: return gj_blk_go<B, 8>(E, blk, st);
+        case 9: return gj_rot_go<B, 1>(E, blk, st);
+        case 10: return gj_rot_go<B, 2>(E, blk, st);
+        case 11: return gj_rot_go<B, 4>(E, blk, st);
+        case 12: return gj_rot_go<B, 8>(E, blk, st);
+        case 13: return gj_rot_go<B, 16>(E, blk, st);
+        case 4: return gj_cols_go<B, 1>(E, blk, st);
+        case 5: return gj_cols_go<B, 2>(E, blk, st);
+        case 6: return gj_cols_go<B, 4>(E, blk, st);
+        case 7: return gj_cols_go<B, 8>(E, blk, st);
+        case 8: return gj_cols_go<B, 16>(E, blk, st);
+        case 1: return gj_go<B, 4>(E, blk, st);
+        case 2: return gj_go<B, 16>(E, blk, st);
+        case 3: return gj_go<B, (B <= 100 ? B : 1)>(E, blk, st);
+        default: return gj_go<B, 1>(E, blk, st);
+    }
+}
+
+static cudaError_t gj_dispatch(int B, int v, unsigned E, float* blk, cudaStream_t st, bool* ok) {
+    *ok = true;
+    switch (B) {
+#define EMG_GJ_CASE(BB) \
+    case BB:            \
+        return gj_variant_valid<BB>(v) ? gj_launch<BB>(v, E, blk, st) : gj_launch<BB>(0, E, blk, st);
+        EMG_BSIZES(EMG_GJ_CASE)
+#undef EMG_GJ_CASE
+        default:
+            *ok = false;
+            return cudaSuccess;
+    }
+}
+
+static bool gj_valid(int B, int v) {
+    switch (B) {
+#define EMG_GJ_CASE(BB) \
+    case BB:            \
+        return gj_variant_valid<BB>(v);
+        EMG_BSIZES(EMG_GJ_CASE)
+#undef EMG_GJ_CASE
+        default:
+            return false;
+    }
+}
+
+// Deterministic, diagonally dominant stand-in blocks for timing the variants.
+__global__ void k_fill_tuning_blocks(int64_t n, int B, float* __restrict__ blk) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * B * B) return;
+    const int c = (int)(t % B), r = (int)((t / B) % B);
+    const uint32_t h = (uint32_t)(t * 2654435761ull) ^ (uint32_t)(t >> 13);
+    blk[t] = (r == c ? (float)B : 0.0f) + ((float)(h & 0xffffu) / 65536.0f - 0.5f);
+}
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, bool>, int> g_gj_best;   // (device, B, unblocked asked) -> variant
+}  // namespace
+
+// Times every valid variant on min(E, 2048) stand-in blocks per block size of the FP32 levels
+// and keeps the fastest, once per (device, B) for the process.
+emg_status tune_gj(emg_ctx* c) {
+    if (!blocks_f32(c->prm.prec)) return EMG_OK;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (int p = 1; p <= c->p_max; ++p) {
+        LevelDev& L = c->lv[p];
+        const auto key = std::make_tuple(c->device, L.B, c->prm.block_kernels == 3);
+        // the family: blocked where a blocked variant is valid (unless the unblocked forms are
+        // asked for), else unblocked
+        bool blocked = false;
+        if (c->prm.block_kernels != 3)
+            for (int v = kGjBlkFirst; v < kGjVariants; ++v) blocked = blocked || gj_valid(L.B, v);
+        const int v_lo = blocked ? kGjBlkFirst : 0, v_hi = blocked ? kGjVariants : kGjBlkFirst;
+        if (!c->prm.autotune) {
+            L.gj_variant = 0;
+            for (int v = v_lo; v < v_hi; ++v)
+                if (gj_valid(L.B, v)) {
+                    L.gj_variant = v;
+                    break;
+                }
+            continue;
+        }
+        if (L.tc_gj) {
+            c->tuning += "gj B=" + std::to_string(L.B) + ": blocked tensor-core form (not tuned); ";
+            continue;
+        }
+        auto it = g_gj_best.find(key);
+        if (it != g_gj_best.end()) {
+            L.gj_variant = it->second;
+            c->tuning += "gj B=" + std::to_string(L.B) + ": " + gj_variant_name(it->second) +
+                         " (tuned earlier in this process); ";
+            continue;
+        }
+        const int64_t n = std::min<int64_t>(c->E, 2048);
+        float* scratch = nullptr;
+        EMG_CUDA_TRY(c, cudaMallocAsync((void**)&scratch, (size_t)n * L.B * L.B * sizeof(float), c->stream));
+        k_fill_tuning_blocks<<<(unsigned)((n * L.B * L.B + 255) / 256), 256, 0, c->stream>>>(n, L.B, scratch);
+        cudaEvent_t e0, e1;
+        EMG_CUDA_TRY(c, cudaEventCreate(&e0));
+        EMG_CUDA_TRY(c, cudaEventCreate(&e1));
+        int best = v_lo;
+        float best_ms = 1e30f;
+        std::string note = "gj B=" + std::to_string(L.B) + ":";
+        for (int v = v_lo; v < v_hi; ++v) {
+            if (!gj_valid(L.B, v)) continue;
+            bool ok = true;
+            float ms = 1e30f;
+            for (int rep = 0; rep < 3 && ok; ++rep) {
+                EMG_CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+                EMG_CUDA_TRY(c, gj_dispatch(L.B, v, (unsigned)n, scratch, c->stream, &ok));
+                EMG_CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+                EMG_CUDA_TRY(c, cudaEventSynchronize(e1));
+                float t = 0.0f;
+                EMG_CUDA_TRY(c, cudaEventElapsedTime(&t, e0, e1));
+                if (rep > 0) ms = std::min(ms, t);   // the first run warms up
+            }
+            char buf[64];
+            std::snprintf(buf, sizeof(buf), " %.3f ms, ", ms);
+            note += " " + gj_variant_name(v) + buf;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = v;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        EMG_CUDA_TRY(c, cudaFreeAsync(scratch, c->stream));
+        g_gj_best[key] = best;
+        L.gj_variant = best;
+        c->tuning += note + "-> " + gj_variant_name(best) + "; ";
+    }
+    return EMG_OK;
+}
+
+emg_status launch_lu32(emg_ctx* c, int p) {
+    LevelDev& L = c->lv[p];
+    if (L.tc_gj) {
+        bool built = false;
+        const emg_status st = launch_gj_tc(c, L.B, L.blk32, &built);
+        if (built) return st;
+    }
+    bool ok = true;
+    {
+        ProfScope _ps(c, PC_LU);
+        EMG_CUDA_TRY(c, gj_dispatch(L.B, L.gj_variant, (unsigned)c->E, L.blk32, c->stream, &ok));
+    }
+    if (!ok) {
+        c->err = "unsupported block size";
+        return EMG_ERR_ARG;
+    }
+    return EMG_OK;
+}
+
+}  // namespace emg

@@ -321,6 +321,217 @@ __global__ void __launch_bounds__(DiagCfg<D, P>::THREADS, (DiagMinB<D, P, T>::V)
     }
 }
 
+// Register-blocked SIMT form of the float32 assembly (the default float32 form): thread
+// (a, i, jg) accumulates row (a,i) of the block for all five b and the JW columns j of group jg,
+// acc[b][j] += s_b psi_j with s_b = sum_k W d_k psi_i A_k[a][b] formed once per point and
+// reused across the JW columns; every staged basis row is read 16 bytes at a time and
+// broadcast.  Per entry the terms are summed in the order of k_diag_blocks (points in order,
+// then the faces, each product as one FMA), so both forms give bitwise the same blocks.
+template <int D, int P>
+struct DiagRb {
+    static constexpr int N = Lv<D, P>::N;
+    static constexpr int JW = N <= 16 ? ((N + 3) / 4) * 4 : 20;    // columns j per thread
+    static constexpr int JG = (N + JW - 1) / JW;                     // column groups
+    static constexpr int NPAD = JG * JW;                             // padded basis row
+    static constexpr int ROWS = 5 * N;                               // (a, i)
+    static constexpr int THREADS = ((ROWS * JG + 31) / 32) * 32;
+    static constexpr int QC = D == 2 ? 36 : 24;                      // volume points per chunk
+    static constexpr int B = Lv<D, P>::B;
+    // the finished block leaves through shared memory: whole when it fits, else one b at a time
+    static constexpr bool WHOLE = (size_t)B * B * sizeof(float) <= 24576;
+    static constexpr int OLD = N + 1;                                // row stride of a b-slab
+    static constexpr int OB = WHOLE ? B * B : ROWS * OLD;
+    // shared memory (floats): the chunk and face buffers, with the output buffer over them
+    static constexpr int Q = Lv<D, P>::Q, QF = Lv<D, P>::QF;
+    static constexpr int O_PS = 0;                                   // [QC][NPAD]
+    static constexpr int O_FPS = O_PS + QC * NPAD;                   // [QF][NPAD]
+    static constexpr int O_GS = O_FPS + QF * NPAD;                   // [QC][D][N]
+    static constexpr int O_AS = O_GS + QC * D * N;                   // [QC][D][25]
+    static constexpr int O_US = O_AS + QC * D * 25;                  // [QC][5]
+    static constexpr int O_FJ = O_US + QC * 5;                       // [QF][25]
+    static constexpr int PHASE = O_FJ + QF * 25;
+    static constexpr int SM = PHASE > OB ? PHASE : OB;
+    static constexpr int REGS = 5 * JW > 80 ? 168 : 128;             // register budget per thread
+    static constexpr int MINB = (65536 / (THREADS * REGS)) < 1 ? 1 : 65536 / (THREADS * REGS);
+};
+
+template <int D, int P>
+__global__ void __launch_bounds__(DiagRb<D, P>::THREADS, DiagRb<D, P>::MINB) k_diag_blocks_rb(
+    int E, int nmax, const double* __restrict__ u, const float* __restrict__ vpsi, const float* __restrict__ vgw,
+    const int* __restrict__ elem_face, const float* __restrict__ fpsiL, const float* __restrict__ fpsiR,
+    const float* __restrict__ fjl, const float* __restrict__ fjr, const double* __restrict__ psic,
+    const double* __restrict__ hlen, const double* __restrict__ cfl_dev, double g, int shifted,
+    float* __restrict__ out) {
+    using L = Lv<D, P>;
+    using R = DiagRb<D, P>;
+    constexpr int N = L::N, Q = L::Q, QF = L::QF, B = L::B, NF = L::NF;
+    constexpr int JW = R::JW, JG = R::JG, NPAD = R::NPAD, QC = R::QC;
+    __shared__ double ud[B];
+    __shared__ float us[B];
+    __shared__ __align__(16) float smf[R::SM];
+    __shared__ double s_dtau;
+    float(*ps)[NPAD] = reinterpret_cast<float(*)[NPAD]>(smf + R::O_PS);
+    float(*fps)[NPAD] = reinterpret_cast<float(*)[NPAD]>(smf + R::O_FPS);
+    float(*gs)[D][N] = reinterpret_cast<float(*)[D][N]>(smf + R::O_GS);
+    float(*As)[D][25] = reinterpret_cast<float(*)[D][25]>(smf + R::O_AS);
+    float(*Us)[5] = reinterpret_cast<float(*)[5]>(smf + R::O_US);
+    float(*fjs)[25] = reinterpret_cast<float(*)[25]>(smf + R::O_FJ);
+    float* ob = smf;   // over the chunk buffers, once the accumulation is done
+    const int e = blockIdx.x;
+    const int tid = threadIdx.x;
+    for (int t = tid; t < B; t += blockDim.x) {
+        const double v = u[(size_t)e * B + t];
+        ud[t] = v;
+        us[t] = (float)v;
+    }
+    __syncthreads();
+    if (tid == 0 && shifted) {
+        double Uc[5];
+        for (int a = 0; a < 5; ++a) {
+            double s = 0.0;
+            for (int i = 0; i < N; ++i) s += ud[a * N + i] * psic[(size_t)e * nmax + i];
+            Uc[a] = s;
+        }
+        const double ir = 1.0 / Uc[0];
+        const double vx = Uc[1] * ir, vy = Uc[2] * ir, vz = Uc[3] * ir;
+        const double q2 = vx * vx + vy * vy + vz * vz;
+        const double pr = (g - 1.0) * (Uc[4] - 0.5 * Uc[0] * q2);
+        const double cs = sqrt(g * pr * ir);
+        s_dtau = cfl_dev[0] * hlen[e] / ((2 * P + 1) * (sqrt(q2) + cs));
+    }
+    // thread (a, i, jg): consecutive threads take consecutive i, so a warp shares a and jg
+    const bool active = tid < R::ROWS * JG;
+    const int a = tid / (N * JG), rem = tid % (N * JG);
+    const int jg = rem / N, i = rem % N;
+    const int j0 = jg * JW;
+    float acc[5][JW];
+#pragma unroll
+    for (int b = 0; b < 5; ++b)
+#pragma unroll
+        for (int j = 0; j < JW; ++j) acc[b][j] = 0.0f;
+    if (P > 0) {
+        for (int q0 = 0; q0 < Q; q0 += QC) {
+            const int nq = (Q - q0) < QC ? (Q - q0) : QC;
+            __syncthreads();
+            const float* pg = vpsi + ((size_t)e * Q + q0) * N;
+            for (int t = tid; t < nq * NPAD; t += blockDim.x) {
+                const int q = t / NPAD, j = t % NPAD;
+                ps[q][j] = j < N ? pg[q * N + j] : 0.0f;
+            }
+            for (int t = tid; t < D * nq * N; t += blockDim.x) {
+                const int k = t / (nq * N), r = t % (nq * N);
+                gs[r / N][k][r % N] = vgw[(((size_t)e * D + k) * Q + q0) * N + r];
+            }
+            for (int t = tid; t < nq * 5; t += blockDim.x) {
+                const int q = t / 5, c = t % 5;
+                const float* pq = pg + (size_t)q * N;
+                float s = 0.0f;
+                for (int m = 0; m < N; ++m) s += us[c * N + m] * pq[m];
+                Us[q][c] = s;
+            }
+            __syncthreads();
+            for (int t = tid; t < nq * D; t += blockDim.x) flux_jac_k(Us[t / D], (float)g, t % D, As[t / D][t % D]);
+            __syncthreads();
+            if (active) {
+#pragma unroll 1
+                for (int t = 0; t < nq; ++t) {
+                    float gk[D];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) gk[k] = gs[t][k][i];
+                    float s[5];
+#pragma unroll
+                    for (int b = 0; b < 5; ++b) {
+                        float x = 0.0f;
+#pragma unroll
+                        for (int k = 0; k < D; ++k) x += gk[k] * As[t][k][a * 5 + b];
+                        s[b] = x;
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < JW; jj += 4) {
+                        const float4 v = *reinterpret_cast<const float4*>(&ps[t][j0 + jj]);
+                        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+#pragma unroll
+                            for (int b = 0; b < 5; ++b) acc[b][jj + c] += s[b] * vv[c];
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll 1
+    for (int lf = 0; lf < NF; ++lf) {
+        const int code = elem_face[(size_t)e * NF + lf];
+        const float* pt = ((code & 1) ? fpsiR : fpsiL) + ((size_t)(code >> 1) * QF) * N;
+        const float* fj = ((code & 1) ? fjr : fjl) + ((size_t)(code >> 1) * QF) * 25;
+        __syncthreads();
+        for (int t = tid; t < QF * NPAD; t += blockDim.x) {
+            const int q = t / NPAD, j = t % NPAD;
+            fps[q][j] = j < N ? pt[q * N + j] : 0.0f;
+        }
+        for (int t = tid; t < QF * 25; t += blockDim.x) fjs[t / 25][t % 25] = (code & 1) ? fj[t] : -fj[t];
+        __syncthreads();
+        if (active) {
+#pragma unroll 1
+            for (int t = 0; t < QF; ++t) {
+                const float pi = fps[t][i];
+                float s[5];
+#pragma unroll
+                for (int b = 0; b < 5; ++b) s[b] = pi * fjs[t][a * 5 + b];
+#pragma unroll
+                for (int jj = 0; jj < JW; jj += 4) {
+                    const float4 v = *reinterpret_cast<const float4*>(&fps[t][j0 + jj]);
+                    const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+#pragma unroll
+                        for (int b = 0; b < 5; ++b) acc[b][jj + c] += s[b] * vv[c];
+                }
+            }
+        }
+    }
+    const float idt = shifted ? (float)(1.0 / s_dtau) : 0.0f;
+    float* g_out = out + (size_t)e * B * B;
+    if (R::WHOLE) {
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int b = 0; b < 5; ++b)
+#pragma unroll
+                for (int j = 0; j < JW; ++j) {
+                    const int jj = j0 + j;
+                    if (jj < N) {
+                        const float v = acc[b][j];
+                        ob[(a * N + i) * B + b * N + jj] = shifted ? ((a == b && i == jj) ? idt : 0.0f) - v : v;
+                    }
+                }
+        }
+        __syncthreads();
+        for (int t = tid; t < B * B; t += blockDim.x) g_out[t] = ob[t];
+    } else {
+        constexpr int OLD = R::OLD;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {   // unrolled: acc[b] stays in registers
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int j = 0; j < JW; ++j) {
+                    const int jj = j0 + j;
+                    if (jj < N) {
+                        const float v = acc[b][j];
+                        ob[(a * N + i) * OLD + jj] = shifted ? ((a == b && i == jj) ? idt : 0.0f) - v : v;
+                    }
+                }
+            }
+            __syncthreads();
+            for (int t = tid; t < R::ROWS * N; t += blockDim.x) {
+                const int r = t / N, j = t % N;
+                g_out[(size_t)r * B + b * N + j] = ob[r * OLD + j];
+            }
+        }
+    }
+}
+
 // ---- tensor-core assembly of the float32 block forms (tcgen05) ------------------------------
 // Eq. jac1 per element as one matrix product C = G Psi with
 //   rows    m = (a b, i)      (25 N rows, in 128-row tiles),
@@ -767,9 +978,14 @@ emg_status launch_diag_blocks32(emg_ctx* c, int p, const double* u, const double
 #define EMG_DB32(DD, PP)                                                                                    \
     {                                                                                                       \
         ProfScope _ps(c, PC_DIAG);                                                                          \
-        k_diag_blocks<DD, PP, float><<<(unsigned)c->E, DiagCfg<DD, PP>::THREADS, 0, c->stream>>>(           \
-            (int)c->E, nmax, u, L.vpsi32, L.vgw32, c->elem_face, L.fpsiL32, L.fpsiR32, L.fjl32, L.fjr32, c->psic, \
-            c->h, cfl_dev, c->prm.gamma, shifted, out);                                                     \
+        if (c->prm.block_kernels == 3)                                                                      \
+            k_diag_blocks<DD, PP, float><<<(unsigned)c->E, DiagCfg<DD, PP>::THREADS, 0, c->stream>>>(       \
+                (int)c->E, nmax, u, L.vpsi32, L.vgw32, c->elem_face, L.fpsiL32, L.fpsiR32, L.fjl32, L.fjr32,  \
+                c->psic, c->h, cfl_dev, c->prm.gamma, shifted, out);                                        \
+        else                                                                                                \
+            k_diag_blocks_rb<DD, PP><<<(unsigned)c->E, DiagRb<DD, PP>::THREADS, 0, c->stream>>>(            \
+                (int)c->E, nmax, u, L.vpsi32, L.vgw32, c->elem_face, L.fpsiL32, L.fpsiR32, L.fjl32, L.fjr32,  \
+                c->psic, c->h, cfl_dev, c->prm.gamma, shifted, out);                                        \
     }
         EMG_DISPATCH_DP(c->dim, p, EMG_DB32)
 #undef EMG_DB32

@@ -52,7 +52,7 @@ def n_terms(dim, p):
 
 @pytest.mark.parametrize("name,mk,p", BLOCK_CASES)
 @pytest.mark.parametrize("cfl", [3.0, 100.0])
-@pytest.mark.parametrize("kernels", [1, 2])          # tensor-core and SIMT forms
+@pytest.mark.parametrize("kernels", [1, 2, 3])       # tensor-core, SIMT, SIMT unblocked inverse
 def test_fp32_block_operator_and_inverse(name, mk, p, cfl, kernels):
     import paper_1807_01151_gb300 as pkg
     desc, dg, u, D = oracle_case(name, mk, p)
@@ -77,7 +77,7 @@ def test_fp32_block_operator_and_inverse(name, mk, p, cfl, kernels):
 
 
 @pytest.mark.parametrize("name,mk,p", BLOCK_CASES)
-@pytest.mark.parametrize("kernels", [1, 2])
+@pytest.mark.parametrize("kernels", [1, 2, 3])
 def test_fp32_block_prk_step_at_block_size(name, mk, p, kernels):
     import paper_1807_01151_gb300 as pkg
     desc, dg, u, D = oracle_case(name, mk, p)
@@ -94,6 +94,56 @@ def test_fp32_block_prk_step_at_block_size(name, mk, p, kernels):
     bound = 8 * np.linalg.cond(P).max() * (eps + B * U32)
     e = rel_err(ug - u, uo - u)
     assert 1e-12 < e <= bound, (e, bound)
+
+
+LEVEL_CASES = [
+    ("cyl8x4_p4", lambda: ogrid(8, 4), 4),                      # B = 15, 30, 50, 75
+    ("sphere6x2x2x2_p3", lambda: cubed_sphere_shell(2, 2), 3),  # B = 20, 50, 100
+]
+
+
+@pytest.mark.parametrize("name,mk,pmax", LEVEL_CASES)
+@pytest.mark.parametrize("kernels", [2, 3])          # blocked and unblocked SIMT inverse
+def test_fp32_inverse_at_every_level(name, mk, pmax, kernels):
+    """The float32 Gauss-Jordan inverse alone, at every block size of the levels: against the
+    FP64 inverse of the very float32 operator the kernel was given.  Gauss-Jordan elimination
+    with partial pivoting is forward stable, ||X^ - X|| / ||X|| <= c B u32 kappa_2(P); asserted
+    with c = 4 per element, and at least float32 error (it is float32 arithmetic)."""
+    import paper_1807_01151_gb300 as pkg
+    desc = mk()
+    dg = DG(desc, pmax)
+    u = perturbed_state(dg, amp=0.002)
+    s = pkg.Solver(desc, p_max=pmax, prec=1, block_kernels=kernels)
+    for p in range(1, pmax + 1):
+        up = np.ascontiguousarray(u[:, :, :dg.N(p)])
+        for cfl in (3.0, 100.0):
+            Pg = s.block_operator(p, up, cfl=cfl, which=0).astype(np.float64)
+            Xg = s.block_operator(p, up, cfl=cfl, which=1)
+            B = Pg.shape[-1]
+            X = np.linalg.inv(Pg)
+            err = np.linalg.norm(Xg - X, ord=2, axis=(1, 2)) / np.linalg.norm(X, ord=2, axis=(1, 2))
+            bound = 4 * np.linalg.cond(Pg) * B * U32
+            assert np.all(err <= bound), (p, cfl, (err / bound).max())
+            assert err.max() > 0.0
+    s.close()
+
+
+@pytest.mark.parametrize("name,mk,pmax", LEVEL_CASES + [("sphere6x1x1x2_p4", lambda: cubed_sphere_shell(1, 2), 4)])
+def test_fp32_assembly_forms_are_bitwise_the_same(name, mk, pmax):
+    """The register-blocked SIMT assembly (several b and j per thread) sums every entry's terms
+    in the order of the one-row-per-thread form: bitwise the same blocks at every level."""
+    import paper_1807_01151_gb300 as pkg
+    desc = mk()
+    dg = DG(desc, pmax)
+    u = perturbed_state(dg, amp=0.002)
+    out = []
+    for bk in (2, 3):
+        s = pkg.Solver(desc, p_max=pmax, prec=1, block_kernels=bk)
+        out.append([s.block_operator(p, np.ascontiguousarray(u[:, :, :dg.N(p)]), cfl=3.0, which=0)
+                    for p in range(1, pmax + 1)])
+        s.close()
+    for x, y in zip(*out):
+        np.testing.assert_array_equal(x, y)
 
 
 @pytest.mark.parametrize("name,mk,p", BLOCK_CASES)
@@ -257,7 +307,7 @@ def test_fp64_form_at_3d_p4():
 
 
 @pytest.mark.parametrize("name,mk,p", BLOCK_CASES)
-@pytest.mark.parametrize("kernels", [1, 2])
+@pytest.mark.parametrize("kernels", [1, 2, 3])
 def test_inverse_of_non_finite_blocks_completes(name, mk, p, kernels):
     """A state with NaN entries (a diverging solve) gives blocks with NaN entries: the
     Gauss-Jordan forms must still pick one pivot row per step (the lowest unused row when a
