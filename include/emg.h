@@ -125,8 +125,17 @@ typedef struct {
                               unchanged).  1 (default): every cycle. */
     int32_t quad_extra;    /* q = p + quad_extra Gauss points per direction and level; only the
                               rule q = p + 2 is built (2, the default; 0 is read as 2) */
-    double omega[3];       /* angular velocity of the rotating frame (Eq. euler); only the
-                              absolute frame omega = 0 is built (other values: EMG_ERR_ARG) */
+    double omega[3];       /* angular velocity of the rotating frame (Eq. euler), (0, 0, 0)
+                              by default (an absolute frame).  Otherwise the state keeps the
+                              absolute velocity v; mass and momentum are carried by the velocity
+                              relative to the frame, v - v_r with v_r = omega x x; the energy
+                              flux is rho E (v - v_r) + p v (what the Appendix's Jacobian
+                              differentiates); the source -rho omega x v is added; walls are at
+                              rest in the frame (the relative velocity is mirrored) and the far
+                              field takes the free stream (absolute frame) through the same
+                              characteristic condition in relative velocities.  In 2-D only a
+                              rotation about z, omega = (0, 0, w), is accepted (else
+                              EMG_ERR_ARG); non-finite values: EMG_ERR_ARG. */
     int32_t block_kernels; /* kernels of the float32 block forms' assembly and inverse:
                               0 (default): per level, the form this build measured faster;
                               1: the tensor-core forms (tcgen05: 3xTF32 assembly, blocked

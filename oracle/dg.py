@@ -31,9 +31,11 @@ class Level:
 
 class DG:
     def __init__(self, desc, p_max, mach=0.3, alpha_deg=0.0, gamma=euler.GAMMA,
-                 exact_state=None, source=None):
+                 exact_state=None, source=None, omega=None):
         """exact_state(x[..., d]) -> U[..., 5] feeds BC_EXACT ghosts; source(x) -> S[..., 5]
-        is added as int psi_i S dx (both only for manufactured-solution tests)."""
+        is added as int psi_i S dx (both only for manufactured-solution tests).  omega: the
+        angular velocity of the rotating frame (Eq. euler; None or 0: a stationary frame;
+        in 2-D only its z component)."""
         self.dim = desc.dim
         self.p_max = p_max
         self.gamma = gamma
@@ -42,6 +44,12 @@ class DG:
         self.Uinf = euler.freestream(mach, alpha_deg, gamma)
         self.exact_state = exact_state
         self.source = source
+        om = None if omega is None else np.asarray(omega, dtype=float)
+        if om is not None and not np.any(om):
+            om = None
+        if om is not None and desc.dim == 2 and (om[0] != 0.0 or om[1] != 0.0):
+            raise ValueError("in 2-D the rotation axis must be z")
+        self.omega = om
         self.E = self.mesh.E
         self.levels = [self._build_level(p) for p in range(p_max + 1)]
 
@@ -83,7 +91,19 @@ class DG:
         L.bnd_code = m.bnd_code
         if self.source is not None:
             L.src = np.einsum('eq,eqi,eqa->eai', W, psi, self.source(x))
+        if self.omega is not None:
+            # frame velocity v_r = omega x x at volume and face points
+            L.vr = self.frame_velocity(x)
+            L.int_vrn = np.sum(self.frame_velocity(xf) * L.int_n, axis=-1)
+            L.bnd_vr = self.frame_velocity(xb)
+            L.bnd_vrn = np.sum(L.bnd_vr * L.bnd_n, axis=-1) if xb.size else np.zeros(xb.shape[:2])
         return L
+
+    def frame_velocity(self, x):
+        """omega x x at points x[..., d] (3 components)."""
+        x3 = np.zeros(x.shape[:-1] + (3,))
+        x3[..., :x.shape[-1]] = x
+        return np.cross(self.omega, x3)
 
     # -- states ---------------------------------------------------------------
     def freestream_state(self, p=None):
@@ -101,20 +121,22 @@ class DG:
         return self.evaluate_at(p, u, x, np.arange(self.E))[:, 0, :]
 
     # -- residual -------------------------------------------------------------
-    def ghost(self, UL, n, x, code, wn=None):
+    def ghost(self, UL, n, x, code, wn=None, vr=None):
         """Ghost states; the slip wall mirrors the velocity about wn (body normal), a
-        symmetry plane (Sec. 5, sphere case) about the face's own normal n."""
+        symmetry plane (Sec. 5, sphere case) about the face's own normal n; in a rotating
+        frame (vr: the frame velocity at the points) the velocity relative to the frame."""
         G = np.empty_like(UL)
         wall = code == BC_WALL
         far = code == BC_FARFIELD
         sym = code == BC_SYMMETRY
         exact = code == BC_EXACT
+        sel = (lambda m: None) if vr is None else (lambda m: vr[m])
         if wall.any():
-            G[wall] = euler.wall_ghost(UL[wall], (n if wn is None else wn)[wall])
+            G[wall] = euler.wall_ghost(UL[wall], (n if wn is None else wn)[wall], sel(wall), self.gamma)
         if sym.any():
-            G[sym] = euler.wall_ghost(UL[sym], n[sym])
+            G[sym] = euler.wall_ghost(UL[sym], n[sym], sel(sym), self.gamma)
         if far.any():
-            G[far] = euler.farfield_ghost(UL[far], n[far], self.Uinf, self.gamma)
+            G[far] = euler.farfield_ghost(UL[far], n[far], self.Uinf, self.gamma, sel(far))
         if exact.any():
             G[exact] = self.exact_state(x[exact]).astype(UL.dtype)
         return G
@@ -123,24 +145,30 @@ class DG:
         """R_p(u), u [E][5][N_p] (real or complex) -> [E][5][N_p]."""
         L = self.levels[p]
         d = self.dim
+        rot = self.omega is not None
         Uq = np.einsum('eai,eqi->eqa', u, L.psi)
-        F = euler.flux(Uq, self.gamma)[..., :d, :]
+        F = euler.flux(Uq, self.gamma, L.vr if rot else None)[..., :d, :]
         R = np.einsum('eqik,eqka->eai', L.wgrad, F)
         m = self.mesh
         if len(m.int_L):
             UL = np.einsum('fai,fqi->fqa', u[m.int_L], L.int_psiL)
             UR = np.einsum('fai,fqi->fqa', u[m.int_R], L.int_psiR)
-            Fh = L.int_amag[..., None] * euler.roe(UL, UR, L.int_n, self.gamma)
+            Fh = L.int_amag[..., None] * euler.roe(UL, UR, L.int_n, self.gamma, L.int_vrn if rot else None)
             np.add.at(R, m.int_L, -np.einsum('fqi,fqa->fai', L.int_psiL, Fh))
             np.add.at(R, m.int_R, np.einsum('fqi,fqa->fai', L.int_psiR, Fh))
         if len(m.bnd_L):
             UL = np.einsum('fai,fqi->fqa', u[m.bnd_L], L.bnd_psi)
             code = np.broadcast_to(L.bnd_code[:, None], UL.shape[:2])
-            G = self.ghost(UL, L.bnd_n, L.bnd_x, code, L.bnd_wn)
-            Fh = L.bnd_amag[..., None] * euler.roe(UL, G, L.bnd_n, self.gamma)
+            G = self.ghost(UL, L.bnd_n, L.bnd_x, code, L.bnd_wn, L.bnd_vr if rot else None)
+            Fh = L.bnd_amag[..., None] * euler.roe(UL, G, L.bnd_n, self.gamma, L.bnd_vrn if rot else None)
             np.add.at(R, m.bnd_L, -np.einsum('fqi,fqa->fai', L.bnd_psi, Fh))
         if self.source is not None:
             R = R + L.src
+        if rot:
+            # Eq. euler's source S = (0, -rho omega x v, 0) = (0, -omega x (rho v), 0), as int psi_i S
+            S = np.zeros(Uq.shape, dtype=Uq.dtype)
+            S[..., 1:4] = -np.cross(np.broadcast_to(self.omega, Uq[..., 1:4].shape), Uq[..., 1:4])
+            R = R + np.einsum('eq,eqi,eqa->eai', L.W, L.psi, S)
         return R
 
     # -- derivatives ----------------------------------------------------------

@@ -390,8 +390,11 @@ emg_status emg_create_mesh(const emg_mesh_desc* m, const emg_params* prm, emg_ct
         return fail(c, EMG_ERR_ARG, "only the rule q = p + 2 is built (quad_extra 2)");
     if (prm->block_kernels < 0 || prm->block_kernels > 3)
         return fail(c, EMG_ERR_ARG, "block_kernels must be 0, 1, 2 or 3");
-    if (prm->omega[0] != 0.0 || prm->omega[1] != 0.0 || prm->omega[2] != 0.0)
-        return fail(c, EMG_ERR_ARG, "only the absolute frame (omega = 0) is built");
+    if (!std::isfinite(prm->omega[0]) || !std::isfinite(prm->omega[1]) || !std::isfinite(prm->omega[2]))
+        return fail(c, EMG_ERR_ARG, "omega must be finite");
+    if (m->dim == 2 && (prm->omega[0] != 0.0 || prm->omega[1] != 0.0))
+        return fail(c, EMG_ERR_ARG, "in 2-D the rotation axis must be z (omega = (0, 0, w))");
+    c->rot = prm->omega[0] != 0.0 || prm->omega[1] != 0.0 || prm->omega[2] != 0.0;
     c->p_max = prm->p_max;
     if (c->prm.jac_freeze < 1) c->prm.jac_freeze = 1;
     EMG_CUDA_TRY(c, cudaGetDevice(&c->device));

@@ -72,6 +72,8 @@ struct LevelDev {
     double* fpsiL = nullptr;   // [F][QF][N]     psi^L_i at the face points
     double* fpsiR = nullptr;   // [F_int][QF][N] psi^R_i at the face points
     double* fwn = nullptr;     // [F-F_int][QF][3] slip-wall reflection normal (body normal)
+    double* vvr = nullptr;     // [E][Q][3]      frame velocity omega x x (rotating frame only)
+    double* fvr = nullptr;     // [F][QF][3]     the same at the face points
     // states and work vectors, [E][5][N]
     double* v = nullptr;       // current approximation
     double* v0 = nullptr;      // restricted state (levels below p_max)
@@ -153,6 +155,7 @@ struct emg_ctx {
     double* elem_x = nullptr;    // [E][2^D][D]
     double* elem_wn = nullptr;   // [E][2^D][D] body normals at the nodes (wall_normal input)
     int has_wn = 0;
+    bool rot = false;              // rotating frame (omega != 0, Eq. euler)
     double* xc = nullptr;        // [E][3]
     double* Lh = nullptr;        // [E][3]
     double* vol = nullptr;       // [E]
@@ -268,7 +271,7 @@ emg_status vcycle_body_up(emg_ctx* c);
 emg_status vcycle_body(emg_ctx* c);
 emg_status run_body(emg_ctx* c);
 emg_status check_flags(emg_ctx* c);
-int64_t estimate_bytes(int dim, int64_t E, int64_t F, int64_t F_int, int p_max, int m, int prec);
+int64_t estimate_bytes(int dim, int64_t E, int64_t F, int64_t F_int, int p_max, int m, int prec, bool rot);
 DevScalars* pinned_scalars_acquire();
 void pinned_scalars_release(DevScalars* p);
 }  // namespace emg

@@ -12,6 +12,10 @@
 namespace emg {
 
 // ---- forward-mode dual numbers ------------------------------------------------------
+// A product that is never fused into a later addition (float); plain for double.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return a * b; }
+
 template <int M, class S = double>
 struct Dual {
     S v;
@@ -96,6 +100,39 @@ __device__ __forceinline__ Dual<M, S> operator-(double a, const Dual<M, S>& b) {
     return dconst<M, S>(a) - b;
 }
 
+// Float duals (the float32 block forms' face Jacobians): every product and sum rounded on its
+// own, never contracted into a fused multiply-add, so that one derivative direction gives the
+// same bits whether it is carried alone or beside others (the compiler may otherwise fuse
+// differently once seeds of 0 and 1 are known constants).
+template <int M>
+__device__ __forceinline__ Dual<M, float> operator*(const Dual<M, float>& a, const Dual<M, float>& b) {
+    Dual<M, float> r;
+    r.v = __fmul_rn(a.v, b.v);
+#pragma unroll
+    for (int i = 0; i < M; ++i) r.d[i] = __fadd_rn(__fmul_rn(a.d[i], b.v), __fmul_rn(a.v, b.d[i]));
+    return r;
+}
+template <int M>
+__device__ __forceinline__ Dual<M, float> operator/(const Dual<M, float>& a, const Dual<M, float>& b) {
+    Dual<M, float> r;
+    const float ib = 1.0f / b.v;
+    r.v = __fmul_rn(a.v, ib);
+#pragma unroll
+    for (int i = 0; i < M; ++i) r.d[i] = __fmul_rn(__fsub_rn(a.d[i], __fmul_rn(r.v, b.d[i])), ib);
+    return r;
+}
+template <int M>
+__device__ __forceinline__ Dual<M, float> operator*(double a, const Dual<M, float>& b) {
+    Dual<M, float> r;
+    const float s = (float)a;
+    r.v = __fmul_rn(s, b.v);
+#pragma unroll
+    for (int i = 0; i < M; ++i) r.d[i] = __fmul_rn(s, b.d[i]);
+    return r;
+}
+template <int M>
+__device__ __forceinline__ Dual<M, float> operator*(const Dual<M, float>& b, double a) { return a * b; }
+
 __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
 __device__ __forceinline__ double abs_(double a) { return fabs(a); }
 __device__ __forceinline__ double powr_(double a, double e) { return pow(a, e); }
@@ -108,7 +145,7 @@ __device__ __forceinline__ Dual<M, S> sqrt_(const Dual<M, S>& a) {
     r.v = sqrt(a.v);
     const S h = (S)0.5 / r.v;
 #pragma unroll
-    for (int i = 0; i < M; ++i) r.d[i] = a.d[i] * h;
+    for (int i = 0; i < M; ++i) r.d[i] = mul_rn(a.d[i], h);
     return r;
 }
 // |x| with d|x|/dx = sign(x), sign(0) = +1 (matches the analytic continuation x*sign(Re x)).
@@ -122,7 +159,7 @@ __device__ __forceinline__ Dual<M, S> powr_(const Dual<M, S>& a, double e) {
     r.v = pow(a.v, (S)e);
     const S g = (S)e * r.v / a.v;
 #pragma unroll
-    for (int i = 0; i < M; ++i) r.d[i] = a.d[i] * g;
+    for (int i = 0; i < M; ++i) r.d[i] = mul_rn(a.d[i], g);
     return r;
 }
 template <int M, class S>
@@ -178,8 +215,13 @@ __device__ __forceinline__ void flux_k(const double U[5], double g, double F[3][
     }
 }
 
-template <class T>
-__device__ __forceinline__ void roe_flux(const T UL[5], const T UR[5], const double n[3], double g, T F[5]) {
+// Roe flux; with ROT the face moves with normal speed vrn (a rotating frame: v_r . n): the
+// normal fluxes carry the relative normal velocity, F_n - vrn U (mass and momentum with
+// v - v_r, energy rho E (v - v_r) + p v), and the waves' speeds are shifted by -vrn; the
+// Roe averages, wave strengths and eigenvectors are those of the stationary face.
+template <class T, bool ROT = false>
+__device__ __forceinline__ void roe_flux(const T UL[5], const T UR[5], const double n[3], double g, T F[5],
+                                         double vrn = 0.0) {
     T rL, vL[3], pL, rR, vR[3], pR;
     primitives(UL, g, rL, vL, pL);
     primitives(UR, g, rR, vR, pR);
@@ -208,11 +250,24 @@ __device__ __forceinline__ void roe_flux(const T UL[5], const T UR[5], const dou
     T dvt[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) dvt[k] = dv[k] - dqn * n[k];
-    T l1 = abs_(qn - c), l2 = abs_(qn), l5 = abs_(qn + c);
+    T l1, l2, l5;
+    if constexpr (ROT) {
+        const T qr = qn - vrn;
+        l1 = abs_(qr - c), l2 = abs_(qr), l5 = abs_(qr + c);
+    } else {
+        l1 = abs_(qn - c), l2 = abs_(qn), l5 = abs_(qn + c);
+    }
     T w1 = l1 * a1, w2 = l2 * a2, w5 = l5 * a5, ws = l2 * rho;
     T FL[5], FR[5];
     flux_n(UL, n, g, FL);
     flux_n(UR, n, g, FR);
+    if constexpr (ROT) {
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+            FL[a] = FL[a] - vrn * UL[a];
+            FR[a] = FR[a] - vrn * UR[a];
+        }
+    }
     T d0 = w1 + w2 + w5;
     F[0] = 0.5 * (FL[0] + FR[0] - d0);
 #pragma unroll
@@ -233,6 +288,24 @@ __device__ __forceinline__ void wall_ghost(const T UL[5], const double n[3], T G
     G[2] = UL[2] - 2.0 * mn * n[1];
     G[3] = UL[3] - 2.0 * mn * n[2];
     G[4] = UL[4];
+}
+
+// Slip wall at rest in a rotating frame: the velocity relative to the frame (v - v_r) mirrored
+// about n, density and pressure kept (the kinetic energy changes with the absolute velocity).
+template <class T>
+__device__ __forceinline__ void wall_ghost_rel(const T UL[5], const double n[3], const double vr[3], double g,
+                                               T G[5]) {
+    T ir = inv_(UL[0]);
+    T v[3] = {UL[1] * ir, UL[2] * ir, UL[3] * ir};
+    T p = (g - 1.0) * (UL[4] - 0.5 * UL[0] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+    T wn = (v[0] - vr[0]) * n[0] + (v[1] - vr[1]) * n[1] + (v[2] - vr[2]) * n[2];
+    T vg[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) vg[k] = v[k] - 2.0 * wn * n[k];
+    G[0] = UL[0];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G[1 + k] = UL[0] * vg[k];
+    G[4] = p * (1.0 / (g - 1.0)) + 0.5 * UL[0] * (vg[0] * vg[0] + vg[1] * vg[1] + vg[2] * vg[2]);
 }
 
 // Subsonic characteristic far field: R+ = q_n,L + 2c_L/(g-1) from inside, R- = q_n,inf -
@@ -270,6 +343,52 @@ __device__ __forceinline__ void farfield_ghost(const T UL[5], const double n[3],
     G[2] = rb * vb[1];
     G[3] = rb * vb[2];
     G[4] = pb * (1.0 / (g - 1.0)) + 0.5 * rb * (vb[0] * vb[0] + vb[1] * vb[1] + vb[2] * vb[2]);
+}
+
+// The far field of a rotating frame: the stationary-frame condition on velocities relative to
+// the frame (v - v_r for the interior state and the free stream, which is given in the
+// absolute frame), the ghost's velocity taken back to the absolute frame.
+template <class T>
+__device__ __forceinline__ void farfield_ghost_rel(const T UL[5], const double n[3], const double Ui[5], double g,
+                                                   const double vr[3], T G[5]) {
+    T ir = inv_(UL[0]);
+    T v[3] = {UL[1] * ir, UL[2] * ir, UL[3] * ir};
+    T q2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    T Ur[5];
+    Ur[0] = UL[0];
+    T w[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        w[k] = v[k] - vr[k];
+        Ur[1 + k] = UL[0] * w[k];
+    }
+    // same pressure: rho E_rel = rho E - rho |v|^2 / 2 + rho |v - v_r|^2 / 2
+    Ur[4] = UL[4] - 0.5 * UL[0] * q2 + 0.5 * UL[0] * (w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    double Uir[5];
+    {
+        const double ri = Ui[0];
+        double vi[3], wi[3];
+        for (int k = 0; k < 3; ++k) {
+            vi[k] = Ui[1 + k] / ri;
+            wi[k] = vi[k] - vr[k];
+        }
+        Uir[0] = ri;
+        for (int k = 0; k < 3; ++k) Uir[1 + k] = ri * wi[k];
+        Uir[4] = Ui[4] - 0.5 * ri * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]) +
+                 0.5 * ri * (wi[0] * wi[0] + wi[1] * wi[1] + wi[2] * wi[2]);
+    }
+    T Gr[5];
+    farfield_ghost(Ur, n, Uir, g, Gr);
+    T ig = inv_(Gr[0]);
+    T wg[3] = {Gr[1] * ig, Gr[2] * ig, Gr[3] * ig};
+    T vb[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) vb[k] = wg[k] + vr[k];
+    G[0] = Gr[0];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G[1 + k] = Gr[0] * vb[k];
+    G[4] = Gr[4] - 0.5 * Gr[0] * (wg[0] * wg[0] + wg[1] * wg[1] + wg[2] * wg[2]) +
+           0.5 * Gr[0] * (vb[0] * vb[0] + vb[1] * vb[1] + vb[2] * vb[2]);
 }
 
 }  // namespace emg

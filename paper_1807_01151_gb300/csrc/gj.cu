@@ -37,6 +37,101 @@ emg_status launch_gj_tc(emg_ctx* c, int B, float* blk, bool* built);
 // row if no candidate is a number).  The summation order differs from the unblocked forms
 // (results agree to float rounding, not bitwise); the variants with different W compute
 // identically.  The inverse is written column-major, as by the other forms.
+// ---- pieces shared by the blocked forms (k_gj_blk, k_gj_la) --------------------------------
+// Pivot key of row r: the magnitude bits of |a| without their lowest 8 (pivots within 2^-15
+// relative of each other tie), then 255 - r, so that the largest key is a row of (nearly) the
+// largest |a| and, among those, the lowest row; a NaN has magnitude part 0, so any number
+// beats it and a column without a number yields its lowest unused row.  Rows r < 128.
+__device__ __forceinline__ unsigned piv_pack(float x, int r) {
+    const unsigned k = (unsigned)(piv_key(x) + 1);   // 0 for NaN
+    return ((k >> 8) << 8) | (unsigned)(255 - r);
+}
+
+// The in-place Gauss-Jordan steps of a panel of NB columns held by one warp (lane tx: rows
+// tx + 32 i, x[i][c] for panel column c), one warp reduction per pivot: pivot rows are
+// recorded in perm[k0 + s] and piv[s]; `used` marks this lane's rows already taken.
+template <int B, int RS, int NB>
+__device__ __forceinline__ void gj_panel_steps(float (&x)[RS][NB], unsigned& used, int nb, int k0, int tx, int* perm,
+                                               int* piv) {
+#pragma unroll
+    for (int s = 0; s < NB; ++s) {
+        if (s >= nb) break;   // uniform
+        unsigned km = 0u;
+#pragma unroll
+        for (int i = 0; i < RS; ++i) {
+            const int r = tx + 32 * i;
+            const unsigned kk = (r < B && !((used >> i) & 1u)) ? piv_pack(x[i][s], r) : 0u;
+            km = kk > km ? kk : km;
+        }
+        km = __reduce_max_sync(0xffffffffu, km);
+        const int p = 255 - (int)(km & 255u);
+        const int pl = p & 31, pi = p >> 5;
+        float rk[NB];
+#pragma unroll
+        for (int ii = 0; ii < RS; ++ii)
+            if (pi == ii) {   // warp-uniform branch
+#pragma unroll
+                for (int c = 0; c < NB; ++c) rk[c] = __shfl_sync(0xffffffffu, x[ii][c], pl);
+            }
+        const float inv = __frcp_rn(rk[s]);   // correctly rounded, as 1.0f / rk[s]
+#pragma unroll
+        for (int c = 0; c < NB; ++c) rk[c] = (c == s) ? inv : rk[c] * inv;
+        float f[RS];
+#pragma unroll
+        for (int i = 0; i < RS; ++i) {
+            f[i] = (tx + 32 * i == p) ? 0.0f : x[i][s];
+            x[i][s] = 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < RS; ++i)
+#pragma unroll
+            for (int c = 0; c < NB; ++c) x[i][c] -= f[i] * rk[c];
+        if (tx == pl) {
+            used |= 1u << pi;
+#pragma unroll
+            for (int ii = 0; ii < RS; ++ii)
+                if (pi == ii) {
+#pragma unroll
+                    for (int c = 0; c < NB; ++c) x[ii][c] = rk[c];
+                }
+        }
+        if (tx == 0) {
+            perm[k0 + s] = p;
+            piv[s] = p;
+        }
+    }
+}
+
+// The panel's pivot rows on this warp's non-panel slots j = SPW .. CS-1 into its buffer yw
+// (row s at yw + s YL; written by the owner lane, 16 bytes at a time), and the factor m[i] that
+// clears this lane's pivot rows (they are rebuilt from F alone): 0 for a pivot row, else 1.
+template <int RS, int CS, int SPW, int YL, int NB>
+__device__ __forceinline__ void gj_gather_pivot_rows(const float (&a)[RS][CS], const int* piv, int nb, int tx,
+                                                     float* yw, float (&m)[RS]) {
+#pragma unroll
+    for (int i = 0; i < RS; ++i) m[i] = 1.0f;
+    for (int s = 0; s < nb; ++s) {
+        const int p = piv[s];
+        const int pl = p & 31, pi = p >> 5;
+        if (tx == pl) {
+#pragma unroll
+            for (int ii = 0; ii < RS; ++ii)
+                if (pi == ii) {
+                    m[ii] = 0.0f;
+#pragma unroll
+                    for (int j0 = 0; j0 < CS - SPW; j0 += 4) {
+                        float4 v;
+                        v.x = a[ii][SPW + j0];
+                        v.y = (j0 + 1 < CS - SPW) ? a[ii][SPW + j0 + 1] : 0.0f;
+                        v.z = (j0 + 2 < CS - SPW) ? a[ii][SPW + j0 + 2] : 0.0f;
+                        v.w = (j0 + 3 < CS - SPW) ? a[ii][SPW + j0 + 3] : 0.0f;
+                        *reinterpret_cast<float4*>(yw + s * YL + j0) = v;
+                    }
+                }
+        }
+    }
+}
+
 template <int B, int W>
 struct GjBlk {
     static constexpr int NB = 8;                        // panel width
@@ -52,7 +147,7 @@ struct GjBlk {
     static constexpr size_t TILE = (size_t)B * LD * sizeof(float);
     static constexpr size_t WORK = (size_t)(2 * R32 * PLD + W * NB * YL) * sizeof(float);
     static constexpr size_t SMEM = ((TILE > WORK ? TILE : WORK) + 15) / 16 * 16;
-    static constexpr bool VALID = (NB % W == 0) && RS * CS <= 64;
+    static constexpr bool VALID = (NB % W == 0) && RS * CS <= 64 && B <= 128;   // piv_pack: rows < 128
 };
 
 template <int B, int W>
@@ -100,64 +195,7 @@ __global__ void __launch_bounds__(32 * W) k_gj_blk(int E, float* __restrict__ bl
             for (int i = 0; i < RS; ++i)
 #pragma unroll
                 for (int c = 0; c < NB; ++c) x[i][c] = Pn[(tx + 32 * i) * PLD + c];
-#pragma unroll
-            for (int s = 0; s < NB; ++s) {
-                if (s >= nb) break;   // uniform
-                // pivot: the largest key among the unused rows (key + 1, so a NaN row is 0)
-                unsigned km = 0u;
-#pragma unroll
-                for (int i = 0; i < RS; ++i) {
-                    const int r = tx + 32 * i;
-                    const unsigned kk = (r < B && !((used >> i) & 1u)) ? (unsigned)(piv_key(x[i][s]) + 1) : 0u;
-                    km = kk > km ? kk : km;
-                }
-                km = __reduce_max_sync(0xffffffffu, km);
-                int rl = B;
-#pragma unroll
-                for (int i = 0; i < RS; ++i) {
-                    const int r = tx + 32 * i;
-                    const bool cand = r < B && !((used >> i) & 1u) &&
-                                      (unsigned)(piv_key(x[i][s]) + 1) == km;
-                    if (cand && r < rl) rl = r;
-                }
-                // lowest row holding the largest key; with km = 0 (no row is a number) every
-                // unused row qualifies: the lowest unused row
-                const int p = (int)__reduce_min_sync(0xffffffffu, (unsigned)rl);
-                const int pl = p & 31, pi = p >> 5;
-                float rk[NB];
-#pragma unroll
-                for (int ii = 0; ii < RS; ++ii)
-                    if (pi == ii) {   // warp-uniform branch
-#pragma unroll
-                        for (int c = 0; c < NB; ++c) rk[c] = __shfl_sync(0xffffffffu, x[ii][c], pl);
-                    }
-                const float inv = 1.0f / rk[s];
-#pragma unroll
-                for (int c = 0; c < NB; ++c) rk[c] = (c == s) ? inv : rk[c] * inv;
-                float f[RS];
-#pragma unroll
-                for (int i = 0; i < RS; ++i) {
-                    f[i] = (tx + 32 * i == p) ? 0.0f : x[i][s];
-                    x[i][s] = 0.0f;
-                }
-#pragma unroll
-                for (int i = 0; i < RS; ++i)
-#pragma unroll
-                    for (int c = 0; c < NB; ++c) x[i][c] -= f[i] * rk[c];
-                if (tx == pl) {
-                    used |= 1u << pi;
-#pragma unroll
-                    for (int ii = 0; ii < RS; ++ii)
-                        if (pi == ii) {
-#pragma unroll
-                            for (int c = 0; c < NB; ++c) x[ii][c] = rk[c];
-                        }
-                }
-                if (tx == 0) {
-                    perm[k0 + s] = p;
-                    s_piv[s] = p;
-                }
-            }
+            gj_panel_steps<B, RS, NB>(x, used, nb, k0, tx, perm, s_piv);
 #pragma unroll
             for (int i = 0; i < RS; ++i)
 #pragma unroll
@@ -167,22 +205,13 @@ __global__ void __launch_bounds__(32 * W) k_gj_blk(int E, float* __restrict__ bl
         // (C) pivot rows of this warp's non-panel columns into the warp's buffer; the pivot
         // rows' own entries are then cleared (they are rebuilt from F alone)
         __syncwarp();
-        for (int s = 0; s < nb; ++s) {
-            const int p = s_piv[s];
-            const int pl = p & 31, pi = p >> 5;
-            if (tx == pl) {
-#pragma unroll
-                for (int ii = 0; ii < RS; ++ii)
-                    if (pi == ii) {
-#pragma unroll
-                        for (int j = SPW; j < CS; ++j) {
-                            yw[s * YL + (j - SPW)] = a[ii][j];
-                            a[ii][j] = 0.0f;
-                        }
-                    }
-            }
-        }
+        float mrow[RS];
+        gj_gather_pivot_rows<RS, CS, SPW, YL, NB>(a, s_piv, nb, tx, yw, mrow);
         __syncwarp();
+#pragma unroll
+        for (int i = 0; i < RS; ++i)
+#pragma unroll
+            for (int j = SPW; j < CS; ++j) a[i][j] *= mrow[i];
 #pragma unroll
         for (int s = 0; s < NB; ++s) {
             if (s >= nb) break;   // uniform
@@ -234,12 +263,203 @@ __global__ void __launch_bounds__(32 * W) k_gj_blk(int E, float* __restrict__ bl
     for (int t = threadIdx.x; t < B * B; t += T) g[t] = tile[(t / B) * LD + (t % B)];
 }
 
+// Look-ahead form of k_gj_blk: warp 0 only factors panels and warps 1..W own the columns
+// (column c: warp 1 + c mod W, slot c / W).  At panel t the update warps first bring panel
+// t+1's columns up to date and hand them to warp 0, then update the remaining columns, so the
+// factorisation of panel t+1 runs while the trailing update of panel t is still going on.
+// Two named barriers carry the hand-offs (panel ready: the update warps arrive, warp 0 waits;
+// factor ready: warp 0 arrives, the update warps wait); panel and factor buffers are double
+// buffered.  Every entry receives the multiply-adds of k_gj_blk in the same order, and the
+// panel steps are those of k_gj_blk: bitwise the same inverse.
+template <int B, int W>
+struct GjLa {
+    static constexpr int NB = 8;
+    static constexpr int SPW = NB / W;
+    static constexpr int RS = (B + 31) / 32;
+    static constexpr int R32 = 32 * RS;
+    static constexpr int NP = (B + NB - 1) / NB;
+    static constexpr int CS = NP * SPW;
+    static constexpr int PLD = NB + 1;
+    static constexpr int YN = CS - SPW;
+    static constexpr int YL = YN > 0 ? ((YN + 3) / 4) * 4 : 4;
+    static constexpr int LD = (B % 2) ? B + 2 : B + 1;
+    static constexpr int THREADS = 32 * (W + 1);
+    static constexpr size_t TILE = (size_t)B * LD * sizeof(float);
+    static constexpr size_t WORK = (size_t)(4 * R32 * PLD + W * NB * YL) * sizeof(float);
+    static constexpr size_t SMEM = ((TILE > WORK ? TILE : WORK) + 15) / 16 * 16;
+    static constexpr bool VALID = (NB % W == 0) && RS * CS <= 64 && NP >= 2 && B <= 128;
+};
+
+__device__ __forceinline__ void named_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+template <int B, int W>
+__global__ void __launch_bounds__(32 * (W + 1)) k_gj_la(int E, float* __restrict__ blk) {
+    using G = GjLa<B, W>;
+    constexpr int NB = G::NB, SPW = G::SPW, RS = G::RS, R32 = G::R32, NP = G::NP, CS = G::CS;
+    constexpr int PLD = G::PLD, YL = G::YL, LD = G::LD, T = G::THREADS;
+    constexpr int BAR_PANEL = 1, BAR_F = 2;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float* tile = reinterpret_cast<float*>(smraw);      // staging (load and store only)
+    float* Pn = tile;                                   // 2 x [R32][PLD] panel columns
+    float* Fs = tile + 2 * R32 * PLD;                   // 2 x [R32][PLD] factored panels
+    float* Yw = tile + 4 * R32 * PLD;                   // [W][NB][YL] pivot rows per update warp
+    __shared__ int perm[B], invp[B];
+    __shared__ int s_piv[2][NB];
+    const int e = blockIdx.x;
+    const int tx = threadIdx.x & 31, wq = threadIdx.x >> 5, w = wq - 1;
+    float* g = blk + (size_t)e * B * B;
+    for (int t = threadIdx.x; t < B * B; t += T) tile[(t / B) * LD + (t % B)] = g[t];
+    __syncthreads();
+    float a[RS][CS];
+    if (wq > 0) {
+#pragma unroll
+        for (int i = 0; i < RS; ++i)
+#pragma unroll
+            for (int j = 0; j < CS; ++j) {
+                const int r = tx + 32 * i, c = w + W * j;
+                a[i][j] = (r < B && c < B) ? tile[r * LD + c] : 0.0f;
+            }
+    }
+    __syncthreads();   // the staging tile becomes the work buffers
+    if (wq == 0) {
+        // ---- factor warp -----------------------------------------------------------------
+        unsigned used = 0u;
+#pragma unroll 1
+        for (int t = 0; t < NP; ++t) {
+            const int k0 = t * NB;
+            const int nb = (B - k0) < NB ? (B - k0) : NB;
+            const float* pn = Pn + (t & 1) * R32 * PLD;
+            float* fs = Fs + (t & 1) * R32 * PLD;
+            named_sync(BAR_PANEL, T);
+            float x[RS][NB];
+#pragma unroll
+            for (int i = 0; i < RS; ++i)
+#pragma unroll
+                for (int c = 0; c < NB; ++c) x[i][c] = pn[(tx + 32 * i) * PLD + c];
+            gj_panel_steps<B, RS, NB>(x, used, nb, k0, tx, perm, s_piv[t & 1]);
+#pragma unroll
+            for (int i = 0; i < RS; ++i)
+#pragma unroll
+                for (int c = 0; c < NB; ++c) fs[(tx + 32 * i) * PLD + c] = x[i][c];
+            __threadfence_block();
+            named_arrive(BAR_F, T);
+        }
+    } else {
+        // ---- update warps ----------------------------------------------------------------
+        float* yw = Yw + (size_t)w * NB * YL;
+#pragma unroll
+        for (int s = 0; s < SPW; ++s)
+#pragma unroll
+            for (int i = 0; i < RS; ++i) Pn[(tx + 32 * i) * PLD + w + W * s] = a[i][s];
+        __threadfence_block();
+        named_arrive(BAR_PANEL, T);
+#pragma unroll 1
+        for (int t = 0; t < NP; ++t) {
+            const int k0 = t * NB;
+            const int nb = (B - k0) < NB ? (B - k0) : NB;
+            const float* fs = Fs + (t & 1) * R32 * PLD;
+            named_sync(BAR_F, T);
+            // pivot rows of this warp's non-panel columns; their own entries are rebuilt from F
+            __syncwarp();
+            float mrow[RS];
+            gj_gather_pivot_rows<RS, CS, SPW, YL, NB>(a, s_piv[t & 1], nb, tx, yw, mrow);
+            __syncwarp();
+#pragma unroll
+            for (int i = 0; i < RS; ++i)
+#pragma unroll
+                for (int j = SPW; j < CS; ++j) a[i][j] *= mrow[i];
+            // (1) slots SPW .. 2 SPW - 1 first: the next panel's columns, handed to warp 0 at once
+            // (at the last panel they hold earlier columns, updated like the rest)
+#pragma unroll
+            for (int s = 0; s < NB; ++s) {
+                if (s >= nb) break;   // uniform
+                float f[RS];
+#pragma unroll
+                for (int i = 0; i < RS; ++i) f[i] = fs[(tx + 32 * i) * PLD + s];
+                const float* yr = yw + s * YL;
+#pragma unroll
+                for (int q = 0; q < SPW; ++q) {
+                    const float yv = yr[q];
+#pragma unroll
+                    for (int i = 0; i < RS; ++i) a[i][SPW + q] = fmaf(f[i], yv, a[i][SPW + q]);
+                }
+            }
+            if (t + 1 < NP) {
+                float* pn = Pn + ((t + 1) & 1) * R32 * PLD;
+#pragma unroll
+                for (int q = 0; q < SPW; ++q)
+#pragma unroll
+                    for (int i = 0; i < RS; ++i) pn[(tx + 32 * i) * PLD + w + W * q] = a[i][SPW + q];
+                __threadfence_block();
+                named_arrive(BAR_PANEL, T);
+            }
+            // (2) the remaining columns (slots 2 SPW .. CS - 1)
+#pragma unroll
+            for (int s = 0; s < NB; ++s) {
+                if (s >= nb) break;   // uniform
+                float f[RS];
+#pragma unroll
+                for (int i = 0; i < RS; ++i) f[i] = fs[(tx + 32 * i) * PLD + s];
+                const float* yr = yw + s * YL;
+#pragma unroll
+                for (int j0 = 0; j0 < CS - SPW; j0 += 4) {
+                    const float4 y4 = *reinterpret_cast<const float4*>(yr + j0);
+                    const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int j = SPW + j0 + q;
+                        if (j >= 2 * SPW && j < CS) {
+#pragma unroll
+                            for (int i = 0; i < RS; ++i) a[i][j] = fmaf(f[i], yv[q], a[i][j]);
+                        }
+                    }
+                }
+            }
+            // (3) the panel's own columns become F
+#pragma unroll
+            for (int s = 0; s < SPW; ++s)
+#pragma unroll
+                for (int i = 0; i < RS; ++i) a[i][s] = fs[(tx + 32 * i) * PLD + w + W * s];
+#pragma unroll
+            for (int i = 0; i < RS; ++i) {
+                float t0[SPW];
+#pragma unroll
+                for (int s = 0; s < SPW; ++s) t0[s] = a[i][s];
+#pragma unroll
+                for (int j = 0; j < CS - SPW; ++j) a[i][j] = a[i][j + SPW];
+#pragma unroll
+                for (int s = 0; s < SPW; ++s) a[i][CS - SPW + s] = t0[s];
+            }
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < B; t += T) invp[perm[t]] = t;
+    __syncthreads();
+    if (wq > 0) {
+#pragma unroll
+        for (int i = 0; i < RS; ++i)
+#pragma unroll
+            for (int j = 0; j < CS; ++j) {
+                const int r = tx + 32 * i, c = w + W * j;
+                if (r < B && c < B) tile[perm[c] * LD + invp[r]] = a[i][j];
+            }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < B * B; t += T) g[t] = tile[(t / B) * LD + (t % B)];
+}
+
 // ---- variants of the FP32 Gauss-Jordan kernel and their tuning --------------------------------
 // Two families.  Unblocked (variants 0..13): variant v < 4 unrolls the pivot loop kGjUnroll[v]
 // times (0 = fully, only for B <= 100); 4..8 are the column-owner form with kGjWarps[v - 4]
 // warps per element (valid while a thread's share of the block stays at most 128 values);
-// 9..13 the rotating column-owner form with kGjWarps[v - 9] warps.  Blocked (14..17):
-// k_gj_blk with kGjBlkWarps[v - 14] warps (valid while a thread holds at most 64 values).
+// 9..13 the rotating column-owner form with kGjWarps[v - 9] warps.  Blocked (14..21):
+// k_gj_blk with kGjBlkWarps[v - 14] warps and the look-ahead k_gj_la with 1 + kGjBlkWarps[v - 18]
+// warps (valid while a thread holds at most 64 values).
 // Within a family the variants do the same arithmetic in the same order, so the tuner's choice
 // never changes a result; the tuner times one family only (the blocked one where it is valid,
 // unless emg_params.block_kernels asks for the unblocked forms).
@@ -247,7 +467,8 @@ constexpr int kGjUnroll[] = {1, 4, 16, 0};
 constexpr int kGjWarps[] = {1, 2, 4, 8, 16};
 constexpr int kGjBlkWarps[] = {1, 2, 4, 8};
 constexpr int kGjBlkFirst = 14;
-constexpr int kGjVariants = 18;
+constexpr int kGjLaFirst = 18;   // look-ahead form, kGjBlkWarps[v - 18] update warps
+constexpr int kGjVariants = 22;
 
 template <int B, int W>
 constexpr bool gj_blk_valid() {
@@ -258,6 +479,14 @@ template <int B>
 static bool gj_variant_valid(int v) {
     if (v < 0 || v >= kGjVariants) return false;
     if (v < 4) return kGjUnroll[v] != 0 || B <= 100;
+    if (v >= kGjLaFirst) {
+        switch (kGjBlkWarps[v - kGjLaFirst]) {
+            case 1: return GjLa<B, 1>::VALID;
+            case 2: return GjLa<B, 2>::VALID;
+            case 4: return GjLa<B, 4>::VALID;
+            default: return GjLa<B, 8>::VALID;
+        }
+    }
     if (v >= kGjBlkFirst) {
         switch (kGjBlkWarps[v - kGjBlkFirst]) {
             case 1: return gj_blk_valid<B, 1>();
@@ -272,6 +501,7 @@ static bool gj_variant_valid(int v) {
 
 static std::string gj_variant_name(int v) {
     if (v < 4) return "tile unroll " + std::to_string(kGjUnroll[v]);
+    if (v >= kGjLaFirst) return "look-ahead 1+" + std::to_string(kGjBlkWarps[v - kGjLaFirst]) + " warps";
     if (v >= kGjBlkFirst) return "blocked " + std::to_string(kGjBlkWarps[v - kGjBlkFirst]) + " warps";
     return std::string(v < 9 ? "cols " : "rotating cols ") + std::to_string(kGjWarps[(v - 4) % 5]) + " warps";
 }
@@ -289,9 +519,26 @@ static cudaError_t gj_blk_go(unsigned E, float* blk, cudaStream_t st) {
     }
 }
 
+template <int B, int W>
+static cudaError_t gj_la_go(unsigned E, float* blk, cudaStream_t st) {
+    if constexpr (GjLa<B, W>::VALID) {
+        const size_t sm = GjLa<B, W>::SMEM;
+        cudaError_t e = cudaFuncSetAttribute(k_gj_la<B, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_gj_la<B, W><<<E, GjLa<B, W>::THREADS, sm, st>>>((int)E, blk);
+        return cudaGetLastError();
+    } else {
+        return cudaErrorInvalidValue;   // not reached: gj_dispatch checks the variant first
+    }
+}
+
 template <int B>
 static cudaError_t gj_launch(int v, unsigned E, float* blk, cudaStream_t st) {
     switch (v) {
+        case 18: return gj_la_go<B, 1>(E, blk, st);
+        case 19: return gj_la_go<B, 2>(E, blk, st);
+        case 20: return gj_la_go<B, 4>(E, blk, st);
+        case 21: return gj_la_go<B, 8>(E, blk, st);
         case 14: return gj_blk_go<B, 1>(E, blk, st);
         case 15: return gj_blk_go<B, 2>(E, blk, st);
         case 16: return gj_blk_go<B, 4>(E, blk, st);
@@ -366,7 +613,7 @@ emg_status tune_gj(emg_ctx* c) {
         bool blocked = false;
         if (c->prm.block_kernels != 3)
             for (int v = kGjBlkFirst; v < kGjVariants; ++v) blocked = blocked || gj_valid(L.B, v);
-        const int v_lo = blocked ? kGjBlkFirst : 0, v_hi = blocked ? kGjVariants : kGjBlkFirst;
+        const int v_lo = blocked ? kGjBlkFirst : 0, v_hi = blocked ? kGjVariants : kGjBlkFirst;   // 14..21 / 0..13
         if (!c->prm.autotune) {
             L.gj_variant = 0;
             for (int v = v_lo; v < v_hi; ++v)

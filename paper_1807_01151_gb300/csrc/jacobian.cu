@@ -21,7 +21,41 @@
 
 namespace emg {
 
-template <int D, int P, class S>
+// The Roe flux of a face point and the ghost state of a boundary point for dual-number
+// states; ROT: the face moves with the rotating frame (v_r at the point from fvr).
+template <bool ROT, class T>
+__device__ __forceinline__ void face_flux_d(const T UL[5], const T UR[5], const double n[3], double g,
+                                            const double* __restrict__ fvr, int64_t idx, T F[5]) {
+    if constexpr (ROT) {
+        const double vrn = fvr[idx * 3] * n[0] + fvr[idx * 3 + 1] * n[1] + fvr[idx * 3 + 2] * n[2];
+        roe_flux<T, true>(UL, UR, n, g, F, vrn);
+    } else {
+        roe_flux(UL, UR, n, g, F);
+    }
+}
+template <bool ROT, class T>
+__device__ __forceinline__ void ghost_d(const T UL[5], const double n[3], int bc, const double* __restrict__ wn,
+                                        const U5& uinf, double g, const double* __restrict__ fvr, int64_t idx,
+                                        T G[5]) {
+    if (bc == EMG_BC_WALL || bc == EMG_BC_SYMMETRY) {
+        const double nw[3] = {wn[0], wn[1], wn[2]};
+        if constexpr (ROT) {
+            const double vr[3] = {fvr[idx * 3], fvr[idx * 3 + 1], fvr[idx * 3 + 2]};
+            wall_ghost_rel(UL, nw, vr, g, G);
+        } else {
+            wall_ghost(UL, nw, G);
+        }
+    } else {
+        if constexpr (ROT) {
+            const double vr[3] = {fvr[idx * 3], fvr[idx * 3 + 1], fvr[idx * 3 + 2]};
+            farfield_ghost_rel(UL, n, uinf.v, g, vr, G);
+        } else {
+            farfield_ghost(UL, n, uinf.v, g, G);
+        }
+    }
+}
+
+template <int D, int P, class S, bool ROT>
 __global__ void __launch_bounds__(128) k_face_jac(int F, int F_int, const int* __restrict__ fL,
                                                   const int* __restrict__ fR, const int* __restrict__ fbc,
                                                   const double* __restrict__ fnrm,
@@ -30,6 +64,7 @@ __global__ void __launch_bounds__(128) k_face_jac(int F, int F_int, const int* _
                                                   const S* __restrict__ fpsiR,
                                                   const double* __restrict__ fwn,
                                                   const double* __restrict__ u, double g, U5 uinf,
+                                                  const double* __restrict__ fvr,
                                                   S* __restrict__ fjl, S* __restrict__ fjr) {
     using L = Lv<D, P>;
     constexpr int N = L::N, QF = L::QF;
@@ -63,7 +98,7 @@ __global__ void __launch_bounds__(128) k_face_jac(int F, int F_int, const int* _
             UR[a] = s;
             dR[a] = dconst<5, S>(s);
         }
-        roe_flux(dL, dR, n, g, Fd);
+        face_flux_d<ROT>(dL, dR, n, g, fvr, idx, Fd);
         for (int a = 0; a < 5; ++a)
             for (int b = 0; b < 5; ++b) fjl[idx * 25 + a * 5 + b] = am * Fd[a].d[b];
         Dual<5, S> cL[5];
@@ -71,20 +106,80 @@ __global__ void __launch_bounds__(128) k_face_jac(int F, int F_int, const int* _
             cL[a] = dconst<5, S>(UL[a]);
             dR[a].d[a] = (S)1;
         }
-        roe_flux(cL, dR, n, g, Fd);
+        face_flux_d<ROT>(cL, dR, n, g, fvr, idx, Fd);
         for (int a = 0; a < 5; ++a)
             for (int b = 0; b < 5; ++b) fjr[idx * 25 + a * 5 + b] = am * Fd[a].d[b];
     } else {
-        if (fbc[f] == EMG_BC_WALL || fbc[f] == EMG_BC_SYMMETRY) {
-            const int64_t bi = idx - (int64_t)F_int * QF;
-            const double nw[3] = {fwn[bi * 3], fwn[bi * 3 + 1], fwn[bi * 3 + 2]};
-            wall_ghost(dL, nw, dR);
-        } else {
-            farfield_ghost(dL, n, uinf.v, g, dR);
-        }
-        roe_flux(dL, dR, n, g, Fd);
+        ghost_d<ROT>(dL, n, fbc[f], fwn + (idx - (int64_t)F_int * QF) * 3, uinf, g, fvr, idx, dR);
+        face_flux_d<ROT>(dL, dR, n, g, fvr, idx, Fd);
         for (int a = 0; a < 5; ++a)
             for (int b = 0; b < 5; ++b) fjl[idx * 25 + a * 5 + b] = am * Fd[a].d[b];
+    }
+}
+
+// The same face Jacobians with one thread per (face point, side, direction b): the traces of a
+// block's PPB face points are formed once in shared memory (one thread per point, side and
+// component, the sums of k_face_jac in its order), then each thread differentiates the Roe flux
+// (on a boundary face: the flux through the ghost state) along U_side[b] alone, with a
+// one-direction dual number: column b of dF~/dU_side.  Forward mode computes every direction
+// with the same operations, so the columns are bitwise those of the five-direction kernel; the
+// flux value is recomputed per direction, for a tenth of the registers and ten threads per point.
+template <int D, int P, class S>
+struct FaceJacCol {
+    static constexpr int PPB = 12;   // face points per block (10 threads each)
+    static constexpr int THREADS = 128;
+};
+
+template <int D, int P, class S, bool ROT>
+__global__ void __launch_bounds__(128) k_face_jac_col(int F, int F_int, const int* __restrict__ fL,
+                                                      const int* __restrict__ fR, const int* __restrict__ fbc,
+                                                      const double* __restrict__ fnrm,
+                                                      const double* __restrict__ famag,
+                                                      const S* __restrict__ fpsiL,
+                                                      const S* __restrict__ fpsiR,
+                                                      const double* __restrict__ fwn,
+                                                      const double* __restrict__ u, double g, U5 uinf,
+                                                      const double* __restrict__ fvr,
+                                                      S* __restrict__ fjl, S* __restrict__ fjr) {
+    using L = Lv<D, P>;
+    constexpr int N = L::N, QF = L::QF, PPB = FaceJacCol<D, P, S>::PPB;
+    __shared__ S Ut[PPB][2][5];
+    const int64_t npts = (int64_t)F * QF;
+    const int64_t p0 = (int64_t)blockIdx.x * PPB;
+    const int tid = threadIdx.x;
+    const int pt = tid / 10, r = tid % 10, side = r / 5, c = r % 5;
+    const int64_t idx = p0 + pt;
+    const bool live = tid < PPB * 10 && idx < npts;
+    const int f = live ? (int)(idx / QF) : 0;
+    const bool used = live && (side == 0 || f < F_int);
+    if (used) {   // trace: component c on this side
+        const double* ue = u + (size_t)(side ? fR[f] : fL[f]) * 5 * N;
+        const S* ps = (side ? fpsiR : fpsiL) + idx * N;
+        S s = (S)0;
+        for (int i = 0; i < N; ++i) s += (S)ue[c * N + i] * ps[i];
+        Ut[pt][side][c] = s;
+    }
+    __syncthreads();
+    if (!used) return;
+    const int b = c;   // from here on: the derivative direction
+    const double n[3] = {fnrm[idx * 3], fnrm[idx * 3 + 1], fnrm[idx * 3 + 2]};
+    const S am = (S)famag[idx];
+    Dual<1, S> dL[5], dR[5], Fd[5];
+    for (int a = 0; a < 5; ++a) dL[a] = dconst<1, S>(Ut[pt][0][a]);
+    if (f < F_int) {
+        for (int a = 0; a < 5; ++a) dR[a] = dconst<1, S>(Ut[pt][1][a]);
+        if (side == 0)
+            dL[b].d[0] = (S)1;
+        else
+            dR[b].d[0] = (S)1;
+        face_flux_d<ROT>(dL, dR, n, g, fvr, idx, Fd);
+        S* out = side ? fjr : fjl;
+        for (int a = 0; a < 5; ++a) out[idx * 25 + a * 5 + b] = am * Fd[a].d[0];
+    } else {
+        dL[b].d[0] = (S)1;
+        ghost_d<ROT>(dL, n, fbc[f], fwn + (idx - (int64_t)F_int * QF) * 3, uinf, g, fvr, idx, dR);
+        face_flux_d<ROT>(dL, dR, n, g, fvr, idx, Fd);
+        for (int a = 0; a < 5; ++a) fjl[idx * 25 + a * 5 + b] = am * Fd[a].d[0];
     }
 }
 
@@ -202,7 +297,7 @@ __global__ void __launch_bounds__(DiagCfg<D, P>::THREADS, (DiagMinB<D, P, T>::V)
     const int* __restrict__ elem_face, const T* __restrict__ fpsiL, const T* __restrict__ fpsiR,
     const T* __restrict__ fjl, const T* __restrict__ fjr, const double* __restrict__ psic,
     const double* __restrict__ hlen, const double* __restrict__ cfl_dev, double g, int shifted,
-    T* __restrict__ out) {
+    const double* __restrict__ vvr, T* __restrict__ out) {
     using L = Lv<D, P>;
     constexpr int N = L::N, Q = L::Q, QF = L::QF, B = L::B, NF = L::NF;
     constexpr int QC = DiagCfg<D, P>::QC;
@@ -269,7 +364,14 @@ __global__ void __launch_bounds__(DiagCfg<D, P>::THREADS, (DiagMinB<D, P, T>::V)
                 Us[q][c] = s;
             }
             __syncthreads();
-            for (int t = tid; t < nq * D; t += blockDim.x) flux_jac_k(Us[t / D], (T)g, t % D, As[t / D][t % D]);
+            for (int t = tid; t < nq * D; t += blockDim.x) {
+                flux_jac_k(Us[t / D], (T)g, t % D, As[t / D][t % D]);
+                if (vvr) {   // rotating frame: A_k - (v_r)_k I
+                    const T vr = (T)vvr[((size_t)e * Q + q0 + t / D) * 3 + t % D];
+#pragma unroll
+                    for (int a = 0; a < 5; ++a) As[t / D][t % D][a * 6] -= vr;
+                }
+            }
             __syncthreads();
             if (active) {
                 for (int t = 0; t < nq; ++t) {
@@ -361,7 +463,7 @@ __global__ void __launch_bounds__(DiagRb<D, P>::THREADS, DiagRb<D, P>::MINB) k_d
     const int* __restrict__ elem_face, const float* __restrict__ fpsiL, const float* __restrict__ fpsiR,
     const float* __restrict__ fjl, const float* __restrict__ fjr, const double* __restrict__ psic,
     const double* __restrict__ hlen, const double* __restrict__ cfl_dev, double g, int shifted,
-    float* __restrict__ out) {
+    const double* __restrict__ vvr, float* __restrict__ out) {
     using L = Lv<D, P>;
     using R = DiagRb<D, P>;
     constexpr int N = L::N, Q = L::Q, QF = L::QF, B = L::B, NF = L::NF;
@@ -430,7 +532,14 @@ __global__ void __launch_bounds__(DiagRb<D, P>::THREADS, DiagRb<D, P>::MINB) k_d
                 Us[q][c] = s;
             }
             __syncthreads();
-            for (int t = tid; t < nq * D; t += blockDim.x) flux_jac_k(Us[t / D], (float)g, t % D, As[t / D][t % D]);
+            for (int t = tid; t < nq * D; t += blockDim.x) {
+                flux_jac_k(Us[t / D], (float)g, t % D, As[t / D][t % D]);
+                if (vvr) {   // rotating frame: A_k - (v_r)_k I
+                    const float vr = (float)vvr[((size_t)e * Q + q0 + t / D) * 3 + t % D];
+#pragma unroll
+                    for (int a = 0; a < 5; ++a) As[t / D][t % D][a * 6] -= vr;
+                }
+            }
             __syncthreads();
             if (active) {
 #pragma unroll 1
@@ -586,7 +695,7 @@ __global__ void __launch_bounds__(256) k_diag_blocks_tc(
     const int* __restrict__ elem_face, const float* __restrict__ fpsiL, const float* __restrict__ fpsiR,
     const float* __restrict__ fjl, const float* __restrict__ fjr, const double* __restrict__ psic,
     const double* __restrict__ hlen, const double* __restrict__ cfl_dev, double g, int shifted,
-    float* __restrict__ out, int* __restrict__ timeout_flag) {
+    const double* __restrict__ vvr, float* __restrict__ out, int* __restrict__ timeout_flag) {
     using C = TcAsm<D, P, BF16>;
     constexpr int N = C::N, Q = C::Q, QF = C::QF, NF = C::NF, B = C::B, KC = C::KC, KTOT = C::KTOT;
     constexpr int NPAD = C::NPAD, MPAD = C::MPAD, MROWS = C::MROWS, T = C::THREADS;
@@ -692,6 +801,11 @@ __global__ void __launch_bounds__(256) k_diag_blocks_tc(
             float A[25];
             if (k < Q) {
                 flux_jac_k(Uq[kl], (float)g, kk, A);
+                if (vvr) {   // rotating frame: A_k - (v_r)_k I
+                    const float vr = (float)vvr[((size_t)e * Q + k) * 3 + kk];
+#pragma unroll
+                    for (int a = 0; a < 5; ++a) A[a * 6] -= vr;
+                }
             } else if (k < KTOT && kk == 0) {
                 const int lf = (k - Q) / QF, tt = (k - Q) % QF, code = fcode[lf];
                 const float* fj = ((code & 1) ? fjr : fjl) + ((size_t)(code >> 1) * QF + tt) * 25;
@@ -888,6 +1002,37 @@ __global__ void k_bsr0(int E, int NF, int QF, const int* __restrict__ elem_face,
     row[ab] = diag;
 }
 
+// Jacobian of the rotating frame's source (Eq. euler: S = (0, -omega x (rho v), 0), linear in U):
+// dS_m/d(rho v)_n = -eps_{m k n} omega_k, so with the orthonormal basis every element's block
+// gains dS/dU on the momentum rows and columns of each mode i (the same i).  The Appendix's
+// printed dS/dU (Eq. dsdu) has the opposite sign; the sign here is that of S as written.
+// Added to D = dR/du (shifted = 0) or subtracted from P = I/dtau - D (shifted = 1); block rows
+// (a, i) of stride ld per element, element stride es.
+template <class T>
+__global__ void k_add_source(int64_t E, int N, int64_t es, int ld, int shifted, U5 om, T* __restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const double dS[3][3] = {{0.0, om.v[2], -om.v[1]}, {-om.v[2], 0.0, om.v[0]}, {om.v[1], -om.v[0], 0.0}};
+    const double sg = shifted ? -1.0 : 1.0;
+    T* b = out + e * es;
+    for (int i = 0; i < N; ++i)
+        for (int m = 0; m < 3; ++m)
+            for (int n = 0; n < 3; ++n)
+                if (m != n) b[(size_t)((1 + m) * N + i) * ld + (1 + n) * N + i] += (T)(sg * dS[m][n]);
+}
+
+template <class T>
+static emg_status add_source_jacobian(emg_ctx* c, int p, int shifted, T* out) {
+    if (!c->rot) return EMG_OK;
+    const LevelDev& L = c->lv[p];
+    U5 om{};
+    for (int k = 0; k < 3; ++k) om.v[k] = c->prm.omega[k];
+    { ProfScope _ps(c, PC_DIAG); k_add_source<T><<<(unsigned)((c->E + 127) / 128), 128, 0, c->stream>>>(
+        c->E, L.N, (int64_t)L.B * L.B, L.B, shifted, om, out); }
+    EMG_CHECK_LAUNCH(c);
+    return EMG_OK;
+}
+
 emg_status launch_face_jacobian(emg_ctx* c, int p, const double* u) {
     LevelDev& L = c->lv[p];
     const int F = (int)c->F, Fi = (int)c->F_int;
@@ -896,9 +1041,15 @@ emg_status launch_face_jacobian(emg_ctx* c, int p, const double* u) {
 #define EMG_FJ(DD, PP)                                                                                       \
     {                                                                                                        \
         const int64_t nf = (int64_t)F * Lv<DD, PP>::QF;                                                      \
-        { ProfScope _ps(c, PC_FACE_JAC); k_face_jac<DD, PP, double><<<(unsigned)((nf + 127) / 128), 128, 0, c->stream>>>(                             \
-            F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL, L.fpsiR, L.fwn, u, c->prm.gamma, ui, \
-            L.fjl, L.fjr); }                                                                                   \
+        ProfScope _ps(c, PC_FACE_JAC);                                                                       \
+        if (c->rot)                                                                                          \
+            k_face_jac<DD, PP, double, true><<<(unsigned)((nf + 127) / 128), 128, 0, c->stream>>>(           \
+                F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL, L.fpsiR, L.fwn, u,          \
+                c->prm.gamma, ui, L.fvr, L.fjl, L.fjr);                                                      \
+        else                                                                                                 \
+            k_face_jac<DD, PP, double, false><<<(unsigned)((nf + 127) / 128), 128, 0, c->stream>>>(          \
+                F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL, L.fpsiR, L.fwn, u,          \
+                c->prm.gamma, ui, nullptr, L.fjl, L.fjr);                                                    \
         EMG_CHECK_LAUNCH(c);                                                                                 \
     }
     EMG_DISPATCH_DP(c->dim, p, EMG_FJ)
@@ -916,12 +1067,12 @@ emg_status launch_diag_blocks(emg_ctx* c, int p, const double* u, const double* 
         ProfScope _ps(c, PC_DIAG);                                                                          \
         k_diag_blocks<DD, PP, double><<<(unsigned)c->E, DiagCfg<DD, PP>::THREADS, 0, c->stream>>>(          \
             (int)c->E, nmax, u, L.vpsi, L.vgw, c->elem_face, L.fpsiL, L.fpsiR, L.fjl, L.fjr, c->psic, c->h, \
-            cfl_dev, c->prm.gamma, shifted, out);                                                           \
+            cfl_dev, c->prm.gamma, shifted, L.vvr, out);                                                    \
     }
     EMG_DISPATCH_DP(c->dim, p, EMG_DB)
 #undef EMG_DB
     EMG_CHECK_LAUNCH(c);
-    return EMG_OK;
+    return add_source_jacobian(c, p, shifted, out);
 }
 
 emg_status launch_face_jacobian32(emg_ctx* c, int p, const double* u) {
@@ -933,9 +1084,24 @@ emg_status launch_face_jacobian32(emg_ctx* c, int p, const double* u) {
     {                                                                                                        \
         const int64_t nf = (int64_t)F * Lv<DD, PP>::QF;                                                      \
         ProfScope _ps(c, PC_FACE_JAC);                                                                       \
-        k_face_jac<DD, PP, float><<<(unsigned)((nf + 127) / 128), 128, 0, c->stream>>>(                      \
-            F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL32, L.fpsiR32, L.fwn, u,          \
-            c->prm.gamma, ui, L.fjl32, L.fjr32);                                                             \
+        constexpr int PPB = FaceJacCol<DD, PP, float>::PPB;                                                  \
+        const unsigned g1 = (unsigned)((nf + 127) / 128), gc = (unsigned)((nf + PPB - 1) / PPB);             \
+        if (c->prm.block_kernels == 3 && c->rot)                                                             \
+            k_face_jac<DD, PP, float, true><<<g1, 128, 0, c->stream>>>(                                      \
+                F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL32, L.fpsiR32, L.fwn, u,      \
+                c->prm.gamma, ui, L.fvr, L.fjl32, L.fjr32);                                                  \
+        else if (c->prm.block_kernels == 3)                                                                  \
+            k_face_jac<DD, PP, float, false><<<g1, 128, 0, c->stream>>>(                                     \
+                F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL32, L.fpsiR32, L.fwn, u,      \
+                c->prm.gamma, ui, nullptr, L.fjl32, L.fjr32);                                                \
+        else if (c->rot)                                                                                     \
+            k_face_jac_col<DD, PP, float, true><<<gc, 128, 0, c->stream>>>(                                  \
+                F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL32, L.fpsiR32, L.fwn, u,      \
+                c->prm.gamma, ui, L.fvr, L.fjl32, L.fjr32);                                                  \
+        else                                                                                                 \
+            k_face_jac_col<DD, PP, float, false><<<gc, 128, 0, c->stream>>>(                                 \
+                F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL32, L.fpsiR32, L.fwn, u,      \
+                c->prm.gamma, ui, nullptr, L.fjl32, L.fjr32);                                                \
     }
     EMG_DISPATCH_DP(c->dim, p, EMG_FJ32)
 #undef EMG_FJ32
@@ -954,10 +1120,10 @@ static emg_status diag_tc_go(emg_ctx* c, const double* u, const double* cfl_dev,
         ProfScope _ps(c, PC_DIAG);
         k_diag_blocks_tc<D, P, BF16><<<(unsigned)c->E, C::THREADS, C::SMEM, c->stream>>>(
             (int)c->E, nmax, u, L.vpsi32, L.vgw32, c->elem_face, L.fpsiL32, L.fpsiR32, L.fjl32, L.fjr32, c->psic,
-            c->h, cfl_dev, c->prm.gamma, shifted, out, &c->sc->timeout);
+            c->h, cfl_dev, c->prm.gamma, shifted, L.vvr, out, &c->sc->timeout);
     }
     EMG_CHECK_LAUNCH(c);
-    return EMG_OK;
+    return add_source_jacobian(c, P, shifted, out);
 }
 
 // Block assembly of the float32 block forms (levels p >= 1): on the tensor cores or, where the
@@ -981,16 +1147,16 @@ emg_status launch_diag_blocks32(emg_ctx* c, int p, const double* u, const double
         if (c->prm.block_kernels == 3)                                                                      \
             k_diag_blocks<DD, PP, float><<<(unsigned)c->E, DiagCfg<DD, PP>::THREADS, 0, c->stream>>>(       \
                 (int)c->E, nmax, u, L.vpsi32, L.vgw32, c->elem_face, L.fpsiL32, L.fpsiR32, L.fjl32, L.fjr32,  \
-                c->psic, c->h, cfl_dev, c->prm.gamma, shifted, out);                                        \
+                c->psic, c->h, cfl_dev, c->prm.gamma, shifted, L.vvr, out);                                 \
         else                                                                                                \
             k_diag_blocks_rb<DD, PP><<<(unsigned)c->E, DiagRb<DD, PP>::THREADS, 0, c->stream>>>(            \
                 (int)c->E, nmax, u, L.vpsi32, L.vgw32, c->elem_face, L.fpsiL32, L.fpsiR32, L.fjl32, L.fjr32,  \
-                c->psic, c->h, cfl_dev, c->prm.gamma, shifted, out);                                        \
+                c->psic, c->h, cfl_dev, c->prm.gamma, shifted, L.vvr, out);                                 \
     }
         EMG_DISPATCH_DP(c->dim, p, EMG_DB32)
 #undef EMG_DB32
         EMG_CHECK_LAUNCH(c);
-        return EMG_OK;
+        return add_source_jacobian(c, p, shifted, out);
     }
 #define EMG_TC(DD, PP) return bf ? diag_tc_go<DD, PP, true>(c, u, cfl_dev, shifted, out) \
                              : diag_tc_go<DD, PP, false>(c, u, cfl_dev, shifted, out)
@@ -1033,6 +1199,13 @@ emg_status launch_bsr0(emg_ctx* c) {
     { ProfScope _ps(c, PC_BSR0); k_bsr0<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>((int)c->E, 2 * c->dim, L.QF, c->elem_face, L.fpsiL,
                                                                L.fpsiR, L.fjl, L.fjr, (int)c->F_int, c->bsr); }
     EMG_CHECK_LAUNCH(c);
+    if (c->rot) {   // p = 0: the diagonal 5x5 block (first of each element's row) gains dS/dU
+        U5 om{};
+        for (int k = 0; k < 3; ++k) om.v[k] = c->prm.omega[k];
+        { ProfScope _ps(c, PC_BSR0); k_add_source<double><<<(unsigned)((c->E + 127) / 128), 128, 0, c->stream>>>(
+            c->E, 1, (1 + 2 * c->dim) * 25, 5, 0, om, c->bsr); }
+        EMG_CHECK_LAUNCH(c);
+    }
     return EMG_OK;
 }
 

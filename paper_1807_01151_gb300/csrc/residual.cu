@@ -5,13 +5,18 @@
 // with both traces, boundary faces with the ghost state of Sec. 3.3) and stores
 // w|n dS| F~; k_volume does, per element, the volume quadrature and the projection of
 // its faces' fluxes (sign -1 on the L side, +1 on the R side: no atomics, deterministic).
+// ROT: a frame rotating with angular velocity omega (Eq. euler): the fluxes carry the velocity
+// relative to the frame v_r = omega x x (tabulated at the points), F_k - (v_r)_k U, the face
+// fluxes move with v_r . n, the ghosts are taken relative to the frame, and the source
+// S = (0, -rho omega x v, 0), linear in U, adds -omega x u_{m,i} to the momentum modes (the
+// orthonormal basis makes int psi_i S = -omega x (rho v)_i).
 #include "common.cuh"
 #include "dispatch.cuh"
 #include "euler.cuh"
 
 namespace emg {
 
-template <int D, int P>
+template <int D, int P, bool ROT>
 __global__ void __launch_bounds__(128) k_face_flux(int F, int F_int, const int* __restrict__ fL,
                                                    const int* __restrict__ fR, const int* __restrict__ fbc,
                                                    const double* __restrict__ fnrm,
@@ -20,7 +25,7 @@ __global__ void __launch_bounds__(128) k_face_flux(int F, int F_int, const int* 
                                                    const double* __restrict__ fpsiR,
                                                    const double* __restrict__ fwn,
                                                    const double* __restrict__ u, double g, U5 uinf,
-                                                   double* __restrict__ fhat) {
+                                                   const double* __restrict__ fvr, double* __restrict__ fhat) {
     using L = Lv<D, P>;
     constexpr int N = L::N, QF = L::QF;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -52,11 +57,26 @@ __global__ void __launch_bounds__(128) k_face_flux(int F, int F_int, const int* 
         // symmetry planes)
         const int64_t bi = idx - (int64_t)F_int * QF;
         const double nw[3] = {fwn[bi * 3], fwn[bi * 3 + 1], fwn[bi * 3 + 2]};
-        wall_ghost(UL, nw, UR);
+        if constexpr (ROT) {
+            const double vr[3] = {fvr[idx * 3], fvr[idx * 3 + 1], fvr[idx * 3 + 2]};
+            wall_ghost_rel(UL, nw, vr, g, UR);
+        } else {
+            wall_ghost(UL, nw, UR);
+        }
     } else {
-        farfield_ghost(UL, n, uinf.v, g, UR);
+        if constexpr (ROT) {
+            const double vr[3] = {fvr[idx * 3], fvr[idx * 3 + 1], fvr[idx * 3 + 2]};
+            farfield_ghost_rel(UL, n, uinf.v, g, vr, UR);
+        } else {
+            farfield_ghost(UL, n, uinf.v, g, UR);
+        }
     }
-    roe_flux(UL, UR, n, g, Fl);
+    if constexpr (ROT) {
+        const double vrn = fvr[idx * 3] * n[0] + fvr[idx * 3 + 1] * n[1] + fvr[idx * 3 + 2] * n[2];
+        roe_flux<double, true>(UL, UR, n, g, Fl, vrn);
+    } else {
+        roe_flux(UL, UR, n, g, Fl);
+    }
     const double am = famag[idx];
 #pragma unroll
     for (int a = 0; a < 5; ++a) fhat[idx * 5 + a] = am * Fl[a];
@@ -76,11 +96,12 @@ struct VolCfg {
     static constexpr int QC = P == 0 ? 1 : (QC0 < L::Q ? (QC0 < 1 ? 1 : QC0) : L::Q);   // points per chunk
 };
 
-template <int D, int P>
+template <int D, int P, bool ROT>
 __global__ void __launch_bounds__(VolCfg<D, P>::THREADS) k_volume(
     int E, const double* __restrict__ u, const double* __restrict__ vpsi, const double* __restrict__ vgw,
     const int* __restrict__ elem_face, const double* __restrict__ fpsiL, const double* __restrict__ fpsiR,
-    const double* __restrict__ fhat, const double* __restrict__ tau, double g, double* __restrict__ R) {
+    const double* __restrict__ fhat, const double* __restrict__ tau, double g, const double* __restrict__ vvr,
+    U5 om, double* __restrict__ R) {
     using L = Lv<D, P>;
     using CF = VolCfg<D, P>;
     constexpr int N = L::N, Q = L::Q, QF = L::QF, B = L::B, NF = L::NF;
@@ -114,6 +135,13 @@ __global__ void __launch_bounds__(VolCfg<D, P>::THREADS) k_volume(
                 }
                 double Fk[3][5];
                 flux_k(U, g, Fk);
+                if constexpr (ROT) {   // F_k - (v_r)_k U
+                    const double* vr = vvr + ((size_t)e * Q + q0 + qq) * 3;
+#pragma unroll
+                    for (int k = 0; k < D; ++k)
+#pragma unroll
+                        for (int a = 0; a < 5; ++a) Fk[k][a] -= vr[k] * U[a];
+                }
 #pragma unroll
                 for (int k = 0; k < D; ++k)
 #pragma unroll
@@ -160,6 +188,12 @@ __global__ void __launch_bounds__(VolCfg<D, P>::THREADS) k_volume(
 #pragma unroll
         for (int a = 0; a < 5; ++a) acc[a] += sg * s[a];
     }
+    if constexpr (ROT) {   // source: -omega x (rho v)_i
+        const double mx = us[el2][1 * N + i2], my = us[el2][2 * N + i2], mz = us[el2][3 * N + i2];
+        acc[1] -= om.v[1] * mz - om.v[2] * my;
+        acc[2] -= om.v[2] * mx - om.v[0] * mz;
+        acc[3] -= om.v[0] * my - om.v[1] * mx;
+    }
     double* Re = R + (size_t)e2 * B + i2;
     const double* te = tau ? tau + (size_t)e2 * B + i2 : nullptr;
 #pragma unroll
@@ -172,19 +206,28 @@ emg_status launch_residual(emg_ctx* c, int p, const double* u, const double* tau
     U5 ui;
     for (int a = 0; a < 5; ++a) ui.v[a] = c->uinf[a];
     const double g = c->prm.gamma;
-#define EMG_RES(DD, PP)                                                                                        \
+    U5 om{};
+    for (int k = 0; k < 3; ++k) om.v[k] = c->prm.omega[k];
+#define EMG_RES_ROT(DD, PP, RR)                                                                                 \
     {                                                                                                          \
         const int64_t nf = (int64_t)F * Lv<DD, PP>::QF;                                                        \
-        { ProfScope _ps(c, PC_RES_FACE); k_face_flux<DD, PP><<<(unsigned)((nf + 127) / 128), 128, 0, c->stream>>>(                              \
-            F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL, L.fpsiR, L.fwn, u, g, ui, L.fhat); }     \
+        { ProfScope _ps(c, PC_RES_FACE); k_face_flux<DD, PP, RR><<<(unsigned)((nf + 127) / 128), 128, 0, c->stream>>>( \
+            F, Fi, c->face_L, c->face_R, c->face_bc, L.fnrm, L.famag, L.fpsiL, L.fpsiR, L.fwn, u, g, ui, L.fvr,     \
+            L.fhat); }                                                                                         \
         EMG_CHECK_LAUNCH(c);                                                                                   \
         constexpr int ET = VolCfg<DD, PP>::ET;                                                                 \
-        { ProfScope _ps(c, PC_RES_VOL); k_volume<DD, PP><<<(unsigned)((E + ET - 1) / ET), VolCfg<DD, PP>::THREADS, 0, c->stream>>>(    \
-            E, u, L.vpsi, L.vgw, c->elem_face, L.fpsiL, L.fpsiR, L.fhat, tau, g, R); }                           \
+        { ProfScope _ps(c, PC_RES_VOL); k_volume<DD, PP, RR><<<(unsigned)((E + ET - 1) / ET), VolCfg<DD, PP>::THREADS, 0, \
+            c->stream>>>(E, u, L.vpsi, L.vgw, c->elem_face, L.fpsiL, L.fpsiR, L.fhat, tau, g, L.vvr, om, R); }      \
         EMG_CHECK_LAUNCH(c);                                                                                   \
     }
+#define EMG_RES(DD, PP)                   \
+    if (c->rot)                           \
+        EMG_RES_ROT(DD, PP, true)         \
+    else                                  \
+        EMG_RES_ROT(DD, PP, false)
     EMG_DISPATCH_DP(c->dim, p, EMG_RES)
 #undef EMG_RES
+#undef EMG_RES_ROT
     return EMG_OK;
 }
 

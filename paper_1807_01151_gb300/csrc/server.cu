@@ -54,7 +54,8 @@ emg_status estimate(const emg_mesh_desc* m, const emg_params* prm, int64_t* byte
     for (int64_t k = 0; k < m->n_elems * nf; ++k) nb += m->face_bc[k] >= 0 ? 1 : 0;
     if ((m->n_elems * nf - nb) % 2 != 0) return EMG_ERR_ARG;
     const int64_t F_int = (m->n_elems * nf - nb) / 2;
-    *bytes = estimate_bytes(m->dim, m->n_elems, F_int + nb, F_int, prm->p_max, prm->krylov_m, prm->prec);
+    const bool rot = prm->omega[0] != 0.0 || prm->omega[1] != 0.0 || prm->omega[2] != 0.0;
+    *bytes = estimate_bytes(m->dim, m->n_elems, F_int + nb, F_int, prm->p_max, prm->krylov_m, prm->prec, rot);
     return EMG_OK;
 }
 

@@ -10,6 +10,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "dispatch.cuh"
 
 namespace emg {
 
@@ -244,10 +245,20 @@ __device__ __forceinline__ void eval_basis(const double x[D], int e, int n, int 
     }
 }
 
+// Frame velocity v_r = omega x x of a rotating frame at the point x (z = 0 in 2-D).
+template <int D>
+__device__ __forceinline__ void frame_velocity(const U5& om, const double x[D], double* vr) {
+    const double x3[3] = {x[0], x[1], D == 3 ? x[D - 1] : 0.0};
+    vr[0] = om.v[1] * x3[2] - om.v[2] * x3[1];
+    vr[1] = om.v[2] * x3[0] - om.v[0] * x3[2];
+    vr[2] = om.v[0] * x3[1] - om.v[1] * x3[0];
+}
+
 template <int D, int NM>
 __global__ void k_vol_tables(int E, int n, int nmax, int q, const double* __restrict__ ex, const double* __restrict__ gl,
                              const double* __restrict__ xc, const double* __restrict__ Lh,
-                             const int* __restrict__ exps, const double* __restrict__ C, double* vpsi, double* vgw) {
+                             const int* __restrict__ exps, const double* __restrict__ C, double* vpsi, double* vgw,
+                             U5 om, double* vvr) {
     int Q = 1;
     for (int d = 0; d < D; ++d) Q *= q;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -262,6 +273,7 @@ __global__ void k_vol_tables(int E, int n, int nmax, int q, const double* __rest
     for (int i = 0; i < n; ++i) vpsi[((size_t)e * Q + t) * n + i] = psi[i];
     for (int d = 0; d < D; ++d)
         for (int i = 0; i < n; ++i) vgw[(((size_t)e * D + d) * Q + t) * n + i] = W * g[i][d];
+    if (vvr) frame_velocity<D>(om, x, vvr + idx * 3);
 }
 
 template <int D, int NM>
@@ -271,7 +283,7 @@ __global__ void k_face_tables(int F, int F_int, int n, int nmax, int q, const in
                               const double* __restrict__ Lh, const int* __restrict__ exps,
                               const double* __restrict__ C, const double* __restrict__ ewn, int has_wn,
                               const int* __restrict__ fbc, double* fnrm, double* famag, double* fpsiL,
-                              double* fpsiR, double* fwn) {
+                              double* fpsiR, double* fwn, U5 om, double* fvr) {
     int QF = 1;
     for (int d = 0; d < D - 1; ++d) QF *= q;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -308,6 +320,7 @@ __global__ void k_face_tables(int F, int F_int, int n, int nmax, int q, const in
         const int64_t bi = (int64_t)(f - F_int) * QF + t;
         for (int k = 0; k < 3; ++k) fwn[bi * 3 + k] = nw[k];
     }
+    if (fvr) frame_velocity<D>(om, x, fvr + idx * 3);
     eval_basis<D, NM>(x, eL, n, nmax, xc, Lh, exps, C, psi, g);
     for (int i = 0; i < n; ++i) fpsiL[idx * n + i] = psi[i];
     if (f < F_int) {
@@ -383,24 +396,27 @@ struct FaceKey {
 template <int D, int NM>
 static emg_status build_tables(emg_ctx* c, int nmax, const int* exps_d) {
     const int E = (int)c->E;
+    U5 om{};
+    for (int k = 0; k < 3; ++k) om.v[k] = c->prm.omega[k];
     for (int p = 0; p <= c->p_max; ++p) {
         LevelDev& L = c->lv[p];
         const int thr = 128;
         int64_t nv = (int64_t)E * L.Q;
         { ProfScope _ps(c, PC_SETUP); k_vol_tables<D, NM><<<(unsigned)((nv + thr - 1) / thr), thr, 0, c->stream>>>(
-            E, L.N, nmax, L.q, c->elem_x, c->gl, c->xc, c->Lh, exps_d, c->C, L.vpsi, L.vgw); }
+            E, L.N, nmax, L.q, c->elem_x, c->gl, c->xc, c->Lh, exps_d, c->C, L.vpsi, L.vgw, om, L.vvr); }
         EMG_CHECK_LAUNCH(c);
         int64_t nf = c->F * L.QF;
         { ProfScope _ps(c, PC_SETUP); k_face_tables<D, NM><<<(unsigned)((nf + thr - 1) / thr), thr, 0, c->stream>>>(
             (int)c->F, (int)c->F_int, L.N, nmax, L.q, c->face_L, c->face_fL, c->face_R, c->elem_x, c->gl, c->xc,
-            c->Lh, exps_d, c->C, c->elem_wn, c->has_wn, c->face_bc, L.fnrm, L.famag, L.fpsiL, L.fpsiR, L.fwn); }
+            c->Lh, exps_d, c->C, c->elem_wn, c->has_wn, c->face_bc, L.fnrm, L.famag, L.fpsiL, L.fpsiR, L.fwn, om,
+            L.fvr); }
         EMG_CHECK_LAUNCH(c);
     }
     return EMG_OK;
 }
 
 // Device bytes that setup_device_mesh allocates, item by item (admission control).
-int64_t estimate_bytes(int dim, int64_t E, int64_t F, int64_t F_int, int p_max, int m, int prec) {
+int64_t estimate_bytes(int dim, int64_t E, int64_t F, int64_t F_int, int p_max, int m, int prec, bool rot) {
     const int nf = 2 * dim, nn = 1 << dim;
     const int nmax = n_modes(dim, p_max);
     const int64_t Fi1 = std::max<int64_t>(F_int, 1), Fb1 = std::max<int64_t>(F - F_int, 1);
@@ -411,6 +427,7 @@ int64_t estimate_bytes(int dim, int64_t E, int64_t F, int64_t F_int, int p_max, 
         b += E * Q * N * (1 + dim) * 8;                                         // vpsi, vgw
         b += F * QF * (3 + 1 + N + 5 + 25) * 8 + Fi1 * QF * (N + 25) * 8 + Fb1 * QF * 3 * 8;
         b += 6 * E * B * 8;                                                     // v, v0, tau, un, r, r2
+        if (rot) b += (E * Q + F * QF) * 3 * 8;                                 // frame velocities
         if (p > 0) {
             if (blocks_f32(prec))
                 b += E * B * B * 4 + E * Q * N * (1 + dim) * 4 + F * QF * (N + 25) * 4 + Fi1 * QF * (N + 25) * 4;
@@ -495,7 +512,7 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
     c->dim = D;
     // -- admission --
     const int m_kr = c->prm.krylov_m;
-    const int64_t need = estimate_bytes(D, E, F, F_int, c->p_max, m_kr, c->prm.prec);
+    const int64_t need = estimate_bytes(D, E, F, F_int, c->p_max, m_kr, c->prm.prec, c->rot);
     size_t fr = 0, tot = 0;
     EMG_CUDA_TRY(c, cudaMemGetInfo(&fr, &tot));
     if (need > (int64_t)fr) {
@@ -584,6 +601,10 @@ emg_status setup_device_mesh(emg_ctx* c, const emg_mesh_desc* m) {
         EMG_ALLOC(L.fhat, double, F * L.QF * 5);
         EMG_ALLOC(L.fjl, double, F * L.QF * 25);
         EMG_ALLOC(L.fjr, double, std::max<int64_t>(F_int, 1) * L.QF * 25);
+        if (c->rot) {
+            EMG_ALLOC(L.vvr, double, E * L.Q * 3);
+            EMG_ALLOC(L.fvr, double, F * L.QF * 3);
+        }
         if (p > 0) {
             if (blocks_f32(c->prm.prec)) {
                 EMG_ALLOC(L.blk32, float, E * L.B * L.B);

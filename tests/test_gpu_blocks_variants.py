@@ -131,7 +131,9 @@ def test_fp32_inverse_at_every_level(name, mk, pmax, kernels):
 @pytest.mark.parametrize("name,mk,pmax", LEVEL_CASES + [("sphere6x1x1x2_p4", lambda: cubed_sphere_shell(1, 2), 4)])
 def test_fp32_assembly_forms_are_bitwise_the_same(name, mk, pmax):
     """The register-blocked SIMT assembly (several b and j per thread) sums every entry's terms
-    in the order of the one-row-per-thread form: bitwise the same blocks at every level."""
+    in the order of the one-row-per-thread form, and the face Jacobians differentiated one
+    direction per thread equal the five-direction dual numbers' columns: bitwise the same
+    blocks at every level (block_kernels 2 against the earlier forms, 3)."""
     import paper_1807_01151_gb300 as pkg
     desc = mk()
     dg = DG(desc, pmax)
@@ -265,7 +267,7 @@ def test_symmetry_plane_residual_and_vcycle(mk, p):
 
 def test_unbuilt_options_are_rejected():
     import paper_1807_01151_gb300 as pkg
-    for kw in (dict(quad_extra=3), dict(omega=(0.0, 0.0, 1.0)), dict(jac_freeze=-1), dict(krylov_tol=-1.0)):
+    for kw in (dict(quad_extra=3), dict(omega=(1.0, 0.0, 0.0)), dict(jac_freeze=-1), dict(krylov_tol=-1.0)):
         with pytest.raises(pkg.EmgError) as ei:
             pkg.Solver(ogrid(8, 2), p_max=1, **kw)
         assert ei.value.status == 1, kw

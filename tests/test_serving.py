@@ -191,3 +191,19 @@ def test_cancel_of_an_active_request_leaves_the_others_intact():
     assert res[keep]["status"] == 0 and res[keep]["cycles"] == cycles_alone
     np.testing.assert_array_equal(srv.take_state(keep), U_alone)
     srv.close()
+
+
+@pytest.mark.gpu
+def test_served_golden_request_ends_at_the_oracle_steady_state():
+    """The golden case (32x16 O-grid, p = 2, Ma 0.3; tests/golden, written from oracle/ alone)
+    served among other solves, in the FP64 and the FP32-block form, ends at the oracle's steady
+    state to 1e-9 (the fixed point R = 0 does not depend on the preconditioner or the mix)."""
+    import os
+    from tests.helpers import rel_err
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", "cyl32x16_p2_steady.npz"))
+    reqs = [((32, 16), 2, 0.3, 0), ((16, 8), 3, 0.3, 1), ((32, 16), 2, 0.3, 1), ((24, 12), 2, 0.2, 0)]
+    ids, res, states, _ = _serve(reqs, max_active=3)
+    for k in (0, 2):
+        r = res[ids[k]]
+        assert r["status"] == 0 and r["res_final"] <= 1e-10 * r["res0"], r
+        assert rel_err(states[ids[k]], g["u"]) < 1e-9, (k, rel_err(states[ids[k]], g["u"]))
