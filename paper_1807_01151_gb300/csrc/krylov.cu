@@ -172,8 +172,8 @@ __device__ __forceinline__ void slice_dots(const double* V, const double* w, int
 #pragma unroll
             for (int i = 0; i < ARN_CHUNK; ++i) {
                 const int col = c0 + i;
-                if (col < nv) v[i] += V[(size_t)col * K0 + k] * wk;
-                else if (col == nv && with_ww) v[i] += wk * wk;
+                if (col < nv) v[i] = __fma_rn(V[(size_t)col * K0 + k], wk, v[i]);
+                else if (col == nv && with_ww) v[i] = __fma_rn(wk, wk, v[i]);
             }
         }
         int c = 0;
@@ -201,24 +201,24 @@ __device__ __forceinline__ void spmv_rows(int64_t k0, int64_t k1, int NF, const 
         if (xr) {
             const double de = dt[e];
 #pragma unroll
-            for (int b = 0; b < 5; ++b) s += row[a * 5 + b] * (de * xr[(size_t)e * 5 + b]);
+            for (int b = 0; b < 5; ++b) s = __fma_rn(row[a * 5 + b], de * xr[(size_t)e * 5 + b], s);
             for (int lf = 0; lf < NF; ++lf) {
                 const int n = nbr[(size_t)e * NF + lf];
                 if (n < 0) continue;
                 const double dn = dt[n];
                 const double* blk = row + (1 + lf) * 25;
 #pragma unroll
-                for (int b = 0; b < 5; ++b) s += blk[a * 5 + b] * (dn * xr[(size_t)n * 5 + b]);
+                for (int b = 0; b < 5; ++b) s = __fma_rn(blk[a * 5 + b], dn * xr[(size_t)n * 5 + b], s);
             }
         } else {
 #pragma unroll
-            for (int b = 0; b < 5; ++b) s += row[a * 5 + b] * __ldcg(x + (size_t)e * 5 + b);
+            for (int b = 0; b < 5; ++b) s = __fma_rn(row[a * 5 + b], __ldcg(x + (size_t)e * 5 + b), s);
             for (int lf = 0; lf < NF; ++lf) {
                 const int n = nbr[(size_t)e * NF + lf];
                 if (n < 0) continue;
                 const double* blk = row + (1 + lf) * 25;
 #pragma unroll
-                for (int b = 0; b < 5; ++b) s += blk[a * 5 + b] * __ldcg(x + (size_t)n * 5 + b);   // other blocks
+                for (int b = 0; b < 5; ++b) s = __fma_rn(blk[a * 5 + b], __ldcg(x + (size_t)n * 5 + b), s);   // other blocks
             }
         }
         out[k] = dt[e] * (scale * s);
@@ -232,13 +232,13 @@ __device__ __forceinline__ double a_row(int64_t k, int NF, const double* __restr
     const double* row = bsr + (size_t)e * (1 + NF) * 25;
     double s = 0.0;
 #pragma unroll
-    for (int b = 0; b < 5; ++b) s += row[a * 5 + b] * __ldcg(x + (size_t)e * 5 + b);
+    for (int b = 0; b < 5; ++b) s = __fma_rn(row[a * 5 + b], __ldcg(x + (size_t)e * 5 + b), s);
     for (int lf = 0; lf < NF; ++lf) {
         const int n = nbr[(size_t)e * NF + lf];
         if (n < 0) continue;
         const double* blk = row + (1 + lf) * 25;
 #pragma unroll
-        for (int b = 0; b < 5; ++b) s += blk[a * 5 + b] * __ldcg(x + (size_t)n * 5 + b);
+        for (int b = 0; b < 5; ++b) s = __fma_rn(blk[a * 5 + b], __ldcg(x + (size_t)n * 5 + b), s);
     }
     return dt[e] * s;
 }
@@ -260,7 +260,7 @@ __device__ __forceinline__ void arn_half1(int j, int64_t K0, int64_t k0, int64_t
     reduce_cols(partA, nb, stride, j + 2, h1, sh);
     for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
         double s = w[k];
-        for (int i = 0; i <= j; ++i) s -= h1[i] * V[(size_t)i * K0 + k];
+        for (int i = 0; i <= j; ++i) s = __fma_rn(-h1[i], V[(size_t)i * K0 + k], s);
         w[k] = s;
     }
     __syncthreads();
@@ -281,7 +281,7 @@ __device__ __forceinline__ bool arn_half2(int j, int m, int64_t K0, int64_t k0, 
                                           double (*sh)[ARN_MAXCOL]) {
     reduce_cols(partB, nb, stride, j + 2, h2, sh);
     double hh = 0.0;
-    for (int i = 0; i <= j; ++i) hh += h2[i] * h2[i];
+    for (int i = 0; i <= j; ++i) hh = __fma_rn(h2[i], h2[i], hh);
     const double hn = sqrt(fmax(h2[j + 1] - hh, 0.0));
     const double w0 = sqrt(h1[j + 1]);
     const bool brk = !(hn > 1e-12 * w0);
@@ -301,7 +301,7 @@ __device__ __forceinline__ bool arn_half2(int j, int m, int64_t K0, int64_t k0, 
     // c = H~_j h2 over l = 0..j+1
     for (int l = threadIdx.x; l <= j + 1; l += ARN_THREADS) {
         double c = 0.0;
-        for (int i = (l > 0 ? l - 1 : 0); i <= j; ++i) c += Hs[l * ARN_HLD + i] * h2[i];
+        for (int i = (l > 0 ? l - 1 : 0); i <= j; ++i) c = __fma_rn(Hs[l * ARN_HLD + i], h2[i], c);
         cs[l] = c;
     }
     __syncthreads();
@@ -311,18 +311,200 @@ __device__ __forceinline__ bool arn_half2(int j, int m, int64_t K0, int64_t k0, 
         double t = a_row(k, NF, bsr, nbr, dt, w1);
         for (int i = 0; i <= j; ++i) {
             const double vi = V[(size_t)i * K0 + k];
-            s -= h2[i] * vi;
-            t -= cs[i] * vi;
+            s = __fma_rn(-h2[i], vi, s);
+            t = __fma_rn(-cs[i], vi, t);
         }
         const double v = s * ih;
         vn[k] = v;
-        t -= cs[j + 1] * v;
+        t = __fma_rn(-cs[j + 1], v, t);
         wn[k] = t * ih;
     }
     __syncthreads();
     slice_dots(V, wn, K0, k0, k1, j + 2, 1, partA_blk, sh);
     return true;
 }
+
+// ---- the persistent process with this thread's Krylov rows in registers -------------------
+// When every thread owns at most one row (chunk <= ARN_THREADS) and m <= MV, the persistent
+// kernel keeps the thread's entries of v_0 .. v_j in registers for the whole process instead of
+// reading them back from V at every sweep and dot product (V is still written: the combination
+// step reads it).  The sweeps, dot products and reductions are those of arn_half1, arn_half2 and
+// slice_dots in the same order, so the results are bitwise the memory form's (and the
+// barrier-free kernels', which share that form).  Loops over i <= j run over the register
+// array with a uniform early exit, so every index is a compile-time one.
+template <int MV>
+__device__ __forceinline__ void slice_dots_rv(const double (&vrow)[MV], double wk, bool has, int nv, double* dst,
+                                              double (*sh)[ARN_MAXCOL]) {
+    const int ncol = nv + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c0 = 0; c0 < MV + 1; c0 += ARN_CHUNK) {
+        if (c0 >= ncol) break;   // uniform
+        double v[ARN_CHUNK];
+#pragma unroll
+        for (int i = 0; i < ARN_CHUNK; ++i) v[i] = 0.0;
+        if (has) {
+#pragma unroll
+            for (int i = 0; i < ARN_CHUNK; ++i) {
+                const int col = c0 + i;
+                if (col < MV && col < nv)
+                    v[i] = __fma_rn(vrow[col < MV ? col : 0], wk, v[i]);
+                else if (col == nv)
+                    v[i] = __fma_rn(wk, wk, v[i]);
+            }
+        }
+        int c = 0;
+        const double x = warp_sum8(v, lane, &c);
+        if ((lane & 3) == 0 && c0 + c < ncol) sh[warp][c0 + c] = x;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncol; c += ARN_THREADS) {
+        double s = 0.0;
+        for (int wv = 0; wv < ARN_WARPS; ++wv) s += sh[wv][c];
+        dst[c] = s;
+    }
+}
+
+template <int MV>
+__device__ __forceinline__ void arn_half1_rv(int j, int nb, int stride, const double (&vrow)[MV], bool has, int64_t k,
+                                             double* w, double& wk, const double* partA, double* partB_blk,
+                                             double* h1, double (*sh)[ARN_MAXCOL]) {
+    reduce_cols(partA, nb, stride, j + 2, h1, sh);
+    double s = 0.0;
+    if (has) {
+        s = w[k];
+#pragma unroll
+        for (int i = 0; i < MV; ++i) {
+            if (i > j) break;   // uniform
+            s = __fma_rn(-h1[i], vrow[i], s);
+        }
+        w[k] = s;
+    }
+    wk = s;
+    __syncthreads();
+    slice_dots_rv<MV>(vrow, s, has, j + 1, partB_blk, sh);
+}
+
+template <int MV>
+__device__ __forceinline__ bool arn_half2_rv(int j, int m, int64_t K0, int64_t k, bool has, int nb, int stride,
+                                             int NF, const double* __restrict__ bsr, const int* __restrict__ nbr,
+                                             const double* __restrict__ dt, double* V, double (&vrow)[MV], double w1k,
+                                             const double* w1, double* wn, double* H, double* Hs, const double* partB,
+                                             double* partA_blk, const double* h1, double* h2, double* cs,
+                                             DevScalars* sc, double (*sh)[ARN_MAXCOL]) {
+    reduce_cols(partB, nb, stride, j + 2, h2, sh);
+    double hh = 0.0;
+    for (int i = 0; i <= j; ++i) hh = __fma_rn(h2[i], h2[i], hh);
+    const double hn = sqrt(fmax(h2[j + 1] - hh, 0.0));
+    const double w0 = sqrt(h1[j + 1]);
+    const bool brk = !(hn > 1e-12 * w0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h1[i] + h2[i];
+        H[(size_t)(j + 1) * m + j] = hn;
+        sc->m_used = j + 1;
+        sc->hsub = hn;
+        sc->w0 = w0;
+        if (!isfinite(hn)) sc->nonfinite = 1;
+        if (brk) sc->broken = 1;
+    }
+    if (brk || j + 1 == m) return false;   // uniform: every block reduced the same values
+    for (int i = threadIdx.x; i <= j + 1; i += ARN_THREADS) Hs[i * ARN_HLD + j] = i <= j ? h1[i] + h2[i] : hn;
+    __syncthreads();
+    const double ih = 1.0 / hn;
+    for (int l = threadIdx.x; l <= j + 1; l += ARN_THREADS) {
+        double c = 0.0;
+        for (int i = (l > 0 ? l - 1 : 0); i <= j; ++i) c = __fma_rn(Hs[l * ARN_HLD + i], h2[i], c);
+        cs[l] = c;
+    }
+    __syncthreads();
+    double wnk = 0.0;
+    if (has) {
+        double s = w1k;
+        double t = a_row(k, NF, bsr, nbr, dt, w1);
+#pragma unroll
+        for (int i = 0; i < MV; ++i) {
+            if (i > j) break;   // uniform
+            const double vi = vrow[i];
+            s = __fma_rn(-h2[i], vi, s);
+            t = __fma_rn(-cs[i], vi, t);
+        }
+        const double v = s * ih;
+        V[(size_t)(j + 1) * K0 + k] = v;
+#pragma unroll
+        for (int i = 0; i < MV; ++i)
+            if (i == j + 1) vrow[i] = v;
+        t = __fma_rn(-cs[j + 1], v, t);
+        wnk = t * ih;
+        wn[k] = wnk;
+    }
+    __syncthreads();
+    slice_dots_rv<MV>(vrow, wnk, has, j + 2, partA_blk, sh);
+    return true;
+}
+
+template <int MV>
+__global__ void __launch_bounds__(ARN_THREADS, 2) k_arnoldi_rv(int64_t K0, int E, int NF, int m,
+                                                               const double* __restrict__ bsr,
+                                                               const int* __restrict__ nbr,
+                                                               const double* __restrict__ dt,
+                                                               const double* __restrict__ r, double* __restrict__ V,
+                                                               double* __restrict__ wbuf, double* __restrict__ H,
+                                                               double* __restrict__ partA, double* __restrict__ partB,
+                                                               double* __restrict__ partC, int stride, GridBar* bar,
+                                                               long long budget, DevScalars* sc) {
+    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
+    __shared__ double h1[ARN_MAXCOL], h2[ARN_MAXCOL], cs[ARN_MAXCOL], red[8];
+    __shared__ double Hs[(ARN_HLD + 1) * ARN_HLD];
+    __shared__ int s_ok;
+    unsigned epoch = 0;
+    const unsigned nb = gridDim.x;
+    const int64_t chunk = (K0 + nb - 1) / nb;   // <= ARN_THREADS (checked by the launcher)
+    const int64_t k0 = (int64_t)blockIdx.x * chunk;
+    const int64_t k1 = (k0 + chunk) < K0 ? (k0 + chunk) : K0;
+    const int64_t k = k0 + threadIdx.x;
+    const bool has = k < k1;
+    double vrow[MV];
+#pragma unroll
+    for (int i = 0; i < MV; ++i) vrow[i] = 0.0;
+    {
+        double v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (has) {
+            const double x = dt[k / 5] * r[k];
+            v[0] = __fma_rn(x, x, v[0]);
+        }
+        block_reduce_store(v, 1, partC + (size_t)blockIdx.x * stride, sh);
+    }
+    if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
+    reduce_cols(partC, nb, stride, 1, red, sh);
+    const double beta = sqrt(red[0]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->beta = beta;
+        sc->m_used = 0;
+        sc->broken = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
+        if (!isfinite(beta)) sc->nonfinite = 1;
+    }
+    if (beta == 0.0 || !isfinite(beta)) return;   // uniform across blocks
+    const double ib = 1.0 / beta;
+    if (has) {
+        vrow[0] = dt[k / 5] * r[k] * ib;
+        V[k] = vrow[0];
+    }
+    spmv_rows(k0, k1, NF, bsr, nbr, dt, nullptr, r, ib, wbuf);   // A v_1 from the inputs: no barrier
+    __syncthreads();
+    slice_dots_rv<MV>(vrow, has ? wbuf[k] : 0.0, has, 1, partA + (size_t)blockIdx.x * stride, sh);
+    for (int j = 0; j < m; ++j) {
+        double* w = wbuf + (size_t)(j & 1) * K0;
+        if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
+        double w1k = 0.0;
+        arn_half1_rv<MV>(j, (int)nb, stride, vrow, has, k, w, w1k, partA, partB + (size_t)blockIdx.x * stride, h1, sh);
+        if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
+        if (!arn_half2_rv<MV>(j, m, K0, k, has, (int)nb, stride, NF, bsr, nbr, dt, V, vrow, w1k, w,
+                              wbuf + (size_t)((j + 1) & 1) * K0, H, Hs, partB, partA + (size_t)blockIdx.x * stride, h1,
+                              h2, cs, sc, sh))
+            break;
+    }
+}
+constexpr int ARN_RV = 32;   // Krylov rows held in registers by k_arnoldi_rv (m <= 32)
 
 // Two grid barriers per Krylov step (one per reduction).
 __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int NF, int m,
@@ -346,7 +528,7 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
         double v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
             const double x = dt[k / 5] * r[k];
-            v[0] += x * x;
+            v[0] = __fma_rn(x, x, v[0]);
         }
         block_reduce_store(v, 1, partC + (size_t)blockIdx.x * stride, sh);
     }
@@ -415,7 +597,7 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arn_start(ArnArgs A) {
     double v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
         const double x = A.dt[k / 5] * A.r[k];
-        v[0] += x * x;
+        v[0] = __fma_rn(x, x, v[0]);
     }
     block_reduce_store(v, 1, A.partC + (size_t)blockIdx.x * A.stride, sh);
 }
@@ -765,10 +947,13 @@ emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, do
     const int64_t K0 = 5 * c->E;
     const int m = c->prm.krylov_m;
     // one cooperative launch: every block must be co-resident for the grid barriers
-    int per_sm = 0, nsm = 0;
+    int per_sm = 0, nsm = 0, per_sm_rv = 0;
     EMG_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi, ARN_THREADS, 0));
+    EMG_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_rv, k_arnoldi_rv<ARN_RV>, ARN_THREADS, 0));
     EMG_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
     const int64_t nb = arnoldi_blocks(K0, nsm, per_sm, c->red_blocks);
+    // rows in registers: one row per thread at most, every block co-resident, m <= ARN_RV
+    const bool rows_in_regs = m <= ARN_RV && (K0 + nb - 1) / nb <= ARN_THREADS && nb <= (int64_t)nsm * per_sm_rv;
     const int stride = MAX_KRYLOV + 8;
     double* partA = c->partial;
     double* partB = partA + (size_t)c->red_blocks * stride;
@@ -811,8 +996,8 @@ emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, do
         {
             ProfScope _ps(c, PC_ARNOLDI);
             auto launch = [&]() {
-                return cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3((unsigned)nb), dim3(ARN_THREADS), args, 0,
-                                                   c->stream);
+                const void* fn = rows_in_regs ? (const void*)k_arnoldi_rv<ARN_RV> : (const void*)k_arnoldi;
+                return cudaLaunchCooperativeKernel(fn, dim3((unsigned)nb), dim3(ARN_THREADS), args, 0, c->stream);
             };
             if (c->capturing) {
                 EMG_CUDA_TRY(c, launch());
