@@ -183,18 +183,34 @@ __device__ __forceinline__ void primitives(const T U[5], double g, T& rho, T v[3
     p = (g - 1.0) * (U[4] - 0.5 * rho * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
 }
 
-// Normal flux F(U).n
+// Normal flux F(U).n from U and its velocity and pressure
 template <class T>
-__device__ __forceinline__ void flux_n(const T U[5], const double n[3], double g, T F[5]) {
-    T rho, v[3], p;
-    primitives(U, g, rho, v, p);
+__device__ __forceinline__ void flux_n_vp(const T U[5], const T v[3], const T& p, const double n[3], T F[5]) {
     T qn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
-    T mq = rho * qn;
+    T mq = U[0] * qn;
     F[0] = mq;
     F[1] = mq * v[0] + p * n[0];
     F[2] = mq * v[1] + p * n[1];
     F[3] = mq * v[2] + p * n[2];
     F[4] = (U[4] + p) * qn;
+}
+
+// Normal flux F(U).n
+template <class T>
+__device__ __forceinline__ void flux_n(const T U[5], const double n[3], double g, T F[5]) {
+    T rho, v[3], p;
+    primitives(U, g, rho, v, p);
+    flux_n_vp(U, v, p, n, F);
+}
+
+// Primitives and 1/rho (computed once: velocity, enthalpy and flux all use it)
+template <class T>
+__device__ __forceinline__ void primitives_ir(const T U[5], double g, T& ir, T v[3], T& p) {
+    ir = inv_(U[0]);
+    v[0] = U[1] * ir;
+    v[1] = U[2] * ir;
+    v[2] = U[3] * ir;
+    p = (g - 1.0) * (U[4] - 0.5 * U[0] * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
 }
 
 // Cartesian flux component k (double only; used by the volume integral).
@@ -222,11 +238,12 @@ __device__ __forceinline__ void flux_k(const double U[5], double g, double F[3][
 template <class T, bool ROT = false>
 __device__ __forceinline__ void roe_flux(const T UL[5], const T UR[5], const double n[3], double g, T F[5],
                                          double vrn = 0.0) {
-    T rL, vL[3], pL, rR, vR[3], pR;
-    primitives(UL, g, rL, vL, pL);
-    primitives(UR, g, rR, vR, pR);
-    T HL = (UL[4] + pL) * inv_(rL);
-    T HR = (UR[4] + pR) * inv_(rR);
+    T irL, vL[3], pL, irR, vR[3], pR;
+    primitives_ir(UL, g, irL, vL, pL);
+    primitives_ir(UR, g, irR, vR, pR);
+    const T rL = UL[0], rR = UR[0];
+    T HL = (UL[4] + pL) * irL;
+    T HR = (UR[4] + pR) * irR;
     T sL = sqrt_(rL), sR = sqrt_(rR);
     T iden = inv_(sL + sR);
     T u[3];
@@ -259,8 +276,8 @@ __device__ __forceinline__ void roe_flux(const T UL[5], const T UR[5], const dou
     }
     T w1 = l1 * a1, w2 = l2 * a2, w5 = l5 * a5, ws = l2 * rho;
     T FL[5], FR[5];
-    flux_n(UL, n, g, FL);
-    flux_n(UR, n, g, FR);
+    flux_n_vp(UL, vL, pL, n, FL);
+    flux_n_vp(UR, vR, pR, n, FR);
     if constexpr (ROT) {
 #pragma unroll
         for (int a = 0; a < 5; ++a) {
