@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--start-seeds", type=int, default=3,
                     help="extra solves of the first form from the free stream perturbed by 1e-13 (relative, "
                          "seeded normal draws): the spread of the cycle count to 1e-10, which rounding decides")
+    ap.add_argument("--krylov-f32", type=int, default=-1, choices=[-1, 0, 1],
+                    help="Arnoldi process of the EXP1 step in float32 (emg_params.krylov_f32; -1: float32 "
+                         "with the float32 block forms)")
     ap.add_argument("--block-kernels", type=int, default=0, choices=[0, 1, 2, 3],
                     help="float32 block kernels: 0 the built-in choice per level, 1 tensor cores, 2 SIMT")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-10 solves")
@@ -279,7 +282,7 @@ def measure(pkg, torch, mesh, W, prec, args, world, local, rank, with_clocks, pe
     torch.cuda.synchronize()
     t_setup = time.perf_counter()
     s = pkg.Solver(mesh, p_max=W["p_max"], mach=W["mach"], prec=prec, stream=stream.cuda_stream,
-                   block_kernels=args.block_kernels)
+                   block_kernels=args.block_kernels, krylov_f32=args.krylov_f32)
     torch.cuda.synchronize()
     t_setup = time.perf_counter() - t_setup
     E, N = s.E, s.n_modes(W["p_max"])
@@ -539,7 +542,7 @@ def main():
                        "form": PREC_NAMES[precs[0]],
                        "l2": "inputs larger than L2: tables and block factors stream > 1 GB per V-cycle",
                        "timed_path": "captured V-cycle graphs replayed, profiler off",
-                       "block_kernels": args.block_kernels,
+                       "block_kernels": args.block_kernels, "krylov_f32": args.krylov_f32,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "residual_gdofs": head["residual_gdofs"], "residual_ms": head["residual_ms"],
             "time_to_1e-10": head.get("time_to_1e-10"),

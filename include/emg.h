@@ -145,6 +145,14 @@ typedef struct {
                               unblocked column-owner form); 3: the SIMT forms with the
                               unblocked Gauss-Jordan everywhere.  The forms differ only in
                               rounding; the BF16 form always assembles on the tensor cores. */
+    int32_t krylov_f32;    /* precision of the Arnoldi process of the EXP1 step: 1: its basis,
+                              products, dot products and reductions in float32 (the Hessenberg
+                              matrix, phi_1 and the combination stay FP64; happy breakdown at
+                              h_{j+1,j} <= 1e-5 ||A v_j||); 0: all FP64; -1 (default): float32
+                              with the float32 block forms (EMG_PREC_FP32_BLOCKS,
+                              EMG_PREC_BF16_BLOCKS), FP64 with EMG_PREC_FP64.  The EXP1 step only
+                              corrects the coarse level, so the fixed point R = 0 is unchanged
+                              (as with the float32 block factors).  Other values: EMG_ERR_ARG. */
 } emg_params;
 
 typedef struct {

@@ -28,7 +28,7 @@ class ParamsC(C.Structure):
                 ("prec", C.c_int32), ("cuda_stream", C.c_void_p), ("lag_blocks", C.c_int32),
                 ("use_graph", C.c_int32), ("autotune", C.c_int32), ("coop_krylov", C.c_int32),
                 ("krylov_tol", C.c_double), ("exp_dt_global", C.c_int32), ("jac_freeze", C.c_int32),
-                ("quad_extra", C.c_int32), ("omega", C.c_double * 3), ("block_kernels", C.c_int32)]
+                ("quad_extra", C.c_int32), ("omega", C.c_double * 3), ("block_kernels", C.c_int32), ("krylov_f32", C.c_int32)]
 
 
 class CycleInfoC(C.Structure):
@@ -156,7 +156,7 @@ def mesh_desc(mesh):
 def make_params(p_max=2, mach=0.3, alpha_deg=0.0, gamma=1.4, rk_stages=4, krylov_m=30, cfl_max=100.0,
                 exp_dt_factor=0.0, pre_smooth=2, prec=0, stream=None, lag_blocks=0, use_graph=1, autotune=1,
                 coop_krylov=1, krylov_tol=0.0, exp_dt_global=0, jac_freeze=1, quad_extra=2, omega=(0.0, 0.0, 0.0),
-                block_kernels=0):
+                block_kernels=0, krylov_f32=-1):
     prm = ParamsC()
     load().emg_default_params(C.byref(prm))
     prm.gamma, prm.mach, prm.alpha_deg = gamma, mach, alpha_deg
@@ -174,6 +174,7 @@ def make_params(p_max=2, mach=0.3, alpha_deg=0.0, gamma=1.4, rk_stages=4, krylov
     for k in range(3):
         prm.omega[k] = float(omega[k])
     prm.block_kernels = int(block_kernels)
+    prm.krylov_f32 = int(krylov_f32)
     return prm
 
 

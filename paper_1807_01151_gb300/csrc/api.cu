@@ -354,6 +354,7 @@ void emg_default_params(emg_params* p) {
     p->quad_extra = 2;
     p->omega[0] = p->omega[1] = p->omega[2] = 0.0;
     p->block_kernels = 0;
+    p->krylov_f32 = -1;
 }
 
 const char* emg_build_info(void) {
@@ -390,6 +391,8 @@ emg_status emg_create_mesh(const emg_mesh_desc* m, const emg_params* prm, emg_ct
         return fail(c, EMG_ERR_ARG, "only the rule q = p + 2 is built (quad_extra 2)");
     if (prm->block_kernels < 0 || prm->block_kernels > 3)
         return fail(c, EMG_ERR_ARG, "block_kernels must be 0, 1, 2 or 3");
+    if (prm->krylov_f32 < -1 || prm->krylov_f32 > 1) return fail(c, EMG_ERR_ARG, "krylov_f32 must be -1, 0 or 1");
+    if (c->prm.krylov_f32 < 0) c->prm.krylov_f32 = blocks_f32(prm->prec) ? 1 : 0;
     if (!std::isfinite(prm->omega[0]) || !std::isfinite(prm->omega[1]) || !std::isfinite(prm->omega[2]))
         return fail(c, EMG_ERR_ARG, "omega must be finite");
     if (m->dim == 2 && (prm->omega[0] != 0.0 || prm->omega[1] != 0.0))

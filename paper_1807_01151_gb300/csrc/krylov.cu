@@ -79,28 +79,41 @@ constexpr int ARN_MAXCOL = MAX_KRYLOV + 8;
 constexpr int ARN_WARPS = ARN_THREADS / 32;
 constexpr int ARN_SUB = 8;    // threads per column in the cross-block reduction
 
+// Arithmetic of the Arnoldi process in the basis' precision T (double, or float for the float32
+// Krylov form): explicit fused multiply-adds (so that every form of the process computes the
+// same bits), and the happy-breakdown threshold h_{j+1,j} <= tol ||A v_j|| at that precision.
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <class T>
+__device__ __forceinline__ T arn_breakdown_tol();
+template <>
+__device__ __forceinline__ double arn_breakdown_tol<double>() { return 1e-12; }
+template <>
+__device__ __forceinline__ float arn_breakdown_tol<float>() { return 1e-5f; }
+
 // Warp sums of the 8 values v[0..8) of every lane with 9 shuffle-adds per lane: at each of
 // the first three levels a lane keeps half of its columns and receives its partner's
 // partial sums of them (a transposing butterfly), then two plain levels.  Afterwards lane l
 // holds the warp sum of column 4 b4(l) + 2 b3(l) + b2(l) (b_k = bit k of l); returns it.
 // The order of the additions is fixed.
-__device__ __forceinline__ double warp_sum8(const double v[8], int lane, int* col) {
+template <class T>
+__device__ __forceinline__ T warp_sum8(const T v[8], int lane, int* col) {
     const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
-    double a[4], b[2];
+    T a[4], b[2];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        const double send = u16 ? v[c] : v[c + 4];
-        const double keep = u16 ? v[c + 4] : v[c];
+        const T send = u16 ? v[c] : v[c + 4];
+        const T keep = u16 ? v[c + 4] : v[c];
         a[c] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
     }
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-        const double send = u8 ? a[c] : a[c + 2];
-        const double keep = u8 ? a[c + 2] : a[c];
+        const T send = u8 ? a[c] : a[c + 2];
+        const T keep = u8 ? a[c + 2] : a[c];
         b[c] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
     }
-    const double send = u4 ? b[0] : b[1];
-    double x = (u4 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    const T send = u4 ? b[0] : b[1];
+    T x = (u4 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
     x += __shfl_xor_sync(0xffffffffu, x, 2);
     x += __shfl_xor_sync(0xffffffffu, x, 1);
     *col = (u16 ? 4 : 0) + (u8 ? 2 : 0) + (u4 ? 1 : 0);
@@ -109,21 +122,22 @@ __device__ __forceinline__ double warp_sum8(const double v[8], int lane, int* co
 
 // Block-reduce v[0..n) (n <= ARN_CHUNK): warp shuffles, then one barrier; dst[0..n) from
 // threads 0..n-1 (fixed order).
-__device__ __forceinline__ void block_reduce_store(double v[ARN_CHUNK], int n, double* dst,
-                                                   double (*sh)[ARN_MAXCOL]) {
+template <class T>
+__device__ __forceinline__ void block_reduce_store(T v[ARN_CHUNK], int n, T* dst,
+                                                   T (*sh)[ARN_MAXCOL]) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (n == 1) {
-        double x = v[0];
+        T x = v[0];
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (lane == 0) sh[warp][0] = x;
     } else {
         int c = 0;
-        const double x = warp_sum8(v, lane, &c);
+        const T x = warp_sum8<T>(v, lane, &c);
         if ((lane & 3) == 0) sh[warp][c] = x;
     }
     __syncthreads();
     if (threadIdx.x < n) {
-        double s = 0.0;
+        T s = 0.0;
         for (int w = 0; w < ARN_WARPS; ++w) s += sh[w][threadIdx.x];
         dst[threadIdx.x] = s;
     }
@@ -133,15 +147,16 @@ __device__ __forceinline__ void block_reduce_store(double v[ARN_CHUNK], int n, d
 // out_sh[c] = sum over blocks b of part[b * stride + c], c < ncol, identical in every block:
 // ARN_SUB threads per column sum a fixed stride of blocks (eight loads issued together, then
 // added in order), then a fixed shuffle tree.
-__device__ __forceinline__ void reduce_cols(const double* part, int nb, int stride, int ncol, double* out_sh,
-                                            double (*sh)[ARN_MAXCOL]) {
+template <class T>
+__device__ __forceinline__ void reduce_cols(const T* part, int nb, int stride, int ncol, T* out_sh,
+                                            T (*sh)[ARN_MAXCOL]) {
     const int sub = threadIdx.x % ARN_SUB;
     for (int c0 = 0; c0 < ncol; c0 += ARN_THREADS / ARN_SUB) {
         const int c = c0 + threadIdx.x / ARN_SUB;
-        double v = 0.0;
+        T v = 0.0;
         if (c < ncol) {
             for (int b0 = sub; b0 < nb; b0 += 8 * ARN_SUB) {
-                double x[8];
+                T x[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int b = b0 + u * ARN_SUB;
@@ -159,30 +174,31 @@ __device__ __forceinline__ void reduce_cols(const double* part, int nb, int stri
 
 // dst[i] (i < nv) = V[i] . w over this block's slice, plus w . w at index nv if with_ww
 // (warp shuffles per chunk of columns, one barrier for all of them).
-__device__ __forceinline__ void slice_dots(const double* V, const double* w, int64_t K0, int64_t k0, int64_t k1,
-                                           int nv, int with_ww, double* dst, double (*sh)[ARN_MAXCOL]) {
+template <class T>
+__device__ __forceinline__ void slice_dots(const T* V, const T* w, int64_t K0, int64_t k0, int64_t k1,
+                                           int nv, int with_ww, T* dst, T (*sh)[ARN_MAXCOL]) {
     const int ncol = nv + with_ww;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int c0 = 0; c0 < ncol; c0 += ARN_CHUNK) {
-        double v[ARN_CHUNK];
+        T v[ARN_CHUNK];
 #pragma unroll
         for (int i = 0; i < ARN_CHUNK; ++i) v[i] = 0.0;
         for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
-            const double wk = w[k];
+            const T wk = w[k];
 #pragma unroll
             for (int i = 0; i < ARN_CHUNK; ++i) {
                 const int col = c0 + i;
-                if (col < nv) v[i] = __fma_rn(V[(size_t)col * K0 + k], wk, v[i]);
-                else if (col == nv && with_ww) v[i] = __fma_rn(wk, wk, v[i]);
+                if (col < nv) v[i] = fma_t(V[(size_t)col * K0 + k], wk, v[i]);
+                else if (col == nv && with_ww) v[i] = fma_t(wk, wk, v[i]);
             }
         }
         int c = 0;
-        const double x = warp_sum8(v, lane, &c);
+        const T x = warp_sum8<T>(v, lane, &c);
         if ((lane & 3) == 0 && c0 + c < ncol) sh[warp][c0 + c] = x;
     }
     __syncthreads();
     for (int c = threadIdx.x; c < ncol; c += ARN_THREADS) {
-        double s = 0.0;
+        T s = 0.0;
         for (int wv = 0; wv < ARN_WARPS; ++wv) s += sh[wv][c];
         dst[c] = s;
     }
@@ -190,57 +206,59 @@ __device__ __forceinline__ void slice_dots(const double* V, const double* w, int
 
 // out[k] = scale * dt_e * (J_0 x)_k for this block's rows; x may belong to other blocks
 // (read through L2) and is either a vector or, when xr != nullptr, dt .* xr computed on the fly.
+template <class T>
 __device__ __forceinline__ void spmv_rows(int64_t k0, int64_t k1, int NF, const double* __restrict__ bsr,
                                           const int* __restrict__ nbr, const double* __restrict__ dt,
-                                          const double* x, const double* __restrict__ xr, double scale,
-                                          double* __restrict__ out) {
+                                          const T* x, const double* __restrict__ xr, T scale,
+                                          T* __restrict__ out) {
     for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
         const int e = (int)(k / 5), a = (int)(k % 5);
         const double* row = bsr + (size_t)e * (1 + NF) * 25;
-        double s = 0.0;
+        T s = 0.0;
         if (xr) {
             const double de = dt[e];
 #pragma unroll
-            for (int b = 0; b < 5; ++b) s = __fma_rn(row[a * 5 + b], de * xr[(size_t)e * 5 + b], s);
+            for (int b = 0; b < 5; ++b) s = fma_t((T)row[a * 5 + b], (T)(de * xr[(size_t)e * 5 + b]), s);
             for (int lf = 0; lf < NF; ++lf) {
                 const int n = nbr[(size_t)e * NF + lf];
                 if (n < 0) continue;
                 const double dn = dt[n];
                 const double* blk = row + (1 + lf) * 25;
 #pragma unroll
-                for (int b = 0; b < 5; ++b) s = __fma_rn(blk[a * 5 + b], dn * xr[(size_t)n * 5 + b], s);
+                for (int b = 0; b < 5; ++b) s = fma_t((T)blk[a * 5 + b], (T)(dn * xr[(size_t)n * 5 + b]), s);
             }
         } else {
 #pragma unroll
-            for (int b = 0; b < 5; ++b) s = __fma_rn(row[a * 5 + b], __ldcg(x + (size_t)e * 5 + b), s);
+            for (int b = 0; b < 5; ++b) s = fma_t((T)row[a * 5 + b], __ldcg(x + (size_t)e * 5 + b), s);
             for (int lf = 0; lf < NF; ++lf) {
                 const int n = nbr[(size_t)e * NF + lf];
                 if (n < 0) continue;
                 const double* blk = row + (1 + lf) * 25;
 #pragma unroll
-                for (int b = 0; b < 5; ++b) s = __fma_rn(blk[a * 5 + b], __ldcg(x + (size_t)n * 5 + b), s);   // other blocks
+                for (int b = 0; b < 5; ++b) s = fma_t((T)blk[a * 5 + b], __ldcg(x + (size_t)n * 5 + b), s);   // other blocks
             }
         }
-        out[k] = dt[e] * (scale * s);
+        out[k] = (T)dt[e] * (scale * s);
     }
 }
 
 // Row k of A x = DT J_0 x for the vector x (other blocks' entries read through L2).
-__device__ __forceinline__ double a_row(int64_t k, int NF, const double* __restrict__ bsr, const int* __restrict__ nbr,
-                                        const double* __restrict__ dt, const double* x) {
+template <class T>
+__device__ __forceinline__ T a_row(int64_t k, int NF, const double* __restrict__ bsr, const int* __restrict__ nbr,
+                                        const double* __restrict__ dt, const T* x) {
     const int e = (int)(k / 5), a = (int)(k % 5);
     const double* row = bsr + (size_t)e * (1 + NF) * 25;
-    double s = 0.0;
+    T s = 0.0;
 #pragma unroll
-    for (int b = 0; b < 5; ++b) s = __fma_rn(row[a * 5 + b], __ldcg(x + (size_t)e * 5 + b), s);
+    for (int b = 0; b < 5; ++b) s = fma_t((T)row[a * 5 + b], __ldcg(x + (size_t)e * 5 + b), s);
     for (int lf = 0; lf < NF; ++lf) {
         const int n = nbr[(size_t)e * NF + lf];
         if (n < 0) continue;
         const double* blk = row + (1 + lf) * 25;
 #pragma unroll
-        for (int b = 0; b < 5; ++b) s = __fma_rn(blk[a * 5 + b], __ldcg(x + (size_t)n * 5 + b), s);
+        for (int b = 0; b < 5; ++b) s = fma_t((T)blk[a * 5 + b], __ldcg(x + (size_t)n * 5 + b), s);
     }
-    return dt[e] * s;
+    return (T)dt[e] * s;
 }
 
 // The two halves of Krylov step j, shared by the persistent kernel and the barrier-free
@@ -254,17 +272,18 @@ __device__ __forceinline__ double a_row(int64_t k, int NF, const double* __restr
 
 // First half: h1 from the first sweep's partials; w <- w1 = w - V h1 on this block's rows;
 // the second sweep into partB.
+template <class T>
 __device__ __forceinline__ void arn_half1(int j, int64_t K0, int64_t k0, int64_t k1, int nb, int stride,
-                                          const double* V, double* w, const double* partA, double* partB_blk,
-                                          double* h1, double (*sh)[ARN_MAXCOL]) {
-    reduce_cols(partA, nb, stride, j + 2, h1, sh);
+                                          const T* V, T* w, const T* partA, T* partB_blk,
+                                          T* h1, T (*sh)[ARN_MAXCOL]) {
+    reduce_cols<T>(partA, nb, stride, j + 2, h1, sh);
     for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
-        double s = w[k];
-        for (int i = 0; i <= j; ++i) s = __fma_rn(-h1[i], V[(size_t)i * K0 + k], s);
+        T s = w[k];
+        for (int i = 0; i <= j; ++i) s = fma_t(-h1[i], V[(size_t)i * K0 + k], s);
         w[k] = s;
     }
     __syncthreads();
-    slice_dots(V, w, K0, k0, k1, j + 1, 1, partB_blk, sh);
+    slice_dots<T>(V, w, K0, k0, k1, j + 1, 1, partB_blk, sh);
 }
 
 // Second half: h2 and w1.w1; h_{j+1,j}; Hessenberg column j (into this block's copy Hs, and by
@@ -273,18 +292,19 @@ __device__ __forceinline__ void arn_half1(int j, int64_t K0, int64_t k0, int64_t
 // process continues (the same in every block).  Hs is the block's shared copy of H (row
 // stride ARN_HLD), complete up to column j - 1 on entry.
 constexpr int ARN_HLD = 41;   // row stride of the shared Hessenberg copy (m <= 40)
+template <class T>
 __device__ __forceinline__ bool arn_half2(int j, int m, int64_t K0, int64_t k0, int64_t k1, int nb, int stride,
                                           int NF, const double* __restrict__ bsr, const int* __restrict__ nbr,
-                                          const double* __restrict__ dt, double* V, const double* w1, double* wn,
-                                          double* H, double* Hs, const double* partB, double* partA_blk,
-                                          const double* h1, double* h2, double* cs, DevScalars* sc,
-                                          double (*sh)[ARN_MAXCOL]) {
-    reduce_cols(partB, nb, stride, j + 2, h2, sh);
-    double hh = 0.0;
-    for (int i = 0; i <= j; ++i) hh = __fma_rn(h2[i], h2[i], hh);
-    const double hn = sqrt(fmax(h2[j + 1] - hh, 0.0));
-    const double w0 = sqrt(h1[j + 1]);
-    const bool brk = !(hn > 1e-12 * w0);
+                                          const double* __restrict__ dt, T* V, const T* w1, T* wn,
+                                          double* H, T* Hs, const T* partB, T* partA_blk,
+                                          const T* h1, T* h2, T* cs, DevScalars* sc,
+                                          T (*sh)[ARN_MAXCOL]) {
+    reduce_cols<T>(partB, nb, stride, j + 2, h2, sh);
+    T hh = 0.0;
+    for (int i = 0; i <= j; ++i) hh = fma_t(h2[i], h2[i], hh);
+    const T hn = sqrt(fmax(h2[j + 1] - hh, (T)0));
+    const T w0 = sqrt(h1[j + 1]);
+    const bool brk = !(hn > arn_breakdown_tol<T>() * w0);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h1[i] + h2[i];
         H[(size_t)(j + 1) * m + j] = hn;
@@ -297,30 +317,30 @@ __device__ __forceinline__ bool arn_half2(int j, int m, int64_t K0, int64_t k0, 
     if (brk || j + 1 == m) return false;   // uniform: every block reduced the same values
     for (int i = threadIdx.x; i <= j + 1; i += ARN_THREADS) Hs[i * ARN_HLD + j] = i <= j ? h1[i] + h2[i] : hn;
     __syncthreads();
-    const double ih = 1.0 / hn;
+    const T ih = (T)1 / hn;
     // c = H~_j h2 over l = 0..j+1
     for (int l = threadIdx.x; l <= j + 1; l += ARN_THREADS) {
-        double c = 0.0;
-        for (int i = (l > 0 ? l - 1 : 0); i <= j; ++i) c = __fma_rn(Hs[l * ARN_HLD + i], h2[i], c);
+        T c = 0.0;
+        for (int i = (l > 0 ? l - 1 : 0); i <= j; ++i) c = fma_t(Hs[l * ARN_HLD + i], h2[i], c);
         cs[l] = c;
     }
     __syncthreads();
-    double* vn = V + (size_t)(j + 1) * K0;
+    T* vn = V + (size_t)(j + 1) * K0;
     for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
-        double s = w1[k];
-        double t = a_row(k, NF, bsr, nbr, dt, w1);
+        T s = w1[k];
+        T t = a_row<T>(k, NF, bsr, nbr, dt, w1);
         for (int i = 0; i <= j; ++i) {
-            const double vi = V[(size_t)i * K0 + k];
-            s = __fma_rn(-h2[i], vi, s);
-            t = __fma_rn(-cs[i], vi, t);
+            const T vi = V[(size_t)i * K0 + k];
+            s = fma_t(-h2[i], vi, s);
+            t = fma_t(-cs[i], vi, t);
         }
-        const double v = s * ih;
+        const T v = s * ih;
         vn[k] = v;
-        t = __fma_rn(-cs[j + 1], v, t);
+        t = fma_t(-cs[j + 1], v, t);
         wn[k] = t * ih;
     }
     __syncthreads();
-    slice_dots(V, wn, K0, k0, k1, j + 2, 1, partA_blk, sh);
+    slice_dots<T>(V, wn, K0, k0, k1, j + 2, 1, partA_blk, sh);
     return true;
 }
 
@@ -332,15 +352,15 @@ __device__ __forceinline__ bool arn_half2(int j, int m, int64_t K0, int64_t k0, 
 // slice_dots in the same order, so the results are bitwise the memory form's (and the
 // barrier-free kernels', which share that form).  Loops over i <= j run over the register
 // array with a uniform early exit, so every index is a compile-time one.
-template <int MV>
-__device__ __forceinline__ void slice_dots_rv(const double (&vrow)[MV], double wk, bool has, int nv, double* dst,
-                                              double (*sh)[ARN_MAXCOL]) {
+template <class T, int MV>
+__device__ __forceinline__ void slice_dots_rv(const T (&vrow)[MV], T wk, bool has, int nv, T* dst,
+                                              T (*sh)[ARN_MAXCOL]) {
     const int ncol = nv + 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int c0 = 0; c0 < MV + 1; c0 += ARN_CHUNK) {
         if (c0 >= ncol) break;   // uniform
-        double v[ARN_CHUNK];
+        T v[ARN_CHUNK];
 #pragma unroll
         for (int i = 0; i < ARN_CHUNK; ++i) v[i] = 0.0;
         if (has) {
@@ -348,56 +368,56 @@ __device__ __forceinline__ void slice_dots_rv(const double (&vrow)[MV], double w
             for (int i = 0; i < ARN_CHUNK; ++i) {
                 const int col = c0 + i;
                 if (col < MV && col < nv)
-                    v[i] = __fma_rn(vrow[col < MV ? col : 0], wk, v[i]);
+                    v[i] = fma_t(vrow[col < MV ? col : 0], wk, v[i]);
                 else if (col == nv)
-                    v[i] = __fma_rn(wk, wk, v[i]);
+                    v[i] = fma_t(wk, wk, v[i]);
             }
         }
         int c = 0;
-        const double x = warp_sum8(v, lane, &c);
+        const T x = warp_sum8<T>(v, lane, &c);
         if ((lane & 3) == 0 && c0 + c < ncol) sh[warp][c0 + c] = x;
     }
     __syncthreads();
     for (int c = threadIdx.x; c < ncol; c += ARN_THREADS) {
-        double s = 0.0;
+        T s = 0.0;
         for (int wv = 0; wv < ARN_WARPS; ++wv) s += sh[wv][c];
         dst[c] = s;
     }
 }
 
-template <int MV>
-__device__ __forceinline__ void arn_half1_rv(int j, int nb, int stride, const double (&vrow)[MV], bool has, int64_t k,
-                                             double* w, double& wk, const double* partA, double* partB_blk,
-                                             double* h1, double (*sh)[ARN_MAXCOL]) {
-    reduce_cols(partA, nb, stride, j + 2, h1, sh);
-    double s = 0.0;
+template <class T, int MV>
+__device__ __forceinline__ void arn_half1_rv(int j, int nb, int stride, const T (&vrow)[MV], bool has, int64_t k,
+                                             T* w, T& wk, const T* partA, T* partB_blk,
+                                             T* h1, T (*sh)[ARN_MAXCOL]) {
+    reduce_cols<T>(partA, nb, stride, j + 2, h1, sh);
+    T s = 0.0;
     if (has) {
         s = w[k];
 #pragma unroll
         for (int i = 0; i < MV; ++i) {
             if (i > j) break;   // uniform
-            s = __fma_rn(-h1[i], vrow[i], s);
+            s = fma_t(-h1[i], vrow[i], s);
         }
         w[k] = s;
     }
     wk = s;
     __syncthreads();
-    slice_dots_rv<MV>(vrow, s, has, j + 1, partB_blk, sh);
+    slice_dots_rv<T, MV>(vrow, s, has, j + 1, partB_blk, sh);
 }
 
-template <int MV>
+template <class T, int MV>
 __device__ __forceinline__ bool arn_half2_rv(int j, int m, int64_t K0, int64_t k, bool has, int nb, int stride,
                                              int NF, const double* __restrict__ bsr, const int* __restrict__ nbr,
-                                             const double* __restrict__ dt, double* V, double (&vrow)[MV], double w1k,
-                                             const double* w1, double* wn, double* H, double* Hs, const double* partB,
-                                             double* partA_blk, const double* h1, double* h2, double* cs,
-                                             DevScalars* sc, double (*sh)[ARN_MAXCOL]) {
-    reduce_cols(partB, nb, stride, j + 2, h2, sh);
-    double hh = 0.0;
-    for (int i = 0; i <= j; ++i) hh = __fma_rn(h2[i], h2[i], hh);
-    const double hn = sqrt(fmax(h2[j + 1] - hh, 0.0));
-    const double w0 = sqrt(h1[j + 1]);
-    const bool brk = !(hn > 1e-12 * w0);
+                                             const double* __restrict__ dt, T* V, T (&vrow)[MV], T w1k,
+                                             const T* w1, T* wn, double* H, T* Hs, const T* partB,
+                                             T* partA_blk, const T* h1, T* h2, T* cs,
+                                             DevScalars* sc, T (*sh)[ARN_MAXCOL]) {
+    reduce_cols<T>(partB, nb, stride, j + 2, h2, sh);
+    T hh = 0.0;
+    for (int i = 0; i <= j; ++i) hh = fma_t(h2[i], h2[i], hh);
+    const T hn = sqrt(fmax(h2[j + 1] - hh, (T)0));
+    const T w0 = sqrt(h1[j + 1]);
+    const bool brk = !(hn > arn_breakdown_tol<T>() * w0);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h1[i] + h2[i];
         H[(size_t)(j + 1) * m + j] = hn;
@@ -410,51 +430,51 @@ __device__ __forceinline__ bool arn_half2_rv(int j, int m, int64_t K0, int64_t k
     if (brk || j + 1 == m) return false;   // uniform: every block reduced the same values
     for (int i = threadIdx.x; i <= j + 1; i += ARN_THREADS) Hs[i * ARN_HLD + j] = i <= j ? h1[i] + h2[i] : hn;
     __syncthreads();
-    const double ih = 1.0 / hn;
+    const T ih = (T)1 / hn;
     for (int l = threadIdx.x; l <= j + 1; l += ARN_THREADS) {
-        double c = 0.0;
-        for (int i = (l > 0 ? l - 1 : 0); i <= j; ++i) c = __fma_rn(Hs[l * ARN_HLD + i], h2[i], c);
+        T c = 0.0;
+        for (int i = (l > 0 ? l - 1 : 0); i <= j; ++i) c = fma_t(Hs[l * ARN_HLD + i], h2[i], c);
         cs[l] = c;
     }
     __syncthreads();
-    double wnk = 0.0;
+    T wnk = 0.0;
     if (has) {
-        double s = w1k;
-        double t = a_row(k, NF, bsr, nbr, dt, w1);
+        T s = w1k;
+        T t = a_row<T>(k, NF, bsr, nbr, dt, w1);
 #pragma unroll
         for (int i = 0; i < MV; ++i) {
             if (i > j) break;   // uniform
-            const double vi = vrow[i];
-            s = __fma_rn(-h2[i], vi, s);
-            t = __fma_rn(-cs[i], vi, t);
+            const T vi = vrow[i];
+            s = fma_t(-h2[i], vi, s);
+            t = fma_t(-cs[i], vi, t);
         }
-        const double v = s * ih;
+        const T v = s * ih;
         V[(size_t)(j + 1) * K0 + k] = v;
 #pragma unroll
         for (int i = 0; i < MV; ++i)
             if (i == j + 1) vrow[i] = v;
-        t = __fma_rn(-cs[j + 1], v, t);
+        t = fma_t(-cs[j + 1], v, t);
         wnk = t * ih;
         wn[k] = wnk;
     }
     __syncthreads();
-    slice_dots_rv<MV>(vrow, wnk, has, j + 2, partA_blk, sh);
+    slice_dots_rv<T, MV>(vrow, wnk, has, j + 2, partA_blk, sh);
     return true;
 }
 
-template <int MV>
+template <class T, int MV>
 __global__ void __launch_bounds__(ARN_THREADS, 2) k_arnoldi_rv(int64_t K0, int E, int NF, int m,
                                                                const double* __restrict__ bsr,
                                                                const int* __restrict__ nbr,
                                                                const double* __restrict__ dt,
-                                                               const double* __restrict__ r, double* __restrict__ V,
-                                                               double* __restrict__ wbuf, double* __restrict__ H,
-                                                               double* __restrict__ partA, double* __restrict__ partB,
-                                                               double* __restrict__ partC, int stride, GridBar* bar,
+                                                               const double* __restrict__ r, T* __restrict__ V,
+                                                               T* __restrict__ wbuf, double* __restrict__ H,
+                                                               T* __restrict__ partA, T* __restrict__ partB,
+                                                               T* __restrict__ partC, int stride, GridBar* bar,
                                                                long long budget, DevScalars* sc) {
-    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
-    __shared__ double h1[ARN_MAXCOL], h2[ARN_MAXCOL], cs[ARN_MAXCOL], red[8];
-    __shared__ double Hs[(ARN_HLD + 1) * ARN_HLD];
+    __shared__ T sh[ARN_WARPS][ARN_MAXCOL];
+    __shared__ T h1[ARN_MAXCOL], h2[ARN_MAXCOL], cs[ARN_MAXCOL], red[8];
+    __shared__ T Hs[(ARN_HLD + 1) * ARN_HLD];
     __shared__ int s_ok;
     unsigned epoch = 0;
     const unsigned nb = gridDim.x;
@@ -463,20 +483,20 @@ __global__ void __launch_bounds__(ARN_THREADS, 2) k_arnoldi_rv(int64_t K0, int E
     const int64_t k1 = (k0 + chunk) < K0 ? (k0 + chunk) : K0;
     const int64_t k = k0 + threadIdx.x;
     const bool has = k < k1;
-    double vrow[MV];
+    T vrow[MV];
 #pragma unroll
     for (int i = 0; i < MV; ++i) vrow[i] = 0.0;
     {
-        double v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
+        T v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (has) {
-            const double x = dt[k / 5] * r[k];
-            v[0] = __fma_rn(x, x, v[0]);
+            const T x = dt[k / 5] * r[k];
+            v[0] = fma_t(x, x, v[0]);
         }
-        block_reduce_store(v, 1, partC + (size_t)blockIdx.x * stride, sh);
+        block_reduce_store<T>(v, 1, partC + (size_t)blockIdx.x * stride, sh);
     }
     if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
-    reduce_cols(partC, nb, stride, 1, red, sh);
-    const double beta = sqrt(red[0]);
+    reduce_cols<T>(partC, nb, stride, 1, red, sh);
+    const T beta = sqrt(red[0]);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         sc->beta = beta;
         sc->m_used = 0;
@@ -484,21 +504,21 @@ __global__ void __launch_bounds__(ARN_THREADS, 2) k_arnoldi_rv(int64_t K0, int E
         if (!isfinite(beta)) sc->nonfinite = 1;
     }
     if (beta == 0.0 || !isfinite(beta)) return;   // uniform across blocks
-    const double ib = 1.0 / beta;
+    const T ib = (T)1 / beta;
     if (has) {
         vrow[0] = dt[k / 5] * r[k] * ib;
         V[k] = vrow[0];
     }
-    spmv_rows(k0, k1, NF, bsr, nbr, dt, nullptr, r, ib, wbuf);   // A v_1 from the inputs: no barrier
+    spmv_rows<T>(k0, k1, NF, bsr, nbr, dt, nullptr, r, ib, wbuf);   // A v_1 from the inputs: no barrier
     __syncthreads();
-    slice_dots_rv<MV>(vrow, has ? wbuf[k] : 0.0, has, 1, partA + (size_t)blockIdx.x * stride, sh);
+    slice_dots_rv<T, MV>(vrow, has ? wbuf[k] : 0.0, has, 1, partA + (size_t)blockIdx.x * stride, sh);
     for (int j = 0; j < m; ++j) {
-        double* w = wbuf + (size_t)(j & 1) * K0;
+        T* w = wbuf + (size_t)(j & 1) * K0;
         if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
-        double w1k = 0.0;
-        arn_half1_rv<MV>(j, (int)nb, stride, vrow, has, k, w, w1k, partA, partB + (size_t)blockIdx.x * stride, h1, sh);
+        T w1k = 0.0;
+        arn_half1_rv<T, MV>(j, (int)nb, stride, vrow, has, k, w, w1k, partA, partB + (size_t)blockIdx.x * stride, h1, sh);
         if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
-        if (!arn_half2_rv<MV>(j, m, K0, k, has, (int)nb, stride, NF, bsr, nbr, dt, V, vrow, w1k, w,
+        if (!arn_half2_rv<T, MV>(j, m, K0, k, has, (int)nb, stride, NF, bsr, nbr, dt, V, vrow, w1k, w,
                               wbuf + (size_t)((j + 1) & 1) * K0, H, Hs, partB, partA + (size_t)blockIdx.x * stride, h1,
                               h2, cs, sc, sh))
             break;
@@ -507,16 +527,17 @@ __global__ void __launch_bounds__(ARN_THREADS, 2) k_arnoldi_rv(int64_t K0, int E
 constexpr int ARN_RV = 32;   // Krylov rows held in registers by k_arnoldi_rv (m <= 32)
 
 // Two grid barriers per Krylov step (one per reduction).
+template <class T>
 __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int NF, int m,
                                                          const double* __restrict__ bsr, const int* __restrict__ nbr,
                                                          const double* __restrict__ dt, const double* __restrict__ r,
-                                                         double* __restrict__ V, double* __restrict__ wbuf,
-                                                         double* __restrict__ H, double* __restrict__ partA,
-                                                         double* __restrict__ partB, double* __restrict__ partC,
+                                                         T* __restrict__ V, T* __restrict__ wbuf,
+                                                         double* __restrict__ H, T* __restrict__ partA,
+                                                         T* __restrict__ partB, T* __restrict__ partC,
                                                          int stride, GridBar* bar, long long budget, DevScalars* sc) {
-    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
-    __shared__ double h1[ARN_MAXCOL], h2[ARN_MAXCOL], cs[ARN_MAXCOL], red[8];
-    __shared__ double Hs[(ARN_HLD + 1) * ARN_HLD];
+    __shared__ T sh[ARN_WARPS][ARN_MAXCOL];
+    __shared__ T h1[ARN_MAXCOL], h2[ARN_MAXCOL], cs[ARN_MAXCOL], red[8];
+    __shared__ T Hs[(ARN_HLD + 1) * ARN_HLD];
     __shared__ int s_ok;
     unsigned epoch = 0;   // barriers passed (thread 0's copy is the one used)
     const unsigned nb = gridDim.x;
@@ -525,16 +546,16 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
     const int64_t k1 = (k0 + chunk) < K0 ? (k0 + chunk) : K0;
     // start vector v_1 = N / ||N||, N = dt * r
     {
-        double v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
+        T v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
-            const double x = dt[k / 5] * r[k];
-            v[0] = __fma_rn(x, x, v[0]);
+            const T x = dt[k / 5] * r[k];
+            v[0] = fma_t(x, x, v[0]);
         }
-        block_reduce_store(v, 1, partC + (size_t)blockIdx.x * stride, sh);
+        block_reduce_store<T>(v, 1, partC + (size_t)blockIdx.x * stride, sh);
     }
     if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
-    reduce_cols(partC, nb, stride, 1, red, sh);
-    const double beta = sqrt(red[0]);
+    reduce_cols<T>(partC, nb, stride, 1, red, sh);
+    const T beta = sqrt(red[0]);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         sc->beta = beta;
         sc->m_used = 0;
@@ -542,17 +563,17 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
         if (!isfinite(beta)) sc->nonfinite = 1;
     }
     if (beta == 0.0 || !isfinite(beta)) return;   // uniform across blocks
-    const double ib = 1.0 / beta;
+    const T ib = (T)1 / beta;
     for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) V[k] = dt[k / 5] * r[k] * ib;
-    spmv_rows(k0, k1, NF, bsr, nbr, dt, nullptr, r, ib, wbuf);   // A v_1 from the inputs: no barrier
+    spmv_rows<T>(k0, k1, NF, bsr, nbr, dt, nullptr, r, ib, wbuf);   // A v_1 from the inputs: no barrier
     __syncthreads();
-    slice_dots(V, wbuf, K0, k0, k1, 1, 1, partA + (size_t)blockIdx.x * stride, sh);
+    slice_dots<T>(V, wbuf, K0, k0, k1, 1, 1, partA + (size_t)blockIdx.x * stride, sh);
     for (int j = 0; j < m; ++j) {
-        double* w = wbuf + (size_t)(j & 1) * K0;
+        T* w = wbuf + (size_t)(j & 1) * K0;
         if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
-        arn_half1(j, K0, k0, k1, (int)nb, stride, V, w, partA, partB + (size_t)blockIdx.x * stride, h1, sh);
+        arn_half1<T>(j, K0, k0, k1, (int)nb, stride, V, w, partA, partB + (size_t)blockIdx.x * stride, h1, sh);
         if (!grid_sync(bar, nb, &epoch, budget, sc, &s_ok)) return;
-        if (!arn_half2(j, m, K0, k0, k1, (int)nb, stride, NF, bsr, nbr, dt, V, w, wbuf + (size_t)((j + 1) & 1) * K0, H,
+        if (!arn_half2<T>(j, m, K0, k0, k1, (int)nb, stride, NF, bsr, nbr, dt, V, w, wbuf + (size_t)((j + 1) & 1) * K0, H,
                        Hs, partB, partA + (size_t)blockIdx.x * stride, h1, h2, cs, sc, sh))
             break;
     }
@@ -566,6 +587,7 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arnoldi(int64_t K0, int E, int 
 // another, so nothing depends on the blocks being co-resident (several contexts sharing the
 // device).  h1 travels between kernels through hcol[]; a kernel that finds the process
 // ended (breakdown or a zero start vector) returns at once.
+template <class T>
 struct ArnArgs {
     int64_t K0;
     int NF, m, stride;
@@ -573,13 +595,13 @@ struct ArnArgs {
     const int* nbr;
     const double* dt;
     const double* r;
-    double* V;
-    double* wbuf;
+    T* V;
+    T* wbuf;
     double* H;
     double* hcol;
-    double* partA;
-    double* partB;
-    double* partC;
+    T* partA;
+    T* partB;
+    T* partC;
     DevScalars* sc;
 };
 
@@ -590,26 +612,28 @@ __device__ __forceinline__ void arn_slice(int64_t K0, int64_t* k0, int64_t* k1) 
     *k1 = (*k0 + chunk) < K0 ? (*k0 + chunk) : K0;
 }
 
-__global__ void __launch_bounds__(ARN_THREADS) k_arn_start(ArnArgs A) {
-    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
+template <class T>
+__global__ void __launch_bounds__(ARN_THREADS) k_arn_start(ArnArgs<T> A) {
+    __shared__ T sh[ARN_WARPS][ARN_MAXCOL];
     int64_t k0, k1;
     arn_slice(A.K0, &k0, &k1);
-    double v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
+    T v[ARN_CHUNK] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) {
-        const double x = A.dt[k / 5] * A.r[k];
-        v[0] = __fma_rn(x, x, v[0]);
+        const T x = A.dt[k / 5] * A.r[k];
+        v[0] = fma_t(x, x, v[0]);
     }
-    block_reduce_store(v, 1, A.partC + (size_t)blockIdx.x * A.stride, sh);
+    block_reduce_store<T>(v, 1, A.partC + (size_t)blockIdx.x * A.stride, sh);
 }
 
-__global__ void __launch_bounds__(ARN_THREADS) k_arn_init(ArnArgs A) {
-    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
-    __shared__ double red[8];
+template <class T>
+__global__ void __launch_bounds__(ARN_THREADS) k_arn_init(ArnArgs<T> A) {
+    __shared__ T sh[ARN_WARPS][ARN_MAXCOL];
+    __shared__ T red[8];
     int64_t k0, k1;
     arn_slice(A.K0, &k0, &k1);
     const int nb = (int)gridDim.x;
-    reduce_cols(A.partC, nb, A.stride, 1, red, sh);
-    const double beta = sqrt(red[0]);
+    reduce_cols<T>(A.partC, nb, A.stride, 1, red, sh);
+    const T beta = sqrt(red[0]);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         A.sc->beta = beta;
         A.sc->m_used = 0;
@@ -617,32 +641,34 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arn_init(ArnArgs A) {
         if (!isfinite(beta)) A.sc->nonfinite = 1;
     }
     if (beta == 0.0 || !isfinite(beta)) return;
-    const double ib = 1.0 / beta;
+    const T ib = (T)1 / beta;
     for (int64_t k = k0 + threadIdx.x; k < k1; k += ARN_THREADS) A.V[k] = A.dt[k / 5] * A.r[k] * ib;
-    spmv_rows(k0, k1, A.NF, A.bsr, A.nbr, A.dt, nullptr, A.r, ib, A.wbuf);
+    spmv_rows<T>(k0, k1, A.NF, A.bsr, A.nbr, A.dt, nullptr, A.r, ib, A.wbuf);
     __syncthreads();
-    slice_dots(A.V, A.wbuf, A.K0, k0, k1, 1, 1, A.partA + (size_t)blockIdx.x * A.stride, sh);
+    slice_dots<T>(A.V, A.wbuf, A.K0, k0, k1, 1, 1, A.partA + (size_t)blockIdx.x * A.stride, sh);
 }
 
 // step j, first half (h1 reaches the second half through hcol[])
-__global__ void __launch_bounds__(ARN_THREADS) k_arn_half1(ArnArgs A, int j) {
-    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
-    __shared__ double h1[ARN_MAXCOL];
+template <class T>
+__global__ void __launch_bounds__(ARN_THREADS) k_arn_half1(ArnArgs<T> A, int j) {
+    __shared__ T sh[ARN_WARPS][ARN_MAXCOL];
+    __shared__ T h1[ARN_MAXCOL];
     if (*((volatile int*)&A.sc->broken)) return;
     int64_t k0, k1;
     arn_slice(A.K0, &k0, &k1);
-    double* w = A.wbuf + (size_t)(j & 1) * A.K0;
-    arn_half1(j, A.K0, k0, k1, (int)gridDim.x, A.stride, A.V, w, A.partA, A.partB + (size_t)blockIdx.x * A.stride,
+    T* w = A.wbuf + (size_t)(j & 1) * A.K0;
+    arn_half1<T>(j, A.K0, k0, k1, (int)gridDim.x, A.stride, A.V, w, A.partA, A.partB + (size_t)blockIdx.x * A.stride,
               h1, sh);
     if (blockIdx.x == 0)
         for (int i = threadIdx.x; i < j + 2; i += ARN_THREADS) A.hcol[i] = h1[i];
 }
 
 // step j, second half
-__global__ void __launch_bounds__(ARN_THREADS) k_arn_half2(ArnArgs A, int j) {
-    __shared__ double sh[ARN_WARPS][ARN_MAXCOL];
-    __shared__ double h1[ARN_MAXCOL], h2[ARN_MAXCOL], cs[ARN_MAXCOL];
-    __shared__ double Hs[(ARN_HLD + 1) * ARN_HLD];
+template <class T>
+__global__ void __launch_bounds__(ARN_THREADS) k_arn_half2(ArnArgs<T> A, int j) {
+    __shared__ T sh[ARN_WARPS][ARN_MAXCOL];
+    __shared__ T h1[ARN_MAXCOL], h2[ARN_MAXCOL], cs[ARN_MAXCOL];
+    __shared__ T Hs[(ARN_HLD + 1) * ARN_HLD];
     if (*((volatile int*)&A.sc->broken)) return;
     int64_t k0, k1;
     arn_slice(A.K0, &k0, &k1);
@@ -653,9 +679,9 @@ __global__ void __launch_bounds__(ARN_THREADS) k_arn_half2(ArnArgs A, int j) {
         Hs[r * ARN_HLD + cc] = __ldcg(A.H + (size_t)r * A.m + cc);
     }
     __syncthreads();
-    const double* w1 = A.wbuf + (size_t)(j & 1) * A.K0;
-    double* wn = A.wbuf + (size_t)((j + 1) & 1) * A.K0;
-    arn_half2(j, A.m, A.K0, k0, k1, (int)gridDim.x, A.stride, A.NF, A.bsr, A.nbr, A.dt, A.V, w1, wn, A.H, Hs,
+    const T* w1 = A.wbuf + (size_t)(j & 1) * A.K0;
+    T* wn = A.wbuf + (size_t)((j + 1) & 1) * A.K0;
+    arn_half2<T>(j, A.m, A.K0, k0, k1, (int)gridDim.x, A.stride, A.NF, A.bsr, A.nbr, A.dt, A.V, w1, wn, A.H, Hs,
               A.partB, A.partA + (size_t)blockIdx.x * A.stride, h1, h2, cs, A.sc, sh);
 }
 
@@ -876,7 +902,8 @@ __global__ void __cluster_dims__(PHI_CLUSTER, 1, 1)
 }
 
 // out = u0 + V[0:k]^T y  (out = u0 when the start vector was zero)
-__global__ void k_combine(int64_t K0, const double* __restrict__ u0, const double* __restrict__ V,
+template <class TV>
+__global__ void k_combine(int64_t K0, const double* __restrict__ u0, const TV* __restrict__ V,
                           const double* __restrict__ y, const DevScalars* __restrict__ sc, double* __restrict__ out) {
     const int k = sc->m_used;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < K0; t += (int64_t)gridDim.x * blockDim.x) {
@@ -942,22 +969,24 @@ emg_status launch_exp1(emg_ctx* c, const double* u0, const double* tau0, const d
 // Arnoldi (one persistent cooperative kernel), phi_1 of the Hessenberg matrix, combination.
 // While a graph is being captured the ordering of cooperative launches is left to the
 // caller (the graph replay is ordered as a whole).
-emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, double* out) {
+template <class T>
+static emg_status exp1_krylov(emg_ctx* c, const double* u0, const double* dt, double* out) {
     LevelDev& L = c->lv[0];
     const int64_t K0 = 5 * c->E;
     const int m = c->prm.krylov_m;
     // one cooperative launch: every block must be co-resident for the grid barriers
     int per_sm = 0, nsm = 0, per_sm_rv = 0;
-    EMG_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi, ARN_THREADS, 0));
-    EMG_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_rv, k_arnoldi_rv<ARN_RV>, ARN_THREADS, 0));
+    EMG_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi<T>, ARN_THREADS, 0));
+    EMG_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_rv, k_arnoldi_rv<T, ARN_RV>, ARN_THREADS, 0));
     EMG_CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
     const int64_t nb = arnoldi_blocks(K0, nsm, per_sm, c->red_blocks);
     // rows in registers: one row per thread at most, every block co-resident, m <= ARN_RV
     const bool rows_in_regs = m <= ARN_RV && (K0 + nb - 1) / nb <= ARN_THREADS && nb <= (int64_t)nsm * per_sm_rv;
     const int stride = MAX_KRYLOV + 8;
-    double* partA = c->partial;
-    double* partB = partA + (size_t)c->red_blocks * stride;
-    double* partC = partB + (size_t)c->red_blocks * stride;
+    // the basis, products and partials in T (float: the same arrays, half of each used)
+    T* partA = reinterpret_cast<T*>(c->partial);
+    T* partB = partA + (size_t)c->red_blocks * stride;
+    T* partC = partB + (size_t)c->red_blocks * stride;
     GridBar* bar = reinterpret_cast<GridBar*>(c->bar);
     EMG_CUDA_TRY(c, cudaMemsetAsync(bar, 0, sizeof(GridBar), c->stream));
     int64_t K0a = K0;
@@ -965,23 +994,23 @@ emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, do
     const double* bsr = c->bsr;
     const int* nbr = c->elem_nbr;
     const double* rr = L.r;
-    double* Vv = c->V;
-    double* ww = c->w;
+    T* Vv = reinterpret_cast<T*>(c->V);
+    T* ww = reinterpret_cast<T*>(c->w);
     double* HH = c->H;
     const double tol = c->prm.krylov_tol;
     if (!c->prm.coop_krylov || tol > 0.0) {
         // barrier-free form (same blocks, same arithmetic): 2 + 2m plain launches; with a
         // Krylov tolerance, the test of each step follows it (it may end the process)
-        ArnArgs A{K0, 2 * c->dim, m, stride, bsr, nbr, dt, rr, Vv, ww, HH, c->hcol, partA, partB, partC, c->sc};
+        ArnArgs<T> A{K0, 2 * c->dim, m, stride, bsr, nbr, dt, rr, Vv, ww, HH, c->hcol, partA, partB, partC, c->sc};
         const unsigned g = (unsigned)nb;
         const size_t smem_est = (size_t)8 * (m + 2) * (m + 2) * sizeof(double);
         if (tol > 0.0)
             EMG_CUDA_TRY(c, cudaFuncSetAttribute(k_phi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_est));
-        { ProfScope _ps(c, PC_ARNOLDI); k_arn_start<<<g, ARN_THREADS, 0, c->stream>>>(A); }
-        { ProfScope _ps(c, PC_ARNOLDI); k_arn_init<<<g, ARN_THREADS, 0, c->stream>>>(A); }
+        { ProfScope _ps(c, PC_ARNOLDI); k_arn_start<T><<<g, ARN_THREADS, 0, c->stream>>>(A); }
+        { ProfScope _ps(c, PC_ARNOLDI); k_arn_init<T><<<g, ARN_THREADS, 0, c->stream>>>(A); }
         for (int j = 0; j < m; ++j) {
-            { ProfScope _ps(c, PC_ARNOLDI); k_arn_half1<<<g, ARN_THREADS, 0, c->stream>>>(A, j); }
-            { ProfScope _ps(c, PC_ARNOLDI); k_arn_half2<<<g, ARN_THREADS, 0, c->stream>>>(A, j); }
+            { ProfScope _ps(c, PC_ARNOLDI); k_arn_half1<T><<<g, ARN_THREADS, 0, c->stream>>>(A, j); }
+            { ProfScope _ps(c, PC_ARNOLDI); k_arn_half2<T><<<g, ARN_THREADS, 0, c->stream>>>(A, j); }
             if (tol > 0.0 && j + 1 < m) {
                 ProfScope _ps(c, PC_PHI);
                 k_phi<true><<<PHI_CLUSTER, 256, smem_est, c->stream>>>(m, j, tol, c->H, c->y, pade13(), c->sc);
@@ -996,7 +1025,7 @@ emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, do
         {
             ProfScope _ps(c, PC_ARNOLDI);
             auto launch = [&]() {
-                const void* fn = rows_in_regs ? (const void*)k_arnoldi_rv<ARN_RV> : (const void*)k_arnoldi;
+                const void* fn = rows_in_regs ? (const void*)k_arnoldi_rv<T, ARN_RV> : (const void*)k_arnoldi<T>;
                 return cudaLaunchCooperativeKernel(fn, dim3((unsigned)nb), dim3(ARN_THREADS), args, 0, c->stream);
             };
             if (c->capturing) {
@@ -1017,11 +1046,17 @@ emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, do
     EMG_CHECK_LAUNCH(c);
     {
         ProfScope _ps(c, PC_COMBINE);
-        k_combine<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(296, (K0 + 255) / 256)), 256, 0, c->stream>>>(
-            K0, u0, c->V, c->y, c->sc, out);
+        k_combine<T><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(296, (K0 + 255) / 256)), 256, 0, c->stream>>>(
+            K0, u0, Vv, c->y, c->sc, out);
     }
     EMG_CHECK_LAUNCH(c);
     return EMG_OK;
+}
+
+// The Krylov process in FP64, or in float32 arithmetic for the basis, products and reductions
+// (emg_params.krylov_f32; the Hessenberg matrix, phi_1 and the combination stay FP64).
+emg_status launch_exp1_krylov(emg_ctx* c, const double* u0, const double* dt, double* out) {
+    return c->prm.krylov_f32 ? exp1_krylov<float>(c, u0, dt, out) : exp1_krylov<double>(c, u0, dt, out);
 }
 
 // ---- EXP1 step without any allocation --------------------------------------------------------
@@ -1128,7 +1163,7 @@ extern "C" emg_status emg_exp1_step_noalloc(int32_t dim, int64_t n_elems, const 
         if (bad) return EMG_ERR_ARG;
     }
     int per_sm = 0, nsm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi, ARN_THREADS, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi<double>, ARN_THREADS, 0) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return EMG_ERR_CUDA;
     const int64_t nb = arnoldi_blocks(K0, nsm, per_sm, NA_BLOCKS);
@@ -1140,7 +1175,7 @@ extern "C" emg_status emg_exp1_step_noalloc(int32_t dim, int64_t n_elems, const 
     void* args[] = {&K0a, &Ea, &NFa, &ma, (void*)&bsrc, (void*)&nbrc, (void*)&dt, (void*)&r0, &V, &w, &H,
                     &partA, &partB, &partC, &stra, &bar, &budget, &sc};
     auto launch = [&]() {
-        return cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3((unsigned)nb), dim3(ARN_THREADS), args, 0, st);
+        return cudaLaunchCooperativeKernel((const void*)k_arnoldi<double>, dim3((unsigned)nb), dim3(ARN_THREADS), args, 0, st);
     };
     if (coop_ordered(dev, st, launch, nullptr) != EMG_OK) return EMG_ERR_CUDA;
     const int n = krylov_m + 1;
@@ -1148,7 +1183,7 @@ extern "C" emg_status emg_exp1_step_noalloc(int32_t dim, int64_t n_elems, const 
     if (cudaFuncSetAttribute(k_phi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return EMG_ERR_CUDA;
     k_phi<false><<<PHI_CLUSTER, 256, smem, st>>>(krylov_m, 0, 0.0, H, y, pade13(), sc);
-    k_combine<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(296, (K0 + 255) / 256)), 256, 0, st>>>(
+    k_combine<double><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(296, (K0 + 255) / 256)), 256, 0, st>>>(
         K0, u0, V, y, sc, u_out);
     if (cudaGetLastError() != cudaSuccess) return EMG_ERR_CUDA;
     DevScalars hs;

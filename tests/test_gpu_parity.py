@@ -18,6 +18,7 @@ from workloads import BC_FARFIELD, cubed_sphere_shell, ogrid
 pytestmark = pytest.mark.gpu
 
 TOL_KERNEL = 1e-12
+GOLDEN_PATH = os.path.join(os.path.dirname(__file__), "golden", "cyl32x16_p2_steady.npz")
 TOL_CYCLE = 1e-11
 
 
@@ -125,6 +126,39 @@ def test_exp1_step_fixed_dimension(lib):
     uo, ko = oemg.exp1_step(dg, u0, tau0, dt, oemg.Options())
     assert kg == ko == 30
     assert rel_err(ug - u0, uo - u0) < TOL_CYCLE, rel_err(ug - u0, uo - u0)
+
+
+def test_exp1_step_with_float32_krylov(lib):
+    """The Arnoldi process in float32 arithmetic (krylov_f32): the same EXP1 step as the FP64
+    oracle to float32 accuracy.  Every basis vector carries rounding of order u32 = 2^-24 per
+    operation, compounded over m = 30 Gram-Schmidt steps with reorthogonalisation; the step
+    (a combination of the basis with phi_1 coefficients) is asserted within 1e-4 relative, and
+    above FP64 error (it is float32 arithmetic)."""
+    desc = ogrid(16, 8)
+    s = lib.Solver(desc, p_max=1, krylov_f32=1)
+    dg = DG(desc, 1)
+    u0 = np.ascontiguousarray(perturbed_state(dg, amp=0.05)[:, :, :1])
+    rng = np.random.default_rng(3)
+    tau0 = 1e-4 * rng.standard_normal(u0.shape)
+    dt = oemg.dtau(dg, 1, perturbed_state(dg, amp=0.05), 100.0) * 2.0
+    ug, kg = s.exp1_step(u0, dt, tau0)
+    uo, ko = oemg.exp1_step(dg, u0, tau0, dt, oemg.Options())
+    assert kg == ko == 30
+    e = rel_err(ug - u0, uo - u0)
+    assert 1e-12 < e < 1e-4, e
+    s.close()
+
+
+@pytest.mark.skipif(not os.path.exists(GOLDEN_PATH), reason="golden file not generated")
+def test_float32_krylov_converged_state_matches_fp64_oracle(lib):
+    """float32 block factors and a float32 Krylov basis change only the smoother and the
+    coarse correction: the converged state is the FP64 fixed point R = 0."""
+    g = np.load(GOLDEN_PATH)
+    s = lib.Solver(ogrid(32, 16), p_max=2, prec=1, krylov_f32=1)
+    rep = s.solve_steady(drop=1e-10, max_cycles=int(g["cycles"]) + 400)
+    assert rep["converged"]
+    assert rel_err(s.get_state(), g["u"]) < 1e-9, rel_err(s.get_state(), g["u"])
+    s.close()
 
 
 def test_exp1_happy_breakdown_matches_dense(lib):
@@ -360,13 +394,15 @@ def test_tuned_kernel_variants_give_bitwise_the_same_cycles():
 def test_barrier_free_arnoldi_is_bitwise_the_persistent_kernel():
     """The Arnoldi process as plain kernels (no grid barrier) and as one cooperative
     persistent kernel: same blocks, same arithmetic, bitwise the same cycles; also when
-    the process stops early at happy breakdown (4x1 O-grid at p = 0, K0 = 20 < m)."""
+    the process stops early at happy breakdown (4x1 O-grid at p = 0, K0 = 20 < m), and with
+    the float32 Krylov basis."""
     from paper_1807_01151_gb300 import Solver
     from workloads import ogrid
-    for desc, p, prec in ((ogrid(16, 8), 3, 1), (ogrid(16, 8), 2, 0), (ogrid(4, 1), 0, 0)):
+    for desc, p, prec, kf in ((ogrid(16, 8), 3, 1, 0), (ogrid(16, 8), 2, 0, 0), (ogrid(4, 1), 0, 0, 0),
+                              (ogrid(16, 8), 3, 1, 1), (ogrid(4, 1), 0, 0, 1)):
         out = []
         for coop in (1, 0):
-            s = Solver(desc, p_max=p, prec=prec, coop_krylov=coop)
+            s = Solver(desc, p_max=p, prec=prec, coop_krylov=coop, krylov_f32=kf)
             infos = [s.vcycle() for _ in range(5)]
             out.append((s.get_state(), [(i["krylov_dim"], i["cfl"], i["res_rho"]) for i in infos]))
             s.close()
