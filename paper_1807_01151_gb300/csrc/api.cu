@@ -87,20 +87,59 @@ __global__ void k_set_ref(DevScalars* sc, double ref) { sc->res_ref = ref; }
 __global__ void k_set_cycle(DevScalars* sc, long long n) { sc->cycle = n; }
 __global__ void k_advance_cycle(DevScalars* sc) { sc->cycle += 1; }
 
+// Work that does not depend on a level's block build (residuals) runs on the side stream
+// while the main stream assembles and factors the blocks: fork_side enqueues `side` on the
+// side stream after everything already on the main stream, join_side makes the main stream
+// wait for it.  Inside a graph capture the two branches become parallel branches of the
+// graph.  With the event profiler on (it times one stream) the side work runs in order.
+static emg_status fork_side(emg_ctx* c, const std::function<emg_status(emg_ctx*)>& side) {
+    if (c->prof.on || !c->stream2) return side(c);
+    EMG_CUDA_TRY(c, cudaEventRecord(c->ev_fork, c->stream));
+    EMG_CUDA_TRY(c, cudaStreamWaitEvent(c->stream2, c->ev_fork, 0));
+    std::swap(c->stream, c->stream2);
+    const emg_status st = side(c);
+    std::swap(c->stream, c->stream2);
+    if (st != EMG_OK) return st;
+    EMG_CUDA_TRY(c, cudaEventRecord(c->ev_join, c->stream2));
+    c->side_pending = true;
+    return EMG_OK;
+}
+static emg_status join_side(emg_ctx* c) {
+    if (!c->side_pending) return EMG_OK;
+    c->side_pending = false;
+    EMG_CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    return EMG_OK;
+}
+
 // One PRK step (Eq. prk_scalar) on level p: u^n = L.v on entry, result in L.v.
-// r_first: R~_p(u^n) if already available (else computed here).  reuse_blocks: apply the
-// factors of the previous step of this level instead of P(u^n) (lagged preconditioner).
-static emg_status prk_step(emg_ctx* c, int p, const double* tau, const double* r_first, bool reuse_blocks = false) {
+// r_first: R~_p(u^n) if already available; side: work to run on the side stream during the
+// block build that leaves R~_p(u^n) in r_first (else R~_p(u^n) itself is computed there when
+// the blocks are built, and in order otherwise).  reuse_blocks: apply the factors of the
+// previous step of this level instead of P(u^n) (lagged preconditioner).
+static emg_status prk_step(emg_ctx* c, int p, const double* tau, const double* r_first, bool reuse_blocks = false,
+                           const std::function<emg_status(emg_ctx*)>& side = nullptr) {
     LevelDev& L = c->lv[p];
     const int64_t S = c->E * L.B;
     EMG_CUDA_TRY(c, cudaMemcpyAsync(L.un, L.v, S * 8, cudaMemcpyDeviceToDevice, c->stream));
     const bool f32 = blocks_f32(c->prm.prec);
     emg_status st = EMG_OK;
     if (!reuse_blocks) {
+        if (side) {
+            st = fork_side(c, side);
+        } else if (!r_first) {
+            st = fork_side(c, [p, tau](emg_ctx* cc) { return launch_residual(cc, p, cc->lv[p].v, tau, cc->lv[p].r); });
+            r_first = L.r;
+        }
+        if (st != EMG_OK) return st;
         st = f32 ? launch_diag_blocks32(c, p, L.un, &c->sc->cfl, 1, L.blk32)
                  : launch_diag_blocks(c, p, L.un, &c->sc->cfl, 1, L.blk);
         if (st != EMG_OK) return st;
         st = f32 ? launch_lu32(c, p) : launch_lu(c, p);
+        if (st != EMG_OK) return st;
+        st = join_side(c);
+        if (st != EMG_OK) return st;
+    } else if (side) {
+        st = side(c);
         if (st != EMG_OK) return st;
     }
     const int s = c->prm.rk_stages;
@@ -139,36 +178,46 @@ emg_status vcycle_body_down(emg_ctx* c) {
         st = launch_dt_global(c, c->dt);
         if (st != EMG_OK) return st;
     }
+    // forcing of the level below (steps 2-3): R~_p(v_p) and R_{p-1}(v0_{p-1}) give tau_{p-1}, and
+    // R~_{p-1}(v0_{p-1}) = R_{p-1}(v0_{p-1}) + tau_{p-1} is the first PRK stage's residual there.
+    // It needs only the restricted state, so it runs on the side stream while the level below
+    // assembles and factors its blocks.
+    auto forcing = [](int p) {
+        return [p](emg_ctx* cc) -> emg_status {
+            LevelDev& Lp = cc->lv[p];
+            LevelDev& Lq = cc->lv[p - 1];
+            emg_status s2 = launch_residual(cc, p, Lp.v, p == cc->p_max ? nullptr : Lp.tau, Lp.r);
+            if (s2 != EMG_OK) return s2;
+            s2 = launch_residual(cc, p - 1, Lq.v0, nullptr, Lq.r2);
+            if (s2 != EMG_OK) return s2;
+            s2 = launch_tau(cc, p - 1, Lp.r, Lq.r2, Lq.tau);
+            if (s2 != EMG_OK) return s2;
+            if (p - 1 >= 1) s2 = launch_axpby(cc, cc->E * Lq.B, 1.0, Lq.r2, 1.0, Lq.tau, Lq.r);
+            return s2;
+        };
+    };
     for (int p = P; p >= 1; --p) {
         LevelDev& L = c->lv[p];
         LevelDev& Lc = c->lv[p - 1];
         const double* tau = p == P ? nullptr : L.tau;
-        const int64_t S = c->E * L.B;
         for (int sm = 0; sm < c->prm.pre_smooth; ++sm) {
-            const double* rfirst = nullptr;
-            if (sm == 0) {
-                if (p == P) {
-                    rfirst = L.r;  // R_pmax(v) from the cycle entry
-                } else {
-                    // R~_p(v0_p) = R_p(v0_p) + tau_p, R_p(v0_p) computed for the forcing (in r2)
-                    st = launch_axpby(c, S, 1.0, L.r2, 1.0, L.tau, L.r);
-                    if (st != EMG_OK) return st;
-                    rfirst = L.r;
-                }
-            }
-            st = prk_step(c, p, tau, rfirst, c->frozen || (c->prm.lag_blocks != 0 && sm > 0));
+            const bool reuse = c->frozen || (c->prm.lag_blocks != 0 && sm > 0);
+            if (sm == 0 && p == P)
+                st = prk_step(c, p, tau, L.r, reuse);   // R_pmax(v) from the cycle entry
+            else if (sm == 0)
+                st = prk_step(c, p, tau, L.r, reuse, forcing(p + 1));   // R~_p(v0_p), from the forcing
+            else
+                st = prk_step(c, p, tau, nullptr, reuse);
             if (st != EMG_OK) return st;
         }
-        // restriction of the smoothed state and of its residual, FAS forcing of level p-1
-        st = launch_residual(c, p, L.v, tau, L.r);
-        if (st != EMG_OK) return st;
+        // restriction of the smoothed state (its residual and the forcing follow, above)
         st = launch_restrict(c, p, L.v, Lc.v0);
         if (st != EMG_OK) return st;
         EMG_CUDA_TRY(c, cudaMemcpyAsync(Lc.v, Lc.v0, c->E * Lc.B * 8, cudaMemcpyDeviceToDevice, c->stream));
-        st = launch_residual(c, p - 1, Lc.v0, nullptr, Lc.r2);
-        if (st != EMG_OK) return st;
-        st = launch_tau(c, p - 1, L.r, Lc.r2, Lc.tau);
-        if (st != EMG_OK) return st;
+        if (p == 1) {   // p = 0 has no blocks to overlap with
+            st = forcing(1)(c);
+            if (st != EMG_OK) return st;
+        }
     }
     LevelDev& L0 = c->lv[0];
     if (P == 0) EMG_CUDA_TRY(c, cudaMemcpyAsync(L0.v0, L0.v, c->E * 5 * 8, cudaMemcpyDeviceToDevice, c->stream));
@@ -407,6 +456,9 @@ emg_status emg_create_mesh(const emg_mesh_desc* m, const emg_params* prm, emg_ct
         EMG_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
         c->own_stream = true;
     }
+    EMG_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking));
+    EMG_CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    EMG_CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     const double g = prm->gamma;
     const double a = prm->alpha_deg * M_PI / 180.0;
     const double vx = prm->mach * std::cos(a), vy = prm->mach * std::sin(a);
@@ -430,6 +482,12 @@ emg_status emg_destroy(emg_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (auto& e : c->prof.ev) cudaEventDestroy(e);
     pinned_scalars_release(c->sc_host);
+    if (c->stream2) {
+        cudaStreamSynchronize(c->stream2);
+        cudaStreamDestroy(c->stream2);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return EMG_OK;

@@ -141,6 +141,9 @@ struct emg_ctx {
     int64_t E = 0, F = 0, F_int = 0, n_nodes = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t stream2 = nullptr;  // side stream: residuals that overlap a level's block build
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool side_pending = false;       // side work enqueued, not yet joined
     int device = 0;
     std::string err;
     int64_t bytes = 0;

@@ -374,6 +374,26 @@ def test_graph_replayed_cycles_are_bitwise_the_kernel_by_kernel_cycles():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("prec", [0, 1])
+def test_side_stream_overlap_is_bitwise_the_serial_order(prec):
+    """The residuals and forcings run on a second stream beside each block build (graph branches
+    or direct launches) give the same bits as the one-stream order the event profiler keeps."""
+    from paper_1807_01151_gb300 import Solver
+    from workloads import ogrid
+    out = []
+    for serial, g in ((1, 0), (0, 0), (0, 1)):
+        s = Solver(ogrid(16, 8), p_max=4, prec=prec, use_graph=g, pre_smooth=2)
+        if serial:
+            s.profile(True)
+        for _ in range(5):
+            s.vcycle(info=False)
+        out.append(s.get_state())
+        s.close()
+    np.testing.assert_array_equal(out[0], out[1])
+    np.testing.assert_array_equal(out[0], out[2])
+
+
+@pytest.mark.gpu
 def test_tuned_kernel_variants_give_bitwise_the_same_cycles():
     """The tuner only picks among variants that compute identically."""
     from paper_1807_01151_gb300 import Solver
