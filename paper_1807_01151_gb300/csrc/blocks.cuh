@@ -20,6 +20,15 @@ __device__ __forceinline__ long long piv_key(double x) {
     return b <= 0x7ff0000000000000ull ? (long long)b : -1ll;
 }
 
+// Two fused multiply-adds d_k <- a b_k + d_k (k = 0, 1) issued as one paired float32
+// instruction; each component is rounded as by fmaf, so the results are bitwise those of two
+// fmaf calls and only the instruction count changes.
+__device__ __forceinline__ void fma2f(float a, float b0, float b1, float& d0, float& d1) {
+    const float2 r = __ffma2_rn(make_float2(a, a), make_float2(b0, b1), make_float2(d0, d1));
+    d0 = r.x;
+    d1 = r.y;
+}
+
 // B = 5 N(p): 2-D p = 1..4, then 3-D p = 1..4 (B = 50 serves both dimensions).
 #define EMG_BSIZES(X) X(15) X(30) X(50) X(75) X(20) X(100) X(175)
 

@@ -83,9 +83,11 @@ __device__ __forceinline__ void gj_panel_steps(float (&x)[RS][NB], unsigned& use
             x[i][s] = 0.0f;
         }
 #pragma unroll
-        for (int i = 0; i < RS; ++i)
+        for (int i = 0; i < RS; ++i) {
 #pragma unroll
-            for (int c = 0; c < NB; ++c) x[i][c] -= f[i] * rk[c];
+            for (int c = 0; c + 1 < NB; c += 2) fma2f(-f[i], rk[c], rk[c + 1], x[i][c], x[i][c + 1]);
+            if (NB % 2) x[i][NB - 1] = fmaf(-f[i], rk[NB - 1], x[i][NB - 1]);
+        }
         if (tx == pl) {
             used |= 1u << pi;
 #pragma unroll
@@ -129,6 +131,24 @@ __device__ __forceinline__ void gj_gather_pivot_rows(const float (&a)[RS][CS], c
                     }
                 }
         }
+    }
+}
+
+// One step of the rank-NB update on the column slots j and j + 1 of a thread,
+// a[i][j] += f[i] y0 and a[i][j + 1] += f[i] y1, for the slots in [JLO, CS) only; both slots
+// in range take one paired multiply-add per row (bitwise two fmaf).
+template <int RS, int CS, int JLO>
+__device__ __forceinline__ void gj_update_pair(float (&a)[RS][CS], const float (&f)[RS], int j, float y0, float y1) {
+    const bool in0 = j >= JLO && j < CS, in1 = j + 1 >= JLO && j + 1 < CS;
+    if (in0 && in1) {
+#pragma unroll
+        for (int i = 0; i < RS; ++i) fma2f(f[i], y0, y1, a[i][j], a[i][j + 1]);
+    } else if (in0) {
+#pragma unroll
+        for (int i = 0; i < RS; ++i) a[i][j] = fmaf(f[i], y0, a[i][j]);
+    } else if (in1) {
+#pragma unroll
+        for (int i = 0; i < RS; ++i) a[i][j + 1] = fmaf(f[i], y1, a[i][j + 1]);
     }
 }
 
@@ -224,11 +244,7 @@ __global__ void __launch_bounds__(32 * W) k_gj_blk(int E, float* __restrict__ bl
                 const float4 y4 = *reinterpret_cast<const float4*>(yr + j0);
                 const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (j0 + q < CS - SPW) {
-#pragma unroll
-                        for (int i = 0; i < RS; ++i) a[i][SPW + j0 + q] = fmaf(f[i], yv[q], a[i][SPW + j0 + q]);
-                    }
+                for (int q = 0; q < 4; q += 2) gj_update_pair<RS, CS, SPW>(a, f, SPW + j0 + q, yv[q], yv[q + 1]);
             }
         }
         // the panel's own columns become F
@@ -411,13 +427,8 @@ __global__ void __launch_bounds__(32 * (W + 1)) k_gj_la(int E, float* __restrict
                     const float4 y4 = *reinterpret_cast<const float4*>(yr + j0);
                     const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int j = SPW + j0 + q;
-                        if (j >= 2 * SPW && j < CS) {
-#pragma unroll
-                            for (int i = 0; i < RS; ++i) a[i][j] = fmaf(f[i], yv[q], a[i][j]);
-                        }
-                    }
+                    for (int q = 0; q < 4; q += 2)
+                        gj_update_pair<RS, CS, 2 * SPW>(a, f, SPW + j0 + q, yv[q], yv[q + 1]);
                 }
             }
             // (3) the panel's own columns become F

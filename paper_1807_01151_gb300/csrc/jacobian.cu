@@ -14,6 +14,7 @@
 
 #include <cuda_bf16.h>
 
+#include "blocks.cuh"
 #include "common.cuh"
 #include "dispatch.cuh"
 #include "euler.cuh"
@@ -560,9 +561,9 @@ __global__ void __launch_bounds__(DiagRb<D, P>::THREADS, DiagRb<D, P>::MINB) k_d
                         const float4 v = *reinterpret_cast<const float4*>(&ps[t][j0 + jj]);
                         const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                        for (int c = 0; c < 4; ++c)
+                        for (int c = 0; c < 4; c += 2)
 #pragma unroll
-                            for (int b = 0; b < 5; ++b) acc[b][jj + c] += s[b] * vv[c];
+                            for (int b = 0; b < 5; ++b) fma2f(s[b], vv[c], vv[c + 1], acc[b][jj + c], acc[b][jj + c + 1]);
                     }
                 }
             }
@@ -592,9 +593,9 @@ __global__ void __launch_bounds__(DiagRb<D, P>::THREADS, DiagRb<D, P>::MINB) k_d
                     const float4 v = *reinterpret_cast<const float4*>(&fps[t][j0 + jj]);
                     const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                    for (int c = 0; c < 4; ++c)
+                    for (int c = 0; c < 4; c += 2)
 #pragma unroll
-                        for (int b = 0; b < 5; ++b) acc[b][jj + c] += s[b] * vv[c];
+                        for (int b = 0; b < 5; ++b) fma2f(s[b], vv[c], vv[c + 1], acc[b][jj + c], acc[b][jj + c + 1]);
                 }
             }
         }
