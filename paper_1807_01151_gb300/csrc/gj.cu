@@ -49,10 +49,11 @@ __device__ __forceinline__ unsigned piv_pack(float x, int r) {
 
 // The in-place Gauss-Jordan steps of a panel of NB columns held by one warp (lane tx: rows
 // tx + 32 i, x[i][c] for panel column c), one warp reduction per pivot: pivot rows are
-// recorded in perm[k0 + s] and piv[s]; `used` marks this lane's rows already taken.
+// recorded in perm[k0 + s] and their steps in invk[p] = k0 + s; `used` marks this lane's rows
+// already taken.
 template <int B, int RS, int NB>
 __device__ __forceinline__ void gj_panel_steps(float (&x)[RS][NB], unsigned& used, int nb, int k0, int tx, int* perm,
-                                               int* piv) {
+                                               int* invk) {
 #pragma unroll
     for (int s = 0; s < NB; ++s) {
         if (s >= nb) break;   // uniform
@@ -99,38 +100,51 @@ __device__ __forceinline__ void gj_panel_steps(float (&x)[RS][NB], unsigned& use
         }
         if (tx == 0) {
             perm[k0 + s] = p;
-            piv[s] = p;
+            invk[p] = k0 + s;
         }
     }
 }
 
 // The panel's pivot rows on this warp's non-panel slots j = SPW .. CS-1 into its buffer yw
-// (row s at yw + s YL; written by the owner lane, 16 bytes at a time), and the factor m[i] that
-// clears this lane's pivot rows (they are rebuilt from F alone): 0 for a pivot row, else 1.
-template <int RS, int CS, int SPW, int YL, int NB>
-__device__ __forceinline__ void gj_gather_pivot_rows(const float (&a)[RS][CS], const int* piv, int nb, int tx,
-                                                     float* yw, float (&m)[RS]) {
+// (the row of step k0 + s at yw + s YL, 16 bytes at a time), and the factor m[i] that clears
+// this lane's pivot rows (they are rebuilt from F alone): 0 for a pivot row, else 1.  Every
+// lane writes its own rows at once: invk[r] is the step at which row r was chosen (-1 while
+// it has not been; rows >= B never are), so the panel's pivot rows are those with
+// k0 <= invk[r] < k0 + nb.
+template <int RS, int CS, int SPW, int YL>
+__device__ __forceinline__ void gj_gather_pivot_rows(const float (&a)[RS][CS], const int* invk, int k0, int nb,
+                                                     int tx, float* yw, float (&m)[RS]) {
 #pragma unroll
-    for (int i = 0; i < RS; ++i) m[i] = 1.0f;
-    for (int s = 0; s < nb; ++s) {
-        const int p = piv[s];
-        const int pl = p & 31, pi = p >> 5;
-        if (tx == pl) {
+    for (int i = 0; i < RS; ++i) {
+        const int s = invk[tx + 32 * i] - k0;
+        const bool piv = (unsigned)s < (unsigned)nb;
+        m[i] = piv ? 0.0f : 1.0f;
+        if (piv) {
 #pragma unroll
-            for (int ii = 0; ii < RS; ++ii)
-                if (pi == ii) {
-                    m[ii] = 0.0f;
-#pragma unroll
-                    for (int j0 = 0; j0 < CS - SPW; j0 += 4) {
-                        float4 v;
-                        v.x = a[ii][SPW + j0];
-                        v.y = (j0 + 1 < CS - SPW) ? a[ii][SPW + j0 + 1] : 0.0f;
-                        v.z = (j0 + 2 < CS - SPW) ? a[ii][SPW + j0 + 2] : 0.0f;
-                        v.w = (j0 + 3 < CS - SPW) ? a[ii][SPW + j0 + 3] : 0.0f;
-                        *reinterpret_cast<float4*>(yw + s * YL + j0) = v;
-                    }
-                }
+            for (int j0 = 0; j0 < CS - SPW; j0 += 4) {
+                float4 v;
+                v.x = a[i][SPW + j0];
+                v.y = (j0 + 1 < CS - SPW) ? a[i][SPW + j0 + 1] : 0.0f;
+                v.z = (j0 + 2 < CS - SPW) ? a[i][SPW + j0 + 2] : 0.0f;
+                v.w = (j0 + 3 < CS - SPW) ? a[i][SPW + j0 + 3] : 0.0f;
+                *reinterpret_cast<float4*>(yw + s * YL + j0) = v;
+            }
         }
+    }
+}
+
+// a[i][j] *= m[i] on the non-panel slots j = SPW .. CS-1, two products per instruction.
+template <int RS, int CS, int SPW>
+__device__ __forceinline__ void gj_clear_pivot_rows(float (&a)[RS][CS], const float (&m)[RS]) {
+#pragma unroll
+    for (int i = 0; i < RS; ++i) {
+#pragma unroll
+        for (int j = SPW; j + 1 < CS; j += 2) {
+            const float2 r = __fmul2_rn(make_float2(a[i][j], a[i][j + 1]), make_float2(m[i], m[i]));
+            a[i][j] = r.x;
+            a[i][j + 1] = r.y;
+        }
+        if ((CS - SPW) % 2) a[i][CS - 1] *= m[i];
     }
 }
 
@@ -171,7 +185,7 @@ struct GjBlk {
 };
 
 template <int B, int W>
-__global__ void __launch_bounds__(32 * W) k_gj_blk(int E, float* __restrict__ blk) {
+__global__ void __launch_bounds__(32 * W, 16 / W) k_gj_blk(int E, float* __restrict__ blk) {
     using G = GjBlk<B, W>;
     constexpr int NB = G::NB, SPW = G::SPW, RS = G::RS, R32 = G::R32, NP = G::NP, CS = G::CS;
     constexpr int PLD = G::PLD, YL = G::YL, LD = G::LD, T = 32 * W;
@@ -180,11 +194,11 @@ __global__ void __launch_bounds__(32 * W) k_gj_blk(int E, float* __restrict__ bl
     float* Pn = tile;                                   // panel columns [R32][PLD]
     float* Fs = tile + R32 * PLD;                       // factored panel F [R32][PLD]
     float* Yw = tile + 2 * R32 * PLD;                   // pivot rows, per warp [W][NB][YL]
-    __shared__ int perm[B], invp[B];
-    __shared__ int s_piv[NB];
+    __shared__ int perm[B], invk[R32];
     const int e = blockIdx.x;
     const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
     float* g = blk + (size_t)e * B * B;
+    for (int t = threadIdx.x; t < R32; t += T) invk[t] = -1;
     for (int t = threadIdx.x; t < B * B; t += T) tile[(t / B) * LD + (t % B)] = g[t];
     __syncthreads();
     float a[RS][CS];
@@ -215,7 +229,7 @@ __global__ void __launch_bounds__(32 * W) k_gj_blk(int E, float* __restrict__ bl
             for (int i = 0; i < RS; ++i)
 #pragma unroll
                 for (int c = 0; c < NB; ++c) x[i][c] = Pn[(tx + 32 * i) * PLD + c];
-            gj_panel_steps<B, RS, NB>(x, used, nb, k0, tx, perm, s_piv);
+            gj_panel_steps<B, RS, NB>(x, used, nb, k0, tx, perm, invk);
 #pragma unroll
             for (int i = 0; i < RS; ++i)
 #pragma unroll
@@ -226,12 +240,9 @@ __global__ void __launch_bounds__(32 * W) k_gj_blk(int E, float* __restrict__ bl
         // rows' own entries are then cleared (they are rebuilt from F alone)
         __syncwarp();
         float mrow[RS];
-        gj_gather_pivot_rows<RS, CS, SPW, YL, NB>(a, s_piv, nb, tx, yw, mrow);
+        gj_gather_pivot_rows<RS, CS, SPW, YL>(a, invk, k0, nb, tx, yw, mrow);
         __syncwarp();
-#pragma unroll
-        for (int i = 0; i < RS; ++i)
-#pragma unroll
-            for (int j = SPW; j < CS; ++j) a[i][j] *= mrow[i];
+        gj_clear_pivot_rows<RS, CS, SPW>(a, mrow);
 #pragma unroll
         for (int s = 0; s < NB; ++s) {
             if (s >= nb) break;   // uniform
@@ -266,14 +277,12 @@ __global__ void __launch_bounds__(32 * W) k_gj_blk(int E, float* __restrict__ bl
     }
     // NP rotations by SPW = CS slots: every column is back in its own slot
     __syncthreads();
-    for (int t = threadIdx.x; t < B; t += T) invp[perm[t]] = t;
-    __syncthreads();
 #pragma unroll
     for (int i = 0; i < RS; ++i)
 #pragma unroll
         for (int j = 0; j < CS; ++j) {
             const int r = tx + 32 * i, c = w + W * j;
-            if (r < B && c < B) tile[perm[c] * LD + invp[r]] = a[i][j];
+            if (r < B && c < B) tile[perm[c] * LD + invk[r]] = a[i][j];
         }
     __syncthreads();
     for (int t = threadIdx.x; t < B * B; t += T) g[t] = tile[(t / B) * LD + (t % B)];
@@ -324,11 +333,11 @@ __global__ void __launch_bounds__(32 * (W + 1)) k_gj_la(int E, float* __restrict
     float* Pn = tile;                                   // 2 x [R32][PLD] panel columns
     float* Fs = tile + 2 * R32 * PLD;                   // 2 x [R32][PLD] factored panels
     float* Yw = tile + 4 * R32 * PLD;                   // [W][NB][YL] pivot rows per update warp
-    __shared__ int perm[B], invp[B];
-    __shared__ int s_piv[2][NB];
+    __shared__ int perm[B], invk[R32];
     const int e = blockIdx.x;
     const int tx = threadIdx.x & 31, wq = threadIdx.x >> 5, w = wq - 1;
     float* g = blk + (size_t)e * B * B;
+    for (int t = threadIdx.x; t < R32; t += T) invk[t] = -1;
     for (int t = threadIdx.x; t < B * B; t += T) tile[(t / B) * LD + (t % B)] = g[t];
     __syncthreads();
     float a[RS][CS];
@@ -357,7 +366,7 @@ __global__ void __launch_bounds__(32 * (W + 1)) k_gj_la(int E, float* __restrict
             for (int i = 0; i < RS; ++i)
 #pragma unroll
                 for (int c = 0; c < NB; ++c) x[i][c] = pn[(tx + 32 * i) * PLD + c];
-            gj_panel_steps<B, RS, NB>(x, used, nb, k0, tx, perm, s_piv[t & 1]);
+            gj_panel_steps<B, RS, NB>(x, used, nb, k0, tx, perm, invk);
 #pragma unroll
             for (int i = 0; i < RS; ++i)
 #pragma unroll
@@ -380,15 +389,14 @@ __global__ void __launch_bounds__(32 * (W + 1)) k_gj_la(int E, float* __restrict
             const int nb = (B - k0) < NB ? (B - k0) : NB;
             const float* fs = Fs + (t & 1) * R32 * PLD;
             named_sync(BAR_F, T);
-            // pivot rows of this warp's non-panel columns; their own entries are rebuilt from F
+            // pivot rows of this warp's non-panel columns; their own entries are rebuilt from F.
+            // Warp 0 may meanwhile be recording panel t+1's pivots in invk: a row it records
+            // reads as -1 or as a step >= k0 + NB, outside this panel's range either way.
             __syncwarp();
             float mrow[RS];
-            gj_gather_pivot_rows<RS, CS, SPW, YL, NB>(a, s_piv[t & 1], nb, tx, yw, mrow);
+            gj_gather_pivot_rows<RS, CS, SPW, YL>(a, invk, k0, nb, tx, yw, mrow);
             __syncwarp();
-#pragma unroll
-            for (int i = 0; i < RS; ++i)
-#pragma unroll
-                for (int j = SPW; j < CS; ++j) a[i][j] *= mrow[i];
+            gj_clear_pivot_rows<RS, CS, SPW>(a, mrow);
             // (1) slots SPW .. 2 SPW - 1 first: the next panel's columns, handed to warp 0 at once
             // (at the last panel they hold earlier columns, updated like the rest)
 #pragma unroll
@@ -449,15 +457,13 @@ __global__ void __launch_bounds__(32 * (W + 1)) k_gj_la(int E, float* __restrict
         }
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < B; t += T) invp[perm[t]] = t;
-    __syncthreads();
     if (wq > 0) {
 #pragma unroll
         for (int i = 0; i < RS; ++i)
 #pragma unroll
             for (int j = 0; j < CS; ++j) {
                 const int r = tx + 32 * i, c = w + W * j;
-                if (r < B && c < B) tile[perm[c] * LD + invp[r]] = a[i][j];
+                if (r < B && c < B) tile[perm[c] * LD + invk[r]] = a[i][j];
             }
     }
     __syncthreads();
