@@ -73,8 +73,9 @@ def diag_flops(s):
     return s.E * (vol + face)
 
 
-def diag_bytes(s):
-    return s.E * s.B * s.B * 8
+def diag_bytes(s, fb=8):
+    """The assembled blocks written once, fb bytes per entry (8: FP64 form, 4: float32 forms)."""
+    return s.E * s.B * s.B * fb
 
 
 def lu_flops(s):
@@ -85,9 +86,10 @@ def stage_flops(s):
     return s.E * 2.0 * s.B * s.B
 
 
-def stage_bytes(s):
-    """LU factors read once, residual and u^n in, u^(k) out."""
-    return s.E * (s.B * s.B * 8 + 3 * s.B * 8 + s.B * 4)
+def stage_bytes(s, fb=8):
+    """Factors (FP64 form) or inverse (float32 forms, fb = 4) read once, residual and u^n in,
+    u^(k) out."""
+    return s.E * (s.B * s.B * fb + 3 * s.B * 8 + (s.B * 4 if fb == 8 else 0))
 
 
 def inverse_flops(s):
@@ -97,6 +99,7 @@ def inverse_flops(s):
 
 def vcycle_work(dim, p_max, E, F, rk_stages=4, pre_smooth=2, krylov_m=30, form=0):
     """Per-V-cycle algorithmic FLOPs and compulsory bytes of each kernel class."""
+    fb = 8 if form == 0 else 4   # bytes per block entry: FP64 factors or float32 inverses
     w = {k: [0.0, 0.0] for k in ("residual_face_flux", "residual_volume", "diag_block_assembly", "block_lu",
                                  "prk_stage_solve", "arnoldi")}
     # residual evaluations per level: cycle entry (p_max) or forcing (p < p_max),
@@ -113,11 +116,11 @@ def vcycle_work(dim, p_max, E, F, rk_stages=4, pre_smooth=2, krylov_m=30, form=0
         w["residual_volume"][1] += n_res * residual_bytes(s) / 2
         if p > 0:
             w["diag_block_assembly"][0] += pre_smooth * diag_flops(s)
-            w["diag_block_assembly"][1] += pre_smooth * diag_bytes(s)
+            w["diag_block_assembly"][1] += pre_smooth * diag_bytes(s, fb)
             w["block_lu"][0] += pre_smooth * (lu_flops(s) if form == 0 else inverse_flops(s))
-            w["block_lu"][1] += pre_smooth * 2 * diag_bytes(s)
+            w["block_lu"][1] += pre_smooth * 2 * diag_bytes(s, fb)
             w["prk_stage_solve"][0] += pre_smooth * rk_stages * stage_flops(s)
-            w["prk_stage_solve"][1] += pre_smooth * rk_stages * stage_bytes(s)
+            w["prk_stage_solve"][1] += pre_smooth * rk_stages * stage_bytes(s, fb)
     K0 = 5 * E
     nf = 2 * dim
     # Arnoldi: m SpMVs over the BSR matrix and CGS2 (two passes of j+1 dots and updates)
