@@ -512,6 +512,28 @@ __global__ void __launch_bounds__(DiagRb<D, P>::THREADS, DiagRb<D, P>::MINB) k_d
     for (int b = 0; b < 5; ++b)
 #pragma unroll
         for (int j = 0; j < JW; ++j) acc[b][j] = 0.0f;
+    // face data (basis traces and the signed face Jacobians) of the next face, loaded into
+    // registers one face ahead so that the loads overlap the previous face's (or, for the
+    // first face, the volume's) accumulation; stored to shared memory between two barriers
+    constexpr int T = R::THREADS;
+    constexpr int NPF = (QF * NPAD + T - 1) / T, NJF = (QF * 25 + T - 1) / T;
+    float pf[NPF], pj[NJF];
+    auto fetch_face = [&](int lf) {
+        const int code = elem_face[(size_t)e * NF + lf];
+        const float* pt = ((code & 1) ? fpsiR : fpsiL) + ((size_t)(code >> 1) * QF) * N;
+        const float* fj = ((code & 1) ? fjr : fjl) + ((size_t)(code >> 1) * QF) * 25;
+#pragma unroll
+        for (int k = 0; k < NPF; ++k) {
+            const int t = tid + k * T, q = t / NPAD, j = t % NPAD;
+            pf[k] = (t < QF * NPAD && j < N) ? pt[q * N + j] : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < NJF; ++k) {
+            const int t = tid + k * T;
+            pj[k] = t < QF * 25 ? ((code & 1) ? fj[t] : -fj[t]) : 0.0f;
+        }
+    };
+    fetch_face(0);
     if (P > 0) {
         for (int q0 = 0; q0 < Q; q0 += QC) {
             const int nq = (Q - q0) < QC ? (Q - q0) : QC;
@@ -571,16 +593,19 @@ __global__ void __launch_bounds__(DiagRb<D, P>::THREADS, DiagRb<D, P>::MINB) k_d
     }
 #pragma unroll 1
     for (int lf = 0; lf < NF; ++lf) {
-        const int code = elem_face[(size_t)e * NF + lf];
-        const float* pt = ((code & 1) ? fpsiR : fpsiL) + ((size_t)(code >> 1) * QF) * N;
-        const float* fj = ((code & 1) ? fjr : fjl) + ((size_t)(code >> 1) * QF) * 25;
         __syncthreads();
-        for (int t = tid; t < QF * NPAD; t += blockDim.x) {
-            const int q = t / NPAD, j = t % NPAD;
-            fps[q][j] = j < N ? pt[q * N + j] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < NPF; ++k) {
+            const int t = tid + k * T;
+            if (t < QF * NPAD) fps[t / NPAD][t % NPAD] = pf[k];
         }
-        for (int t = tid; t < QF * 25; t += blockDim.x) fjs[t / 25][t % 25] = (code & 1) ? fj[t] : -fj[t];
+#pragma unroll
+        for (int k = 0; k < NJF; ++k) {
+            const int t = tid + k * T;
+            if (t < QF * 25) fjs[t / 25][t % 25] = pj[k];
+        }
         __syncthreads();
+        if (lf + 1 < NF) fetch_face(lf + 1);
         if (active) {
 #pragma unroll 1
             for (int t = 0; t < QF; ++t) {
