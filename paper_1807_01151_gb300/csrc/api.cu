@@ -133,11 +133,11 @@ static emg_status prk_step(emg_ctx* c, int p, const double* tau, const double* r
         if (st != EMG_OK) return st;
         st = f32 ? launch_diag_blocks32(c, p, L.un, &c->sc->cfl, 1, L.blk32)
                  : launch_diag_blocks(c, p, L.un, &c->sc->cfl, 1, L.blk);
+        if (st == EMG_OK) st = f32 ? launch_lu32(c, p) : launch_lu(c, p);
+        // joined on every path: a fork left open would also invalidate a graph capture
+        const emg_status sj = join_side(c);
         if (st != EMG_OK) return st;
-        st = f32 ? launch_lu32(c, p) : launch_lu(c, p);
-        if (st != EMG_OK) return st;
-        st = join_side(c);
-        if (st != EMG_OK) return st;
+        if (sj != EMG_OK) return sj;
     } else if (side) {
         st = side(c);
         if (st != EMG_OK) return st;
