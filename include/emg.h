@@ -17,9 +17,9 @@
  *     dimension) is requested, which synchronises the stream.
  *   - Within a call the context may fork work onto a second stream it owns (residual
  *     evaluations that run beside a level's block build) and joins it back before the
- *     call's next dependent step; seen from the caller every call is ordered on the
- *     context's stream (also inside a graph capture of that stream, where the fork and
- *     the join become graph edges).
+ *     call's next dependent step, so that seen from the caller every call stays ordered
+ *     on the context's stream (in the V-cycle graphs the context captures itself, the
+ *     fork and the join are graph edges).
  *   - Modal states use the canonical layout [n_elems][5][N_p] (float64), variables
  *     (rho, rho u, rho v, rho w, rho E) (rho w is kept, and stays 0, in 2-D), modes
  *     in the basis order: total degree 0..p, within a degree x exponent descending,
