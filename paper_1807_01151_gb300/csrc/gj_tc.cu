@@ -6,7 +6,8 @@
 
 namespace emg {
 // ---- blocked Gauss-Jordan inversion with tensor-core trailing updates (tcgen05) ---------------
-// The in-place Gauss-Jordan steps of the kernels above, grouped in panels of KB = 16 pivot
+// The in-place Gauss-Jordan steps of the SIMT forms (gj.cu, gj_tile.cu, gj_cols.cu), grouped
+// in panels of KB = 16 pivot
 // columns.  Step k with pivot row p acts on every column c != k as A[:, c] <- M_k A[:, c],
 // M_k = I + x_k e_p^T, so the KB steps of a panel act on the columns outside it as
 // T = I + X S_P^T (S_P selects the panel's pivot rows); X[:, j] is the panel's column j after
@@ -17,7 +18,7 @@ namespace emg {
 // are warp shuffles, so the steps need no block barrier); then every other column takes the
 // rank-KB update A += X A[P, :] as one tcgen05.mma per row tile and 32-byte K step (3xTF32:
 // x = hi + lo, X_hi R_hi + X_hi R_lo + X_lo R_hi, float32 accumulation).  Pivot choice and tie
-// rule are those of the kernels above (largest |a_rk| among the unused rows, lowest row on
+// rule are those of the SIMT forms (largest |a_rk| among the unused rows, lowest row on
 // ties, the lowest unused row for a non-finite column); the inverse is written column-major
 // with the same permutation.
 template <int B>
