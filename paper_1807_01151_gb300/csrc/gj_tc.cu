@@ -7,8 +7,8 @@
 namespace emg {
 // ---- blocked Gauss-Jordan inversion with tensor-core trailing updates (tcgen05) ---------------
 // The in-place Gauss-Jordan steps of the SIMT forms (gj.cu, gj_tile.cu, gj_cols.cu), grouped
-// in panels of KB = 16 pivot
-// columns.  Step k with pivot row p acts on every column c != k as A[:, c] <- M_k A[:, c],
+// in panels of KB = 16 pivot columns.  Step k with pivot row p acts on every column c != k as
+// A[:, c] <- M_k A[:, c],
 // M_k = I + x_k e_p^T, so the KB steps of a panel act on the columns outside it as
 // T = I + X S_P^T (S_P selects the panel's pivot rows); X[:, j] is the panel's column j after
 // all KB steps minus e_{p_j} (the in-place rule leaves M_j e_{p_j} in column j at step j).
