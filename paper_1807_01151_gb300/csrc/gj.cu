@@ -34,9 +34,10 @@ emg_status launch_gj_tc(emg_ctx* c, int B, float* blk, bool* built);
 // columns in a warp-private buffer (no block barrier) and applies the rank-NB update,
 // s = 0 .. NB-1 in order, one FMA per term.  Pivot choice and tie rule are those of the
 // unblocked forms in gj_tile.cu and gj_cols.cu (largest |a_rk| among the unused rows, lowest
-// row on ties, the lowest unused row if no candidate is a number).  The summation order differs from the unblocked forms
-// (results agree to float rounding, not bitwise); the variants with different W compute
-// identically.  The inverse is written column-major, as by the other forms.
+// row on ties, the lowest unused row if no candidate is a number).  The summation order
+// differs from the unblocked forms (results agree to float rounding, not bitwise); the
+// variants with different W compute identically.  The inverse is written column-major, as
+// by the other forms.
 // ---- pieces shared by the blocked forms (k_gj_blk, k_gj_la) --------------------------------
 // Pivot key of row r: the magnitude bits of |a| without their lowest 8 (pivots within 2^-15
 // relative of each other tie), then 255 - r, so that the largest key is a row of (nearly) the
