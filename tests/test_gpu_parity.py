@@ -2,7 +2,7 @@
 
 Tolerances: the oracle and the kernels evaluate the same FP64 formulas in different
 orders, so single-kernel results agree to a few ulps times the condition of the step;
-the spec bars are 1e-11 (relative) per V-cycle and 1e-9 on the converged state.
+the target tolerances are 1e-11 (relative) per V-cycle and 1e-9 on the converged state.
 """
 import os
 
