@@ -142,7 +142,7 @@ typedef struct {
                               rotation about z, omega = (0, 0, w), is accepted (else
                               EMG_ERR_ARG); non-finite values: EMG_ERR_ARG. */
     int32_t block_kernels; /* kernels of the float32 block forms' assembly and inverse:
-                              0 (default): per level, the form this build measured faster;
+                              0 (default): per level, the form measured faster on GB300;
                               1: the tensor-core forms (tcgen05: 3xTF32 assembly, blocked
                               Gauss-Jordan with rank-16 MMA updates for B = 75, 100, 175);
                               2: the SIMT (FMA) forms (blocked Gauss-Jordan with rank-8

@@ -46,7 +46,7 @@ class Options:
     cfl_max: float = 100.0
     exp_dt_factor: float = 0.0      # <= 0 -> p_max + 1
     breakdown_rel: float = 1e-12
-    res_ref: float = 0.0            # ||R(rho_1)|| of the first cycle (set by the driver)
+    res_ref: float = 0.0            # ||R(rho_1)|| of the first cycle (set by the solve loop)
     pre_smooth: int = 2             # PRK steps per level on the down leg
     krylov_tol: float = 0.0         # > 0: stop the Arnoldi process by the error estimate
     exp_dt_global: bool = False     # one EXP1 step min_e dt_e for the whole mesh
