@@ -74,3 +74,29 @@ def test_residual_count_per_cycle(p_max):
     # 128x64 cylinder at p = 4: 38 evaluations per cycle (the bench's launch count per class)
     if p_max == 4:
         assert sum(counts.values()) == 38
+
+
+def test_kernel_rooflines_divide_model_work_by_measured_time():
+    """bench.py's per-class rooflines: ALU classes report FLOPs / time against the pipe's peak
+    (FP64 for the FP64 form's block kernels, FP32 for the float32 forms), HBM classes bytes /
+    time against the copy bandwidth."""
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "bench_mod", os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    work = pm.vcycle_work(2, 4, 8192, 16512, form=1)
+    prof = {k: {"ms_per_cycle": 2.0} for k in work}
+    peaks = {"fp64_tflops": 1.0, "fp32_tflops": 80.0}
+    out = bench.kernel_rooflines(prof, work, peaks, 6800.0, 1)
+    for k, v in out.items():
+        if v["bound"] == "alu":
+            assert v["achieved"] == pytest.approx(work[k][0] / 2e-3 / 1e12)
+        else:
+            assert v["achieved"] == pytest.approx(work[k][1] / 2e-3 / 1e9)
+        assert v["frac"] == pytest.approx(v["achieved"] / v["peak"])
+    assert out["block_lu"]["peak"] == 80.0 and out["residual_volume"]["peak"] == 1.0
+    assert out["prk_stage_solve"]["bound"] == "hbm" and out["prk_stage_solve"]["peak"] == 6800.0
+    assert bench.kernel_rooflines(prof, pm.vcycle_work(2, 4, 8192, 16512, form=0), peaks, 6800.0,
+                                  0)["block_lu"]["peak"] == 1.0
