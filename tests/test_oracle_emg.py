@@ -261,3 +261,49 @@ def test_frozen_blocks_converge_to_the_same_steady_state():
                                      opts=emg.Options(jac_freeze=3, exp_dt_global=True))
     assert ok, cycles
     assert np.abs(u - u_newton).max() < 1e-9 * np.abs(u_newton).max()
+
+
+def test_arnoldi_orthonormal_basis_and_hessenberg_projection():
+    """Eq. vm: the Arnoldi vectors are orthonormal with v_1 = b/|b|, span the Krylov space
+    {b, Ab, A^2 b, ...}, and H_k = V_k A V_k^T is upper Hessenberg; an invariant subspace of
+    dimension 3 that contains b ends the process after three steps (happy breakdown)."""
+    rng = np.random.default_rng(11)
+    K, m = 40, 12
+    A = rng.standard_normal((K, K))
+    b = rng.standard_normal(K)
+    V, H, beta, k = emg.arnoldi(lambda x: A @ x, b, m)
+    assert k == m and beta == pytest.approx(np.linalg.norm(b), rel=1e-15)
+    assert np.abs(V @ V.T - np.eye(k)).max() < 1e-13
+    assert np.abs(V[0] - b / np.linalg.norm(b)).max() < 1e-15
+    assert np.abs(V @ A @ V.T - H).max() < 1e-12 * np.abs(A).max() * K
+    assert np.abs(np.tril(H, -2)).max() == 0.0
+    kr = np.stack([np.linalg.matrix_power(A, j) @ b for j in range(4)])
+    assert np.abs(kr - (kr @ V.T) @ V).max() < 1e-9 * np.abs(kr).max()
+    # invariant subspace span(q1, q2, q3) with eigenvalues 1, -2, 4 and b its sum: the Krylov
+    # space has dimension 3, the subdiagonal (sqrt 6, sqrt 3) stays well away from rounding
+    Q, _ = np.linalg.qr(rng.standard_normal((K, K)))
+    M = np.zeros((K, K))
+    M[:3, :3] = np.diag([1.0, -2.0, 4.0])
+    M[3:, 3:] = rng.standard_normal((K - 3, K - 3))
+    A2 = Q @ M @ Q.T
+    b2 = Q[:, :3] @ np.ones(3)
+    _, H2, _, k2 = emg.arnoldi(lambda x: A2 @ x, b2, m)
+    assert k2 == 3
+    assert np.allclose(np.diag(H2, -1), [np.sqrt(6.0), np.sqrt(3.0)], rtol=1e-12)
+
+
+def test_residual_norm_is_the_l2_norm_of_the_density_residual_field():
+    """The norm of Eq. cfl: with the orthonormal basis the sum of the squared density
+    coefficients equals the quadrature of R_h(rho)^2 over the mesh (on the rule the basis was
+    orthonormalised with, p = p_max); the norm divides its square root by |Omega|, itself the
+    quadrature of 1."""
+    dg = DG(ogrid(6, 3), 2)
+    L = dg.levels[2]
+    R = np.random.default_rng(5).standard_normal((dg.E, 5, dg.N(2)))
+    Rh = np.einsum('eqi,ei->eq', L.psi, R[:, 0, :])
+    vol = L.W.sum()
+    assert vol == pytest.approx(dg.mesh.domain_volume, rel=1e-13)
+    assert emg.residual_norm(dg, R) == pytest.approx(np.sqrt(np.sum(L.W * Rh ** 2)) / vol, rel=1e-12)
+    R2 = R.copy()
+    R2[:, 1:, :] = 0.0
+    assert emg.residual_norm(dg, R2) == emg.residual_norm(dg, R)

@@ -107,3 +107,19 @@ def test_face_matching_and_normals_close_the_element():
         n_int = len(m.int_L)
         n_bnd = len(m.bnd_L)
         assert 2 * n_int + n_bnd == m.E * m.nf
+
+
+def test_gauss_legendre_rule():
+    """q-point Gauss-Legendre on [-1, 1]: the two-point rule +-1/sqrt(3) with unit weights, and
+    every rule integrates x^k exactly for k <= 2q - 1 (2/(k + 1) for even k, 0 for odd) but
+    not x^(2q)."""
+    from oracle.geometry import gauss_legendre
+    x, w = gauss_legendre(2)
+    assert np.allclose(np.sort(x), [-1 / np.sqrt(3), 1 / np.sqrt(3)], rtol=0, atol=1e-15)
+    assert np.allclose(w, [1.0, 1.0], rtol=0, atol=1e-15)
+    for q in range(1, 8):
+        x, w = gauss_legendre(q)
+        for k in range(2 * q):
+            exact = 2.0 / (k + 1) if k % 2 == 0 else 0.0
+            assert abs(np.sum(w * x ** k) - exact) < 1e-14
+        assert abs(np.sum(w * x ** (2 * q)) - 2.0 / (2 * q + 1)) > 1e-6

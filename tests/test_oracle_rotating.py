@@ -98,3 +98,14 @@ def test_rotating_jacobians_against_finite_differences():
 def test_rotation_axis_must_be_z_in_2d():
     with pytest.raises(ValueError):
         DG(ogrid(4, 2), 1, omega=(0.1, 0.0, 0.0))
+
+
+def test_frame_velocity_is_omega_cross_x():
+    """v_r = omega x x: about z in 2-D, (-w y, w x, 0); in 3-D the three components of the
+    cross product (its sign decides the direction of the relative fluxes)."""
+    dg = DG(ogrid(4, 2), 1, omega=(0.0, 0.0, 0.5))
+    x = np.array([[1.0, 2.0], [-3.0, 0.5]])
+    assert np.allclose(dg.frame_velocity(x), [[-1.0, 0.5, 0.0], [-0.25, -1.5, 0.0]], rtol=0, atol=1e-15)
+    dg3 = DG(cubed_sphere_shell(1, 1), 1, omega=(1.0, 2.0, 3.0))
+    assert np.allclose(dg3.frame_velocity(np.array([[4.0, 5.0, 6.0]])), [[2 * 6 - 3 * 5, 3 * 4 - 1 * 6, 1 * 5 - 2 * 4]],
+                       rtol=0, atol=1e-15)
