@@ -123,3 +123,25 @@ def test_gauss_legendre_rule():
             exact = 2.0 / (k + 1) if k % 2 == 0 else 0.0
             assert abs(np.sum(w * x ** k) - exact) < 1e-14
         assert abs(np.sum(w * x ** (2 * q)) - 2.0 / (2 * q + 1)) > 1e-6
+
+
+@pytest.mark.parametrize("mk", [lambda: ogrid(8, 3), lambda: cubed_sphere_shell(2, 1)])
+def test_wall_normals_are_radial_on_circle_and_sphere(mk):
+    """The slip-wall reflection normal (node normals of the true wall, interpolated with the
+    face's shape functions and normalised): for a circle or a sphere about the origin the
+    interpolated node normals are the face point over the radius, so the normal is the point's
+    radial direction exactly, not the facet normal; far-field faces keep the facet normal."""
+    from oracle.dg import DG
+    from workloads import BC_WALL
+    dg = DG(mk(), 1)
+    m, L = dg.mesh, dg.levels[1]
+    wall = m.bnd_code == BC_WALL
+    assert wall.any()
+    x = L.bnd_x[wall]
+    radial = np.zeros(x.shape[:-1] + (3,))
+    radial[..., :dg.dim] = x / np.linalg.norm(x, axis=-1, keepdims=True)
+    wn = L.bnd_wn[wall]
+    assert np.abs(np.abs(np.sum(wn * radial, axis=-1)) - 1.0).max() < 1e-13
+    facet = L.bnd_n[wall]
+    assert np.abs(np.abs(np.sum(facet * radial, axis=-1)) - 1.0).max() > 1e-4
+    assert np.array_equal(L.bnd_wn[~wall], L.bnd_n[~wall])
