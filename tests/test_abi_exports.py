@@ -48,3 +48,38 @@ def test_host_only_calls(lib):
     assert b"sm_103a" in lib.emg_build_info()
     assert lib.emg_profile_class_name(0) == b"residual_face_flux"
     assert lib.emg_last_error(None) == b"null context"
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding mirrors has the header's size and field offsets, as a C
+    compiler lays them out (gcc on the header itself)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    from paper_1807_01151_gb300 import _lib
+    pairs = {"emg_mesh_desc": _lib.MeshDescC, "emg_params": _lib.ParamsC, "emg_cycle_info": _lib.CycleInfoC,
+             "emg_solve_report": _lib.SolveReportC, "emg_server_params": _lib.ServerParamsC,
+             "emg_request_result": _lib.RequestResultC}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "emg.h"', 'int main(void) {']
+    for cname, py in pairs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    import ctypes
+    got = {}
+    for line in out:
+        if line.strip():
+            cname, field, val = line.split()
+            got[cname, field] = int(val)
+    for cname, py in pairs.items():
+        assert got[cname, "sizeof"] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[cname, f] == getattr(py, f).offset, (cname, f)
