@@ -52,7 +52,7 @@ def test_host_only_calls(lib):
 
 def test_ctypes_structs_match_the_header_layout(tmp_path):
     """Every struct the binding mirrors has the header's size and field offsets, as a C
-    compiler lays them out (gcc on the header itself)."""
+    compiler lays them out (gcc on the header itself, as strict C99)."""
     import shutil
     import subprocess
     gcc = shutil.which("gcc")
@@ -71,7 +71,7 @@ def test_ctypes_structs_match_the_header_layout(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text("\n".join(lines) + "\n")
     exe = tmp_path / "layout"
-    subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    subprocess.run([gcc, "-std=c99", "-pedantic-errors", "-Wall", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     import ctypes
     got = {}
